@@ -1,0 +1,362 @@
+"""Benchmark of the signed-particle Wigner Monte Carlo hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload NAME]
+
+A step is one pass of the whole hot path over the ensemble: survivor
+enumeration and occupied cells (rule 2 rebuild), the Wigner kernel on the
+occupied cells with gamma and the momentum CDF, and the particle step (drift,
+absorption, pair creation, signed histogram).  The default workload is the
+2000-cell barrier with 1e7 particles (FP32 kernel).  `value` is particle-steps/s
+over all ranks; N > 1 runs independent replicas (one simulation per rank, its
+own Philox stream), so scaling is weak.  `--impl reference` times the CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import wmc_inputs as wi  # noqa: E402
+
+METRIC = "particle-steps/s; kernel cell·M evals/s at stated err vs FP64 (TC vs FP32)"
+UNIT = "particle-steps/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_rate(w, budget_s: float, n_steps_min: int = 1, max_steps: int = 1000):
+    """Oracle particle-steps/s on w, stepping until budget_s has elapsed."""
+    import oracle
+    p = oracle.params(w)
+    V = wi.potential(w)
+    h = wi.initial_histogram(w)
+    ps = 0
+    t_used = 0.0
+    steps = 0
+    t = 1
+    while steps < max_steps and (steps < n_steps_min or t_used < budget_s):
+        t0 = time.perf_counter()
+        h, st = oracle.simulate(p, h, t, 1, V=V)
+        t_used += time.perf_counter() - t0
+        ps += int(st[oracle.ST_PARTICLE_STEPS])
+        steps += 1
+        t += 1
+    return ps / t_used, ps, steps, t_used
+
+
+def reference_arm(args, w):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    # size each step's sample so that the whole run stays within about 3 minutes
+    per_step_budget = 150.0 / max(1, args.steps + args.warmup)
+    rate0, _, _, _ = oracle_rate(wi.scaled(w, 200_000), 0.0)
+    n0 = int(min(w.packet.n0, max(20_000, rate0 * per_step_budget)))
+    ws = wi.scaled(w, n0)
+    oracle_rate(ws, 0.0, n_steps_min=args.warmup, max_steps=args.warmup) if args.warmup else None
+    rate, ps, steps, secs = oracle_rate(ws, 0.0, n_steps_min=args.steps, max_steps=args.steps)
+    sample = f"{w.name} with N0={n0} (packet shape kept), {steps} oracle steps, {secs:.1f} s"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_x": w.n_x, "Q": w.Q, "n_M": w.n_M, "N0": n0, "kernel": "fp64 oracle"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- native arm
+def native_arm(args, w):
+    import torch
+    from paper_1806_00082_gb300 import build, wmc
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wmc.load()
+
+    wl = w.replace(sim=rank)          # independent replica per rank
+    p = wmc.Params.of(wl)
+    V = torch.from_numpy(wi.potential(wl)).to(dev)
+    h0 = torch.from_numpy(wi.initial_histogram(wl)).to(dev)
+    ws = wmc.workspace(p, dev)
+    a = h0.clone()
+    b = torch.empty_like(a)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    n_iter = max(1, (args.steps + 1) // 2)      # one timed iteration = one graph launch of 2 steps
+    steps = 2 * n_iter
+    with torch.cuda.stream(stream):
+        wmc.init(p, ws)
+        t = 1
+        for _ in range(max(1, (args.warmup + 1) // 2)):
+            wmc.run(p, V, a, b, t, 2, ws)
+            t += 2
+        wmc.reset_counters(p, ws)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_iter)]
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            for q in range(n_iter):
+                flush.zero_()                    # inputs are L2-resident: flush between iterations
+                ev[q][0].record(stream)
+                wmc.run(p, V, a, b, t, 2, ws)
+                ev[q][1].record(stream)
+                t += 2
+            stream.synchronize()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        c = wmc.get_counters(p, ws)
+    ps_local = float(c["particle_steps"])
+    ms_max = ms
+    if world > 1:
+        tt = torch.tensor([ms, ps_local], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.SUM)
+        ms_max, ps_total = float(mx[0]), float(tt[1])
+    else:
+        ps_total = ps_local
+    value = ps_total / (ms_max * 1e-3)
+
+    # ---- dominant kernel: the particle step, timed alone with events on its stream
+    roof = step_roofline(wmc, torch, p, wl, V, a, b, ws, stream, t, flush)
+    # ---- end to end through the C ABI with host buffers
+    e2e = end_to_end(wmc, torch, p, V, ws, stream, h0, t + 4 * n_iter)
+    # ---- kernel evaluation throughput, all cells of the 16384-cell double barrier
+    kev = kernel_eval_rate(wmc, torch, dev, stream, flush) if rank == 0 else None
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, ps_cpu, st_cpu, secs = oracle_rate(w, 10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{w.name} full N0={w.packet.n0}, first {st_cpu} steps ({secs:.1f} s, single thread)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n_x": w.n_x, "Q": w.Q, "n_M": w.n_M, "N0": w.packet.n0,
+                   "dt_fs": w.dt_s / 1e-15, "kernel": "fp32 (compensated)",
+                   "parallelism": f"replicas x{world}", "l2": "flushed between timed iterations (2 steps each)"},
+        "clocks": clk.summary(),
+        "gpu_launches": 5 * steps + n_iter,
+        "e2e": e2e,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "kernel_eval": kev,
+        "counters": {k: c[k] for k in ("pairs", "absorbed", "dropped", "n_occ", "flags")},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def step_roofline(wmc, torch, p, wl, V, a, b, ws, stream, t, flush, n=20):
+    """Average duration of the particle-step kernel over n steps driven call by
+    call, with CUDA events on the launching stream around each wmc_step."""
+    peaks, src = _peaks()
+    durs = []
+    philox_calls = 0
+    D = None
+    with torch.cuda.stream(stream):
+        for q in range(n):
+            wmc.annihilate(p, a, ws)
+            wmc.kernel_eval_occupied(p, V, ws)
+            if D is None:
+                Ms = np.arange(p.n_M) - p.n_M // 2
+                D = Ms != 0
+            counts = a.abs().sum(dim=0).cpu().numpy()
+            philox_calls += int(counts[D].sum())
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wmc.step(p, a, t + q, b, ws)
+            e1.record(stream)
+            stream.synchronize()
+            durs.append(e0.elapsed_time(e1) * 1e-3)
+            a.copy_(b)
+        c = wmc.get_counters(p, ws)
+    # pair-creation draws: only particles in cells with gamma > 0 draw one
+    gen_draws = 0 if c["pairs"] == 0 else None
+    sec = float(np.mean(durs))
+    per_launch = philox_calls / n
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    # ALU peak for Philox4x32-10: 20 32x32->64-bit multiplies per call on the
+    # 64-lane-per-SM integer multiply path, at the maximum SM clock.
+    peak_calls = 152 * 64 * sm_mhz * 1e6 / 20
+    achieved = per_launch / sec
+    return {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": peak_calls,
+            "unit": "Philox4x32-10/s", "frac": achieved / peak_calls, "traffic": None,
+            "per_launch": {"philox_calls": per_launch, "gen_draws": gen_draws, "seconds": sec},
+            "peak_source": f"derived: 152 SMs x 64 IMAD lanes x {sm_mhz:.0f} MHz / 20 multiplies"}
+
+
+def end_to_end(wmc, torch, p, V, ws, stream, h0, t0, n=10):
+    """Per step: H2D of the state from pinned memory, one wmc_run step, D2H of
+    the new state; timed with events on the stream."""
+    host_in = h0.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    a = torch.empty_like(h0)
+    b = torch.empty_like(h0)
+    with torch.cuda.stream(stream):
+        wmc.reset_counters(p, ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for q in range(n):
+            a.copy_(host_in, non_blocking=True)
+            wmc.run(p, V, a, b, t0 + q, 1, ws)
+            host_out.copy_(a, non_blocking=True)
+        e1.record(stream)
+        stream.synchronize()
+        c = wmc.get_counters(p, ws)
+    secs = e0.elapsed_time(e1) * 1e-3
+    nbytes = h0.numel() * 4
+    return {"value": c["particle_steps"] / secs, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": n}
+
+
+def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
+    w = wi.DOUBLE_BARRIER_16384
+    p = wmc.Params.of(w)
+    V = torch.from_numpy(wi.potential(w)).to(dev)
+    ws = wmc.workspace(p, dev)
+    occ = torch.arange(w.n_x, dtype=torch.int32, device=dev)
+    out = torch.empty((w.n_x, w.Q // 2), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        wmc.init(p, ws)
+        for _ in range(3):
+            wmc.kernel_eval(p, V, occ, ws, out=out)
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wmc.kernel_eval(p, V, occ, ws, out=out)
+            e1.record(stream)
+            stream.synchronize()
+            tot += e0.elapsed_time(e1) * 1e-3
+    sec = tot / reps
+    h = w.Q // 2
+    flops = 2.0 * w.n_x * (h - 1) ** 2
+    return {"workload": f"{w.name}, all {w.n_x} cells", "prec": "fp32", "cellM_per_s": w.n_x * w.n_M / sec,
+            "seconds": sec, "tflops_algorithmic": flops / sec / 1e12, "err_bound_normwise": 1e-6}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="barrier-2000", choices=sorted(wi.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = wi.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return reference_arm(args, w)
+    return native_arm(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * wmc.h -- C ABI of libwmc, the GB300 (sm_103a) hot path of the signed-particle
+ * Wigner Monte Carlo method with the analytically weighted network kernel
+ * (Sellier, Leygonie, Marceau Caron, arXiv:1806.00082).
+ *
+ * Plain C: every pointer argument is either a DEVICE pointer (marked [dev]) or
+ * a HOST pointer (marked [host]); sizes are in elements unless stated.  The
+ * caller allocates every buffer and keeps ownership; the library allocates no
+ * device memory on any call below.  Every call is asynchronous on the given
+ * stream unless it says it synchronises.  Argument errors are returned at once;
+ * conditions found on the device (population too large, gamma dt >= 1) set
+ * flags in the workspace that wmc_get_counters() reads.
+ *
+ * Notation (Sec. 2 of the paper):
+ *   cells i = 0 .. n_x-1 of width dx, centre (i + 1/2) dx;
+ *   coherence length L_C = Q dx (Q even), h = Q / 2;
+ *   momentum index M in [-n_M/2, n_M/2), momentum M dp with dp = pi hbar / L_C;
+ *   column k = M + n_M/2 of every [.. x n_M] array.
+ *
+ * Wigner kernel, Eq. (wigner-1d-discrete), with the network weight
+ * w_l = -2 dx / (hbar L_C) of Sec. 2.2:
+ *   V_W(i; M) = -(2 / (hbar Q)) sum_{m=1}^{h-1} sin(2 pi (m M mod Q) / Q) [V(i+m) - V(i-m)]
+ * in 1/s for V in eV.  It is periodic in M with period Q, odd in M, and zero
+ * at M = 0 and M = h, so a row is stored as its half period
+ *   VWh[row][r] = V_W(i; r), r = 0 .. h-1  (VWh[row][0] = 0),
+ * and V_W(i; M) = VWh[r], -VWh[Q - r] or 0 for r = M mod Q below, above or at h.
+ *
+ * Ensemble: the state is the net signed histogram hist[i][k] (int32,
+ * row-major [n_x][n_M]) left by annihilation (rule 2: opposite signs in one
+ * (cell, M) cancel).  Its survivors are numbered row-major over (i, k); the
+ * particle with number id sits in cell i at offset f = u24(Philox(id, t-1,
+ * REPOS, sim).w0) in [0, 1), where t-1 is the step that rebuilt it.
+ * Step t (postulate, Sec. 2.1): every particle drifts, f' = fl32(f + D[M]) with
+ * D[M] = fl32(M hbar pi dt / (m Q dx^2)) cells, and moves to the next or
+ * previous cell when f' >= 1 or f' < 0 (leaving [0, n_x) absorbs it); in its new
+ * cell c it creates a pair with probability gamma(c) dt, gamma = sum_M V_W^+
+ * (Eq. momentum_integral), drawn as u53(w0, w1) < gamma dt from
+ * Philox(id, t, GEN, sim); the pair sits in c with signs +s, -s and momenta
+ * M + M', M - M', M' drawn from V_W^+(c; .) / gamma(c) as the smallest k with
+ * CDF[k] > u53(w2, w3) gamma; children outside the momentum grid are dropped
+ * (or wrapped).  Counts of parents and children in each (cell, M) are summed
+ * with their signs: that sum is the annihilated state of step t.
+ * Philox4x32-10 (Salmon et al., SC'11), key (seed_lo, seed_hi), counter
+ * (id, step, purpose, sim); u24(w) = (w >> 8) 2^-24;
+ * u53(a, b) = ((a >> 5) 2^26 + (b >> 6)) 2^-53.
+ */
+#ifndef WMC_H_
+#define WMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* wmc_stream_t;
+
+typedef struct wmc_params {
+  double dx_m;          /* cell width dx [m] */
+  double mass_kg;       /* particle mass [kg] */
+  double dt_s;          /* time step [s] */
+  uint64_t seed;        /* Philox key (low word, high word) */
+  int32_t n_x;          /* cells, 1 .. 2^24 */
+  int32_t Q;            /* quadrature points L_C / dx, even, 2 .. 4096 */
+  int32_t n_M;          /* momentum indices, even, 2 .. 4096 */
+  int32_t bc_potential; /* 0: V = 0 outside [0, n_x); 1: V takes the edge value */
+  int32_t child_wrap;   /* 0: drop children outside the momentum grid; 1: wrap */
+  uint32_t sim;         /* simulation index: Philox counter word 3 */
+} wmc_params;
+
+typedef enum wmc_status {
+  WMC_OK = 0,
+  WMC_ERR_ARG = 1,          /* bad argument or parameter */
+  WMC_ERR_CAPACITY = 2,     /* population >= 2^32 or output capacity too small */
+  WMC_ERR_RATE = 3,         /* gamma dt >= 1 in an evaluated cell */
+  WMC_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  WMC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  WMC_ERR_UNSUPPORTED = 6   /* precision or shape not supported by this build */
+} wmc_status;
+
+/* Input precision of the sine x dV contraction (accumulation is FP32). */
+typedef enum wmc_precision {
+  WMC_FP32 = 0,        /* FP32 inputs, compensated FP32 accumulation (SIMT) */
+  WMC_BF16 = 1,        /* BF16 inputs on the tensor cores */
+  WMC_FP16 = 2,        /* FP16 inputs on the tensor cores */
+  WMC_FP16_SPLIT = 3,  /* FP16 hi/lo split, three tensor-core products */
+  WMC_TF32X3 = 4       /* TF32 hi/lo split, three tensor-core products */
+} wmc_precision;
+
+/* Device flags, readable with wmc_get_counters(). */
+#define WMC_FLAG_RATE 1u      /* an evaluated cell had gamma dt >= 1 (events then always fire) */
+#define WMC_FLAG_CAPACITY 2u  /* population >= 2^32 (the step did nothing) or a capacity was short */
+#define WMC_FLAG_TIMEOUT 4u   /* a bounded device wait gave up */
+
+/* Counters kept in the workspace, cumulative since wmc_init / wmc_reset_counters. */
+typedef struct wmc_counters {
+  uint64_t population;      /* survivors enumerated by the last wmc_annihilate */
+  uint64_t particle_steps;  /* sum over steps of the population at step start */
+  uint64_t pairs;           /* pairs created */
+  uint64_t absorbed;        /* particles that left [0, n_x) */
+  int64_t absorbed_signed;  /* sum of their signs */
+  uint64_t dropped;         /* children outside the momentum grid (drop mode) */
+  int64_t dropped_signed;   /* sum of their signs */
+  int32_t n_occ;            /* cells whose kernel the last step evaluated */
+  int32_t n_items;          /* work items of the last step */
+  uint32_t flags;           /* WMC_FLAG_* */
+  uint32_t step;            /* device step counter used by wmc_run */
+} wmc_counters;
+
+/* Library version string. */
+const char* wmc_version(void);
+
+/* Static description of a status code. */
+const char* wmc_status_string(wmc_status s);
+
+/* Bytes of device workspace for these parameters (0 if they are invalid).
+ * The workspace holds the survivor enumeration, the occupied-cell list, the
+ * kernel rows, CDFs and thresholds of up to n_x cells, the drift table, the
+ * sine matrices and the counters.  Allocate it once per simulation, aligned
+ * to 256 bytes (any cudaMalloc / torch allocation is). */
+size_t wmc_workspace_size(const wmc_params* p);
+
+/* Checks p, fills the workspace's constant tables (drift D, sine matrices)
+ * and zeroes its counters.  ws [dev] of ws_bytes >= wmc_workspace_size(p).
+ * Must precede every other call that takes ws.  Stream-ordered. */
+wmc_status wmc_init(const wmc_params* p, void* ws, size_t ws_bytes, wmc_stream_t stream);
+
+/* Zeroes the counters and flags of an initialised workspace. */
+wmc_status wmc_reset_counters(const wmc_params* p, void* ws, wmc_stream_t stream);
+
+/* Reads the counters (synchronises the stream).  out [host]. */
+wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* out, wmc_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Kernel evaluation on given cells -- Eq. (wigner-1d-discrete) as the N = 1
+ * analytic network of Sec. 2.2 (hidden units V(l) sin(theta_l), output weight
+ * w_l): a contraction of the potential differences against the integer-indexed
+ * sine matrix S[m][r] = sin(2 pi (m r mod Q) / Q).
+ *   V    [dev] float[n_x], eV.
+ *   occ  [dev] int32[n_occ], cells in [0, n_x) (any order, repeats allowed).
+ *   n_occ 0 .. n_x (host value).
+ *   prec WMC_FP32 or a tensor-core form (WMC_ERR_UNSUPPORTED if not built).
+ *   VWh  [dev] float[n_occ][Q/2], half-period rows (layout above); written.
+ * ------------------------------------------------------------------------- */
+wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
+                           wmc_precision prec, float* VWh, void* ws, wmc_stream_t stream);
+
+/* gamma and the momentum CDF of kernel rows -- Eq. (momentum_integral): for each
+ * row, cdf[row][k] = sum_{k' <= k} max(V_W(k'), 0) in FP64, summed in ascending
+ * k, and gamma[row] = cdf[row][n_M - 1].
+ *   VWh   [dev] float[n_rows][Q/2].
+ *   cdf   [dev] double[n_rows][n_M] (row-major) or NULL.
+ *   gamma [dev] double[n_rows]. */
+wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows, double* cdf,
+                          double* gamma, void* ws, wmc_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * The simulation step, as three stream-ordered calls on one workspace:
+ *   wmc_annihilate(hist_t-1)  -> survivor enumeration + occupied cells
+ *   wmc_kernel_eval_occupied  -> V_W, CDF, gamma on those cells
+ *   wmc_step(hist_t-1 -> hist_t)
+ * wmc_run() chains them for many steps (in a CUDA graph where it can).
+ * ------------------------------------------------------------------------- */
+
+/* Rule 2 rebuild: enumerates the survivors of the net histogram hist [dev]
+ * int32[n_x][n_M] (row-major ids, work items of 4096 particles), marks the
+ * cells the next drift can reach (occupied cells and their neighbour in each
+ * drift direction present) as the occupied list for the kernel, and, if
+ * rho [dev] int64[n_x] is not NULL, writes the density (rule 1) of hist.
+ * A population >= 2^32 sets WMC_FLAG_CAPACITY and the next step does nothing. */
+wmc_status wmc_annihilate(const wmc_params* p, const int32_t* hist, int64_t* rho, void* ws,
+                          wmc_stream_t stream);
+
+/* Kernel rows, CDFs and event thresholds for the occupied list of the last
+ * wmc_annihilate, kept in the workspace.  V [dev] float[n_x] in eV. */
+wmc_status wmc_kernel_eval_occupied(const wmc_params* p, const float* V, wmc_precision prec, void* ws,
+                                    wmc_stream_t stream);
+
+/* Same, but the kernel values come from a caller table instead of the
+ * contraction (e.g. a trained network's output): table [dev] float[n_x][Q/2]
+ * half-period rows for every cell. */
+wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, void* ws,
+                                     wmc_stream_t stream);
+
+/* Step t >= 1 of the postulate (drift, absorption, pair creation, histogram of
+ * parents and children): reads hist_in [dev] (the state left by step t-1, as
+ * enumerated by the last wmc_annihilate) and writes the net histogram of step
+ * t to hist_out [dev] int32[n_x][n_M] (overwritten; must not alias hist_in). */
+wmc_status wmc_step(const wmc_params* p, const int32_t* hist_in, uint32_t t, int32_t* hist_out, void* ws,
+                    wmc_stream_t stream);
+
+/* n_steps steps t = t_first .. t_first + n_steps - 1 starting from hist_a [dev]
+ * (the state after step t_first - 1), using hist_b [dev] as the second
+ * buffer; the final state is left in hist_a.  prec selects the kernel form.
+ * use_graph != 0 captures the step pair in a CUDA graph (not on the legacy
+ * default stream, where it runs the calls directly). */
+wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t* hist_b, uint32_t t_first,
+                   int32_t n_steps, wmc_precision prec, int32_t use_graph, void* ws, wmc_stream_t stream);
+
+/* Rule 1: rho[i] = sum_k hist[i][k].  hist [dev] int32[n_x][n_M], rho [dev] int64[n_x]. */
+wmc_status wmc_density(const wmc_params* p, const int32_t* hist, int64_t* rho, wmc_stream_t stream);
+
+/* Explicit survivors of the last wmc_annihilate, as rebuilt at step t (the
+ * offset of id is u24(Philox(id, t, REPOS, sim).w0)): SoA arrays [dev] of
+ * capacity elements, written in id order.  If the population exceeds capacity
+ * nothing is written and WMC_FLAG_CAPACITY is set. */
+wmc_status wmc_materialize(const wmc_params* p, const int32_t* hist, uint32_t t, int32_t* cell, float* f,
+                           int16_t* M, int8_t* sign, int64_t capacity, void* ws, wmc_stream_t stream);
+
+/* Philox4x32-10 of n counters ctr [dev] uint32[n][4] under key (key0, key1),
+ * out [dev] uint32[n][4].  The generator the step uses, exposed for checks. */
+wmc_status wmc_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int64_t n, uint32_t* out,
+                             wmc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WMC_H_ */

@@ -1,0 +1,340 @@
+// Host side of the libwmc C ABI: argument checks, workspace layout, the
+// per-step call sequence and its CUDA-graph capture.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "wmc_internal.cuh"
+
+namespace wmc {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool params_ok(const wmc_params* p) {
+  if (!p) return false;
+  if (p->n_x < 1 || p->n_x > (1 << 24)) return false;
+  if (p->Q < 2 || p->Q > 4096 || (p->Q & 1)) return false;
+  if (p->n_M < 2 || p->n_M > 4096 || (p->n_M & 1)) return false;
+  if (!(p->dx_m > 0) || !(p->mass_kg > 0) || !(p->dt_s > 0)) return false;
+  if (p->bc_potential != 0 && p->bc_potential != 1) return false;
+  if (p->child_wrap != 0 && p->child_wrap != 1) return false;
+  // a particle may move at most to the neighbouring cell in one step
+  const double d1 = ((kHbarJs * kPi) * p->dt_s) / ((p->mass_kg * (double)p->Q) * (p->dx_m * p->dx_m));
+  const float dmax = (float)((double)(p->n_M / 2) * d1);
+  if (!(dmax < 1.0f)) return false;
+  return true;
+}
+
+Layout layout(const wmc_params& p) {
+  Layout L;
+  const size_t nx = (size_t)p.n_x, nM = (size_t)p.n_M;
+  L.h = p.Q / 2;
+  L.Kp = ((L.h - 1 + 31) / 32) * 32;
+  if (L.Kp == 0) L.Kp = 32;
+  L.Np = ((L.h + 63) / 64) * 64;
+  L.ld = p.n_x;
+  size_t o = 0;
+  L.header = o; o = align256(o + sizeof(DevHeader));
+  L.T = o; o = align256(o + sizeof(unsigned long long) * nx);
+  L.R = o; o = align256(o + sizeof(unsigned long long) * (nx + 1));
+  L.IP = o; o = align256(o + sizeof(int) * (nx + 1));
+  L.reach = o; o = align256(o + nx);
+  L.occ = o; o = align256(o + sizeof(int) * nx);
+  L.row_map = o; o = align256(o + sizeof(int) * nx);
+  L.VWh = o; o = align256(o + sizeof(float) * nx * (size_t)L.h);
+  L.cdf = o; o = align256(o + sizeof(double) * nx * nM);
+  L.gamma = o; o = align256(o + sizeof(double) * nx);
+  L.gthr = o; o = align256(o + sizeof(unsigned long long) * nx);
+  L.D = o; o = align256(o + sizeof(float) * nM);
+  L.B = o; o = align256(o + sizeof(float) * (size_t)L.Kp * (size_t)L.Np);
+  L.total = o;
+  return L;
+}
+
+View view(const wmc_params& p, void* ws) {
+  const Layout L = layout(p);
+  char* b = static_cast<char*>(ws);
+  View v;
+  v.hdr = reinterpret_cast<DevHeader*>(b + L.header);
+  v.T = reinterpret_cast<unsigned long long*>(b + L.T);
+  v.R = reinterpret_cast<unsigned long long*>(b + L.R);
+  v.IP = reinterpret_cast<int*>(b + L.IP);
+  v.reach = reinterpret_cast<unsigned char*>(b + L.reach);
+  v.occ = reinterpret_cast<int*>(b + L.occ);
+  v.row_map = reinterpret_cast<int*>(b + L.row_map);
+  v.VWh = reinterpret_cast<float*>(b + L.VWh);
+  v.cdf = reinterpret_cast<double*>(b + L.cdf);
+  v.gamma = reinterpret_cast<double*>(b + L.gamma);
+  v.gthr = reinterpret_cast<unsigned long long*>(b + L.gthr);
+  v.D = reinterpret_cast<float*>(b + L.D);
+  v.B = reinterpret_cast<float*>(b + L.B);
+  return v;
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 1;
+  }
+  return cached[dev];
+}
+
+__global__ void k_set_step(DevHeader* hdr, uint32_t step) { hdr->step = step; }
+
+__global__ void k_reset_counters(DevHeader* hdr) {
+  hdr->particle_steps = 0;
+  hdr->pairs = 0;
+  hdr->absorbed = 0;
+  hdr->absorbed_signed = 0;
+  hdr->dropped = 0;
+  hdr->dropped_signed = 0;
+  hdr->flags = 0;
+}
+
+static wmc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WMC_OK : WMC_ERR_CUDA; }
+
+// drift + kernel + step for one step, state in -> out, step number on the device
+static wmc_status one_step(const wmc_params& p, const View& v, const float* V, const int32_t* in, int32_t* out,
+                           wmc_precision prec, int device_step, uint32_t t, cudaStream_t s) {
+  const Layout L = layout(p);
+  cudaError_t e = launch_plan(p, v, in, nullptr, device_step, s);
+  if (e != cudaSuccess) return WMC_ERR_CUDA;
+  (void)prec;
+  e = launch_kernel_eval(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, s);
+  if (e != cudaSuccess) return WMC_ERR_CUDA;
+  e = launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, L.ld, 1, v.gamma, v.gthr, &v.hdr->flags, s);
+  if (e != cudaSuccess) return WMC_ERR_CUDA;
+  e = cudaMemsetAsync(out, 0, sizeof(int32_t) * (size_t)p.n_x * (size_t)p.n_M, s);
+  if (e != cudaSuccess) return WMC_ERR_CUDA;
+  e = launch_step(p, v, in, t, device_step, out, s);
+  return cuda_status(e);
+}
+
+// One cached executable graph of the step pair a -> b -> a.
+struct GraphCache {
+  std::mutex mu;
+  bool valid = false;
+  wmc_params p;
+  const void *V, *a, *b, *ws;
+  int prec;
+  cudaStream_t stream;
+  int device;
+  cudaGraphExec_t exec = nullptr;
+};
+static GraphCache g_graph;
+
+}  // namespace wmc
+
+using namespace wmc;
+
+extern "C" {
+
+const char* wmc_version(void) { return "libwmc 0.1 (sm_103a)"; }
+
+const char* wmc_status_string(wmc_status s) {
+  switch (s) {
+    case WMC_OK: return "ok";
+    case WMC_ERR_ARG: return "invalid argument";
+    case WMC_ERR_CAPACITY: return "capacity exceeded";
+    case WMC_ERR_RATE: return "gamma dt >= 1";
+    case WMC_ERR_CUDA: return "CUDA error";
+    case WMC_ERR_TIMEOUT: return "device wait timed out";
+    case WMC_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+size_t wmc_workspace_size(const wmc_params* p) {
+  if (!params_ok(p)) return 0;
+  return layout(*p).total;
+}
+
+wmc_status wmc_init(const wmc_params* p, void* ws, size_t ws_bytes, wmc_stream_t stream) {
+  if (!params_ok(p) || !ws) return WMC_ERR_ARG;
+  if (((uintptr_t)ws & 255) != 0) return WMC_ERR_ARG;
+  const Layout L = layout(*p);
+  if (ws_bytes < L.total) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  (void)num_sms();
+  prepare_step(*p);
+  return cuda_status(launch_init_tables(*p, v, (cudaStream_t)stream));
+}
+
+wmc_status wmc_reset_counters(const wmc_params* p, void* ws, wmc_stream_t stream) {
+  if (!params_ok(p) || !ws) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  k_reset_counters<<<1, 1, 0, (cudaStream_t)stream>>>(v.hdr);
+  return cuda_status(cudaGetLastError());
+}
+
+wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* out, wmc_stream_t stream) {
+  if (!params_ok(p) || !ws || !out) return WMC_ERR_ARG;
+  DevHeader h;
+  const View v = view(*p, const_cast<void*>(ws));
+  cudaError_t e = cudaMemcpyAsync(&h, v.hdr, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return WMC_ERR_CUDA;
+  out->population = h.population;
+  out->particle_steps = h.particle_steps;
+  out->pairs = h.pairs;
+  out->absorbed = h.absorbed;
+  out->absorbed_signed = h.absorbed_signed;
+  out->dropped = h.dropped;
+  out->dropped_signed = h.dropped_signed;
+  out->n_occ = h.n_occ;
+  out->n_items = h.n_items;
+  out->flags = h.flags;
+  out->step = h.step;
+  if (h.magic != kMagic) return WMC_ERR_ARG;
+  return WMC_OK;
+}
+
+wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
+                           wmc_precision prec, float* VWh, void* ws, wmc_stream_t stream) {
+  if (!params_ok(p) || !V || !ws || n_occ < 0 || (n_occ > 0 && (!occ || !VWh))) return WMC_ERR_ARG;
+  if (prec != WMC_FP32) return WMC_ERR_UNSUPPORTED;
+  if (n_occ == 0) return WMC_OK;
+  const View v = view(*p, ws);
+  return cuda_status(launch_kernel_eval(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, (cudaStream_t)stream));
+}
+
+wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows, double* cdf, double* gamma,
+                          void* ws, wmc_stream_t stream) {
+  if (!params_ok(p) || n_rows < 0 || (n_rows > 0 && (!VWh || !gamma))) return WMC_ERR_ARG;
+  (void)ws;
+  if (n_rows == 0) return WMC_OK;
+  return cuda_status(launch_cdf(*p, VWh, nullptr, n_rows, n_rows, cdf, 1, p->n_M, gamma, nullptr, nullptr,
+                                (cudaStream_t)stream));
+}
+
+wmc_status wmc_annihilate(const wmc_params* p, const int32_t* hist, int64_t* rho, void* ws, wmc_stream_t stream) {
+  if (!params_ok(p) || !hist || !ws) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  return cuda_status(launch_plan(*p, v, hist, rho, 0, (cudaStream_t)stream));
+}
+
+wmc_status wmc_kernel_eval_occupied(const wmc_params* p, const float* V, wmc_precision prec, void* ws,
+                                    wmc_stream_t stream) {
+  if (!params_ok(p) || !V || !ws) return WMC_ERR_ARG;
+  if (prec != WMC_FP32) return WMC_ERR_UNSUPPORTED;
+  const View v = view(*p, ws);
+  const Layout L = layout(*p);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_kernel_eval(*p, V, v.occ, &v.hdr->n_occ, 0, p->n_x, v.B, v.VWh, s);
+  if (e == cudaSuccess)
+    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, L.ld, 1, v.gamma, v.gthr, &v.hdr->flags, s);
+  return cuda_status(e);
+}
+
+wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, void* ws, wmc_stream_t stream) {
+  if (!params_ok(p) || !table || !ws) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  const Layout L = layout(*p);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_gather_table(*p, table, v.occ, &v.hdr->n_occ, p->n_x, v.VWh, s);
+  if (e == cudaSuccess)
+    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, L.ld, 1, v.gamma, v.gthr, &v.hdr->flags, s);
+  return cuda_status(e);
+}
+
+wmc_status wmc_step(const wmc_params* p, const int32_t* hist_in, uint32_t t, int32_t* hist_out, void* ws,
+                    wmc_stream_t stream) {
+  if (!params_ok(p) || !hist_in || !hist_out || !ws || hist_in == hist_out || t == 0) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(hist_out, 0, sizeof(int32_t) * (size_t)p->n_x * (size_t)p->n_M, s);
+  if (e == cudaSuccess) e = launch_step(*p, v, hist_in, t, 0, hist_out, s);
+  return cuda_status(e);
+}
+
+wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t* hist_b, uint32_t t_first,
+                   int32_t n_steps, wmc_precision prec, int32_t use_graph, void* ws, wmc_stream_t stream) {
+  if (!params_ok(p) || !V || !hist_a || !hist_b || hist_a == hist_b || !ws || n_steps < 0 || t_first == 0)
+    return WMC_ERR_ARG;
+  if (prec != WMC_FP32) return WMC_ERR_UNSUPPORTED;
+  if (n_steps == 0) return WMC_OK;
+  const View v = view(*p, ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  k_set_step<<<1, 1, 0, s>>>(v.hdr, t_first - 1u);
+  if (cudaGetLastError() != cudaSuccess) return WMC_ERR_CUDA;
+  const int pairs = n_steps / 2;
+  if (use_graph && s != nullptr && pairs > 0) {
+    std::lock_guard<std::mutex> lock(g_graph.mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool hit = g_graph.valid && memcmp(&g_graph.p, p, sizeof(wmc_params)) == 0 && g_graph.V == V &&
+                     g_graph.a == hist_a && g_graph.b == hist_b && g_graph.ws == ws && g_graph.prec == (int)prec &&
+                     g_graph.stream == s && g_graph.device == dev;
+    if (!hit) {
+      if (g_graph.exec) {
+        cudaGraphExecDestroy(g_graph.exec);
+        g_graph.exec = nullptr;
+      }
+      g_graph.valid = false;
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WMC_ERR_CUDA;
+      wmc_status st = one_step(*p, v, V, hist_a, hist_b, prec, 1, 0, s);
+      if (st == WMC_OK) st = one_step(*p, v, V, hist_b, hist_a, prec, 1, 0, s);
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (st != WMC_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return WMC_ERR_CUDA;
+      }
+      e = cudaGraphInstantiate(&g_graph.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return WMC_ERR_CUDA;
+      g_graph.valid = true;
+      g_graph.p = *p;
+      g_graph.V = V;
+      g_graph.a = hist_a;
+      g_graph.b = hist_b;
+      g_graph.ws = ws;
+      g_graph.prec = (int)prec;
+      g_graph.stream = s;
+      g_graph.device = dev;
+    }
+    for (int q = 0; q < pairs; ++q)
+      if (cudaGraphLaunch(g_graph.exec, s) != cudaSuccess) return WMC_ERR_CUDA;
+  } else {
+    for (int q = 0; q < pairs; ++q) {
+      wmc_status st = one_step(*p, v, V, hist_a, hist_b, prec, 1, 0, s);
+      if (st == WMC_OK) st = one_step(*p, v, V, hist_b, hist_a, prec, 1, 0, s);
+      if (st != WMC_OK) return st;
+    }
+  }
+  if (n_steps & 1) {
+    wmc_status st = one_step(*p, v, V, hist_a, hist_b, prec, 1, 0, s);
+    if (st != WMC_OK) return st;
+    if (cudaMemcpyAsync(hist_a, hist_b, sizeof(int32_t) * (size_t)p->n_x * (size_t)p->n_M,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return WMC_ERR_CUDA;
+  }
+  return WMC_OK;
+}
+
+wmc_status wmc_density(const wmc_params* p, const int32_t* hist, int64_t* rho, wmc_stream_t stream) {
+  if (!params_ok(p) || !hist || !rho) return WMC_ERR_ARG;
+  return cuda_status(launch_density(*p, hist, rho, (cudaStream_t)stream));
+}
+
+wmc_status wmc_materialize(const wmc_params* p, const int32_t* hist, uint32_t t, int32_t* cell, float* f,
+                           int16_t* M, int8_t* sign, int64_t capacity, void* ws, wmc_stream_t stream) {
+  if (!params_ok(p) || !hist || !ws || capacity < 0) return WMC_ERR_ARG;
+  if (capacity > 0 && (!cell || !f || !M || !sign)) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  return cuda_status(launch_materialize(*p, v, hist, t, cell, f, M, sign, capacity, (cudaStream_t)stream));
+}
+
+wmc_status wmc_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int64_t n, uint32_t* out,
+                             wmc_stream_t stream) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return WMC_ERR_ARG;
+  return cuda_status(launch_philox(ctr, key0, key1, n, out, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Internal declarations shared by the libwmc translation units: workspace
+// layout, device header, Philox4x32-10 and launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wmc.h"
+
+namespace wmc {
+
+constexpr double kHbarEVs = 6.582119569e-16;  // hbar [eV s]
+constexpr double kHbarJs = 1.054571817e-34;   // hbar [J s]
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr uint32_t kPurposeGen = 1u;    // Philox counter word 2 of the pair-creation draw
+constexpr uint32_t kPurposeRepos = 2u;  // ... of the offset a survivor is re-emitted at
+
+// Step work decomposition: a work item is up to kChunk consecutive particles of
+// one cell; a block of kStepThreads threads handles one item at a time and
+// each thread kPerThread consecutive particles of it.
+constexpr int kStepThreads = 256;
+constexpr int kPerThread = 16;
+constexpr int kChunk = kStepThreads * kPerThread;
+
+constexpr unsigned kMagic = 0x574d4331u;  // "WMC1": set by wmc_init
+
+// Lives at offset 0 of the workspace.
+struct DevHeader {
+  unsigned long long population;      // survivors enumerated by the last plan
+  unsigned long long particle_steps;  // cumulative
+  unsigned long long pairs;
+  unsigned long long absorbed;
+  long long absorbed_signed;
+  unsigned long long dropped;
+  long long dropped_signed;
+  int n_items;
+  int n_occ;
+  unsigned int flags;
+  unsigned int step;    // device step counter (wmc_run)
+  unsigned int magic;
+  unsigned int pad[5];
+};
+
+// Byte offsets of the workspace regions (all 256-aligned).
+struct Layout {
+  size_t header, T, R, IP, reach, occ, row_map, VWh, cdf, gamma, gthr, D, B, total;
+  int h;     // Q / 2
+  int Kp;    // contraction length h - 1 padded to a multiple of 32
+  int Np;    // output columns h padded to a multiple of 64
+  int ld;    // leading dimension of the transposed CDF (= n_x)
+};
+
+bool params_ok(const wmc_params* p);
+Layout layout(const wmc_params& p);
+
+// Device pointers of one workspace.
+struct View {
+  DevHeader* hdr;
+  unsigned long long* T;   // [n_x] survivors per cell
+  unsigned long long* R;   // [n_x + 1] first id of each cell (exclusive prefix of T)
+  int* IP;                 // [n_x + 1] first work item of each cell
+  unsigned char* reach;    // [n_x] bit0 occupied, bit1 some drift right, bit2 some drift left
+  int* occ;                // [n_x] occupied-cell list (ascending)
+  int* row_map;            // [n_x] cell -> row of occ, or -1
+  float* VWh;              // [n_x][h] kernel half-period rows, by occ row
+  double* cdf;             // [n_M][ld] CDF, transposed (column k, row)
+  double* gamma;           // [n_x] gamma by occ row
+  unsigned long long* gthr;// [n_x] event threshold: u53 integer < gthr <=> u53 < gamma dt
+  float* D;                // [n_M] drift per step in cells
+  float* B;                // [Kp][Np] sine matrix S[m][r], m = kk + 1
+};
+View view(const wmc_params& p, void* ws);
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of two 32x32 -> 64-bit
+// multiplications (0xD2511F53, 0xCD9E8D57) with the word permutation of the
+// four-word variant, and a Weyl key schedule (0x9E3779B9, 0xBB67AE85).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t s);
+cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, int advance_step,
+                        cudaStream_t s);
+cudaError_t launch_kernel_eval(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
+                               int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s);
+cudaError_t launch_gather_table(const wmc_params& p, const float* table, const int* occ, const int* n_occ_dev,
+                                int max_rows, float* VWh, cudaStream_t s);
+// CDF of rows: cdf[k * ldk + row * ldr]; gthr/flags may be null.
+cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host,
+                       int max_rows, double* cdf, long long ldk, long long ldr, double* gamma,
+                       unsigned long long* gthr, unsigned int* flags, cudaStream_t s);
+cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_in, uint32_t t, int t_from_device,
+                        int32_t* hist_out, cudaStream_t s);
+cudaError_t launch_materialize(const wmc_params& p, const View& v, const int32_t* hist, uint32_t t, int32_t* cell,
+                               float* f, int16_t* M, int8_t* sign, long long capacity, cudaStream_t s);
+cudaError_t launch_density(const wmc_params& p, const int32_t* hist, int64_t* rho, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, long long n, uint32_t* out,
+                          cudaStream_t s);
+
+int num_sms();
+// Caches the step kernel's launch shape for this device (call outside graph capture).
+void prepare_step(const wmc_params& p);
+
+}  // namespace wmc

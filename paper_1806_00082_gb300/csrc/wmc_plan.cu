@@ -1,0 +1,245 @@
+// Survivor enumeration after annihilation (rule 2), occupied cells for the
+// kernel, density (rule 1), constant tables and the Philox check kernel.
+#include <math.h>
+
+#include "wmc_internal.cuh"
+
+namespace wmc {
+
+// ---------------------------------------------------------------- constant tables
+// D[k] = fl32(M * d1), d1 = hbar pi dt / (m Q dx^2), M = k - n_M/2: the free
+// drift of momentum M dp over dt, in cells.  B[kk][r] = sin(2 pi ((kk+1) r mod Q) / Q)
+// for kk < h-1, r < h (zero padding elsewhere): the integer-indexed sine matrix
+// of the network's hidden layer (Sec. 2.2).
+__global__ void k_init_tables(int n_M, int Q, double d1, float* __restrict__ D, float* __restrict__ B, int Kp,
+                              int Np, DevHeader* hdr) {
+  const int h = Q / 2;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  if (tid == 0) {
+    DevHeader z = {};
+    z.magic = kMagic;
+    *hdr = z;
+  }
+  for (long long k = tid; k < n_M; k += nthreads) D[k] = __double2float_rn((double)(k - n_M / 2) * d1);
+  for (long long q = tid; q < (long long)Kp * Np; q += nthreads) {
+    const int kk = (int)(q / Np), r = (int)(q % Np);
+    float v = 0.f;
+    if (kk < h - 1 && r < h) {
+      const long long t = ((long long)(kk + 1) * r) % Q;
+      v = __double2float_rn(sinpi(2.0 * (double)t / (double)Q));
+    }
+    B[q] = v;
+  }
+}
+
+cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t s) {
+  const Layout L = layout(p);
+  const double d1 = ((kHbarJs * kPi) * p.dt_s) / ((p.mass_kg * (double)p.Q) * (p.dx_m * p.dx_m));
+  k_init_tables<<<256, 256, 0, s>>>(p.n_M, p.Q, d1, v.D, v.B, L.Kp, L.Np, v.hdr);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- per-cell scan
+// One warp per cell: survivors T[i] = sum_k |n(i,k)|, reach bits (bit0 cell
+// occupied, bit1 a momentum that drifts right is present, bit2 one that drifts
+// left), and optionally the density rho[i] = sum_k n(i,k).
+__global__ void k_rows(const int32_t* __restrict__ hist, int n_x, int n_M, const float* __restrict__ D,
+                       unsigned long long* __restrict__ T, unsigned char* __restrict__ reach,
+                       long long* __restrict__ rho) {
+  const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_x) return;
+  const int32_t* row = hist + (size_t)warp * n_M;
+  unsigned long long a = 0;
+  long long sn = 0;
+  unsigned bits = 0;
+  if ((n_M & 3) == 0) {
+    const int4* row4 = reinterpret_cast<const int4*>(row);
+    const float4* D4 = reinterpret_cast<const float4*>(D);
+    for (int q = lane; q < n_M / 4; q += 32) {
+      const int4 n = row4[q];
+      const float4 d = D4[q];
+      const int nv[4] = {n.x, n.y, n.z, n.w};
+      const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (nv[e]) {
+          a += (unsigned long long)(nv[e] < 0 ? -(long long)nv[e] : (long long)nv[e]);
+          sn += nv[e];
+          bits |= 1u | (dv[e] > 0.f ? 2u : 0u) | (dv[e] < 0.f ? 4u : 0u);
+        }
+      }
+    }
+  } else {
+    for (int k = lane; k < n_M; k += 32) {
+      const int n = row[k];
+      if (n) {
+        a += (unsigned long long)(n < 0 ? -(long long)n : (long long)n);
+        sn += n;
+        bits |= 1u | (D[k] > 0.f ? 2u : 0u) | (D[k] < 0.f ? 4u : 0u);
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    sn += __shfl_down_sync(0xffffffffu, sn, off);
+    bits |= __shfl_down_sync(0xffffffffu, bits, off);
+  }
+  if (lane == 0) {
+    T[warp] = a;
+    reach[warp] = (unsigned char)bits;
+    if (rho) rho[warp] = sn;
+  }
+}
+
+__device__ __forceinline__ int needs_kernel(const unsigned char* reach, int i, int n_x) {
+  return (reach[i] & 1) || (i > 0 && (reach[i - 1] & 2)) || (i + 1 < n_x && (reach[i + 1] & 4));
+}
+
+__device__ __forceinline__ int items_of(unsigned long long t) { return (int)((t + kChunk - 1) / kChunk); }
+
+// One block: exclusive prefix sums of survivors (ids), work items and needed
+// cells, then the occupied list and row map.  Single block because n_x is at
+// most a few 10^4 in the workloads and this runs once per step.
+constexpr int kPlanThreads = 1024;
+
+__global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned long long* __restrict__ T,
+                                                       const unsigned char* __restrict__ reach,
+                                                       unsigned long long* __restrict__ R, int* __restrict__ IP,
+                                                       int* __restrict__ occ, int* __restrict__ row_map,
+                                                       DevHeader* hdr, int advance_step) {
+  __shared__ unsigned long long wT[32];
+  __shared__ int wI[32], wN[32], wBig[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int per = (n_x + kPlanThreads - 1) / kPlanThreads;
+  const int lo = min(tid * per, n_x), hi = min(lo + per, n_x);
+  unsigned long long aT = 0;
+  int aI = 0, aN = 0, big = 0;
+  for (int i = lo; i < hi; ++i) {
+    const unsigned long long t = T[i];
+    aT += t;
+    aI += items_of(t);
+    aN += needs_kernel(reach, i, n_x);
+    big |= t > 0x7fffffffull;
+  }
+  // block-wide exclusive scan of (aT, aI, aN)
+  unsigned long long iT = aT;
+  int iI = aI, iN = aN;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long uT = __shfl_up_sync(0xffffffffu, iT, off);
+    const int uI = __shfl_up_sync(0xffffffffu, iI, off);
+    const int uN = __shfl_up_sync(0xffffffffu, iN, off);
+    if (lane >= off) {
+      iT += uT;
+      iI += uI;
+      iN += uN;
+    }
+  }
+  big = __any_sync(0xffffffffu, big);
+  if (lane == 31) {
+    wT[wid] = iT;
+    wI[wid] = iI;
+    wN[wid] = iN;
+    wBig[wid] = big;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long sT = wT[lane];
+    int sI = wI[lane], sN = wN[lane], sB = wBig[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long uT = __shfl_up_sync(0xffffffffu, sT, off);
+      const int uI = __shfl_up_sync(0xffffffffu, sI, off);
+      const int uN = __shfl_up_sync(0xffffffffu, sN, off);
+      if (lane >= off) {
+        sT += uT;
+        sI += uI;
+        sN += uN;
+      }
+    }
+    sB = __any_sync(0xffffffffu, sB);
+    wT[lane] = sT;
+    wI[lane] = sI;
+    wN[lane] = sN;
+    wBig[lane] = sB;
+  }
+  __syncthreads();
+  const unsigned long long baseT = (wid ? wT[wid - 1] : 0ull) + iT - aT;
+  int baseI = (wid ? wI[wid - 1] : 0) + iI - aI;
+  int baseN = (wid ? wN[wid - 1] : 0) + iN - aN;
+  unsigned long long r = baseT;
+  for (int i = lo; i < hi; ++i) {
+    const unsigned long long t = T[i];
+    R[i] = r;
+    IP[i] = baseI;
+    if (needs_kernel(reach, i, n_x)) {
+      occ[baseN] = i;
+      row_map[i] = baseN;
+      ++baseN;
+    } else {
+      row_map[i] = -1;
+    }
+    r += t;
+    baseI += items_of(t);
+  }
+  if (tid == kPlanThreads - 1) {
+    const unsigned long long P = wT[31];
+    const int too_big = wBig[31] || P >= (1ull << 32);
+    R[n_x] = P;
+    IP[n_x] = wI[31];
+    hdr->population = P;
+    hdr->n_items = too_big ? 0 : wI[31];
+    hdr->n_occ = wN[31];
+    if (too_big) atomicOr(&hdr->flags, WMC_FLAG_CAPACITY);
+    if (advance_step) hdr->step += 1u;
+  }
+}
+
+cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, int advance_step,
+                        cudaStream_t s) {
+  const int warps_per_block = 8;
+  const int blocks = (p.n_x + warps_per_block - 1) / warps_per_block;
+  k_rows<<<blocks, warps_per_block * 32, 0, s>>>(hist, p.n_x, p.n_M, v.D, v.T, v.reach,
+                                                 reinterpret_cast<long long*>(rho));
+  k_plan<<<1, kPlanThreads, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.hdr, advance_step);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- density
+__global__ void k_density(const int32_t* __restrict__ hist, int n_x, int n_M, long long* __restrict__ rho) {
+  const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_x) return;
+  const int32_t* row = hist + (size_t)warp * n_M;
+  long long sn = 0;
+  for (int k = lane; k < n_M; k += 32) sn += row[k];
+#pragma unroll
+  for (int off = 16; off; off >>= 1) sn += __shfl_down_sync(0xffffffffu, sn, off);
+  if (lane == 0) rho[warp] = sn;
+}
+
+cudaError_t launch_density(const wmc_params& p, const int32_t* hist, int64_t* rho, cudaStream_t s) {
+  const int blocks = (p.n_x + 7) / 8;
+  k_density<<<blocks, 256, 0, s>>>(hist, p.n_x, p.n_M, reinterpret_cast<long long*>(rho));
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Philox check
+__global__ void k_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1, long long n, uint4* __restrict__ out) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    out[q] = philox4x32_10(ctr[q], k0, k1);
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, long long n, uint32_t* out,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = (n + 255) / 256;
+  k_philox<<<(unsigned)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(reinterpret_cast<const uint4*>(ctr), k0, k1,
+                                                                      n, reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace wmc

@@ -1,0 +1,248 @@
+"""Thin Python binding of libwmc (include/wmc.h): argument marshalling only.
+
+Every function here has the name of the C entry point without the ``wmc_``
+prefix, takes torch CUDA tensors for device buffers and passes their data
+pointers, with the current torch stream, to the library.  All the work runs in
+libwmc's kernels; if the library is missing this module raises at import of
+the first call, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libwmc.so")
+
+FP32, BF16, FP16, FP16_SPLIT, TF32X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp16": FP16, "fp16_split": FP16_SPLIT, "tf32x3": TF32X3}
+
+FLAG_RATE, FLAG_CAPACITY, FLAG_TIMEOUT = 1, 2, 4
+STATUS = {0: "ok", 1: "invalid argument", 2: "capacity exceeded", 3: "gamma dt >= 1", 4: "CUDA error",
+          5: "device wait timed out", 6: "unsupported"}
+
+# Every entry point include/wmc.h declares (checked by the tests).
+EXPORTS = (
+    "wmc_version", "wmc_status_string", "wmc_workspace_size", "wmc_init", "wmc_reset_counters",
+    "wmc_get_counters", "wmc_kernel_eval", "wmc_kernel_cdf", "wmc_annihilate", "wmc_kernel_eval_occupied",
+    "wmc_kernel_table_occupied", "wmc_step", "wmc_run", "wmc_density", "wmc_materialize", "wmc_philox4x32_10",
+)
+
+
+class WmcError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """wmc_params (include/wmc.h)."""
+
+    _fields_ = [
+        ("dx_m", ctypes.c_double),
+        ("mass_kg", ctypes.c_double),
+        ("dt_s", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("n_x", ctypes.c_int32),
+        ("Q", ctypes.c_int32),
+        ("n_M", ctypes.c_int32),
+        ("bc_potential", ctypes.c_int32),
+        ("child_wrap", ctypes.c_int32),
+        ("sim", ctypes.c_uint32),
+    ]
+
+    @classmethod
+    def of(cls, obj, **override) -> "Params":
+        """From any object (or dict) with the same attribute names."""
+        get = (lambda k: obj[k]) if isinstance(obj, dict) else (lambda k: getattr(obj, k))
+        vals = {}
+        for name, _ in cls._fields_:
+            vals[name] = override[name] if name in override else get(name)
+        return cls(**vals)
+
+    @property
+    def h(self) -> int:
+        return self.Q // 2
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [
+        ("population", ctypes.c_uint64),
+        ("particle_steps", ctypes.c_uint64),
+        ("pairs", ctypes.c_uint64),
+        ("absorbed", ctypes.c_uint64),
+        ("absorbed_signed", ctypes.c_int64),
+        ("dropped", ctypes.c_uint64),
+        ("dropped_signed", ctypes.c_int64),
+        ("n_occ", ctypes.c_int32),
+        ("n_items", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("step", ctypes.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Loads libwmc.so (built by ``paper_1806_00082_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libwmc is not built ({p} missing): run paper_1806_00082_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        vp, i32, u32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64
+        pp = ctypes.POINTER(Params)
+        sig = {
+            "wmc_version": ([], ctypes.c_char_p),
+            "wmc_status_string": ([i32], ctypes.c_char_p),
+            "wmc_workspace_size": ([pp], ctypes.c_size_t),
+            "wmc_init": ([pp, vp, ctypes.c_size_t, vp], i32),
+            "wmc_reset_counters": ([pp, vp, vp], i32),
+            "wmc_get_counters": ([pp, vp, ctypes.POINTER(Counters), vp], i32),
+            "wmc_kernel_eval": ([pp, vp, vp, i32, i32, vp, vp, vp], i32),
+            "wmc_kernel_cdf": ([pp, vp, i32, vp, vp, vp, vp], i32),
+            "wmc_annihilate": ([pp, vp, vp, vp, vp], i32),
+            "wmc_kernel_eval_occupied": ([pp, vp, i32, vp, vp], i32),
+            "wmc_kernel_table_occupied": ([pp, vp, vp, vp], i32),
+            "wmc_step": ([pp, vp, u32, vp, vp, vp], i32),
+            "wmc_run": ([pp, vp, vp, vp, u32, i32, i32, i32, vp, vp], i32),
+            "wmc_density": ([pp, vp, vp, vp], i32),
+            "wmc_materialize": ([pp, vp, u32, vp, vp, vp, vp, i64, vp, vp], i32),
+            "wmc_philox4x32_10": ([vp, u32, u32, i64, vp, vp], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libwmc device arguments must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("libwmc device arguments must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(name: str, code: int):
+    if code != 0:
+        raise WmcError(name, code)
+
+
+def version() -> str:
+    return load().wmc_version().decode()
+
+
+def workspace_size(p: Params) -> int:
+    return load().wmc_workspace_size(ctypes.byref(p))
+
+
+def workspace(p: Params, device=None) -> torch.Tensor:
+    n = workspace_size(p)
+    if n == 0:
+        raise WmcError("wmc_workspace_size", 1)
+    return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
+def init(p: Params, ws: torch.Tensor) -> None:
+    _check("wmc_init", load().wmc_init(ctypes.byref(p), _ptr(ws), ws.numel(), _stream()))
+
+
+def reset_counters(p: Params, ws: torch.Tensor) -> None:
+    _check("wmc_reset_counters", load().wmc_reset_counters(ctypes.byref(p), _ptr(ws), _stream()))
+
+
+def get_counters(p: Params, ws: torch.Tensor) -> dict:
+    c = Counters()
+    _check("wmc_get_counters", load().wmc_get_counters(ctypes.byref(p), _ptr(ws), ctypes.byref(c), _stream()))
+    return c.as_dict()
+
+
+def kernel_eval(p: Params, V: torch.Tensor, occ: torch.Tensor, ws: torch.Tensor, prec: int = FP32,
+                out: torch.Tensor | None = None) -> torch.Tensor:
+    n = occ.numel()
+    if out is None:
+        out = torch.empty((n, p.h), dtype=torch.float32, device=V.device)
+    _check("wmc_kernel_eval", load().wmc_kernel_eval(ctypes.byref(p), _ptr(V), _ptr(occ), n, prec, _ptr(out),
+                                                     _ptr(ws), _stream()))
+    return out
+
+
+def kernel_cdf(p: Params, VWh: torch.Tensor, ws: torch.Tensor | None = None, with_cdf: bool = True):
+    n = VWh.shape[0]
+    cdf = torch.empty((n, p.n_M), dtype=torch.float64, device=VWh.device) if with_cdf else None
+    gamma = torch.empty(n, dtype=torch.float64, device=VWh.device)
+    _check("wmc_kernel_cdf", load().wmc_kernel_cdf(ctypes.byref(p), _ptr(VWh), n, _ptr(cdf), _ptr(gamma),
+                                                   _ptr(ws), _stream()))
+    return cdf, gamma
+
+
+def annihilate(p: Params, hist: torch.Tensor, ws: torch.Tensor, rho: torch.Tensor | None = None):
+    _check("wmc_annihilate", load().wmc_annihilate(ctypes.byref(p), _ptr(hist), _ptr(rho), _ptr(ws), _stream()))
+    return rho
+
+
+def kernel_eval_occupied(p: Params, V: torch.Tensor, ws: torch.Tensor, prec: int = FP32) -> None:
+    _check("wmc_kernel_eval_occupied",
+           load().wmc_kernel_eval_occupied(ctypes.byref(p), _ptr(V), prec, _ptr(ws), _stream()))
+
+
+def kernel_table_occupied(p: Params, table: torch.Tensor, ws: torch.Tensor) -> None:
+    _check("wmc_kernel_table_occupied",
+           load().wmc_kernel_table_occupied(ctypes.byref(p), _ptr(table), _ptr(ws), _stream()))
+
+
+def step(p: Params, hist_in: torch.Tensor, t: int, hist_out: torch.Tensor, ws: torch.Tensor) -> None:
+    _check("wmc_step", load().wmc_step(ctypes.byref(p), _ptr(hist_in), t, _ptr(hist_out), _ptr(ws), _stream()))
+
+
+def run(p: Params, V: torch.Tensor, hist_a: torch.Tensor, hist_b: torch.Tensor, t_first: int, n_steps: int,
+        ws: torch.Tensor, prec: int = FP32, use_graph: bool = True) -> None:
+    _check("wmc_run", load().wmc_run(ctypes.byref(p), _ptr(V), _ptr(hist_a), _ptr(hist_b), t_first, n_steps, prec,
+                                     1 if use_graph else 0, _ptr(ws), _stream()))
+
+
+def density(p: Params, hist: torch.Tensor, rho: torch.Tensor | None = None) -> torch.Tensor:
+    if rho is None:
+        rho = torch.empty(p.n_x, dtype=torch.int64, device=hist.device)
+    _check("wmc_density", load().wmc_density(ctypes.byref(p), _ptr(hist), _ptr(rho), _stream()))
+    return rho
+
+
+def materialize(p: Params, hist: torch.Tensor, t: int, ws: torch.Tensor, capacity: int):
+    dev = hist.device
+    cell = torch.empty(capacity, dtype=torch.int32, device=dev)
+    f = torch.empty(capacity, dtype=torch.float32, device=dev)
+    M = torch.empty(capacity, dtype=torch.int16, device=dev)
+    s = torch.empty(capacity, dtype=torch.int8, device=dev)
+    _check("wmc_materialize", load().wmc_materialize(ctypes.byref(p), _ptr(hist), t, _ptr(cell), _ptr(f), _ptr(M),
+                                                     _ptr(s), capacity, _ptr(ws), _stream()))
+    return cell, f, M, s
+
+
+def philox4x32_10(ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
+    """ctr: uint32-valued int32/int64 CUDA tensor [n, 4] (viewed as 32-bit words)."""
+    c = ctr.to(torch.int32).contiguous()
+    out = torch.empty_like(c)
+    _check("wmc_philox4x32_10", load().wmc_philox4x32_10(_ptr(c), key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF,
+                                                         c.shape[0], _ptr(out), _stream()))
+    return out

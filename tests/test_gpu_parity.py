@@ -1,0 +1,302 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: bit-exact for Philox words, CDFs built from the same FP32 kernel values,
+histograms, counters and survivors (same kernel table, same Philox streams);
+kernel values within 1e-6 normwise of the FP64 oracle (FP32 form); densities of
+the full production loop (FP32 kernel in the loop) within 1e-3 L1 of the
+oracle's FP64 run under common random numbers.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import wmc_inputs as wi
+from tests._util import gpu_run, gpu_run_table, normwise, oracle_tables
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KERNEL_TOL = 1e-6       # normwise, FP32 form vs FP64 oracle
+DENSITY_L1_TOL = 1e-3   # sum_i |rho_gpu - rho_oracle| / N0
+
+
+@pytest.fixture(scope="module")
+def wmc():
+    from paper_1806_00082_gb300 import build, wmc as w
+    build.build()
+    w.load()
+    return w
+
+
+# --------------------------------------------------------------------------- Philox
+def test_philox_matches_oracle(wmc):
+    rng = np.random.default_rng(0)
+    n = 100_000
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = (0x9E3779B9, 0xDEADBEEF)
+    out = wmc.philox4x32_10(torch.from_numpy(ctr.view(np.int32)).cuda(), *key).cpu().numpy().view(np.uint32)
+    for q in list(range(0, n, 997)) + [n - 1]:
+        assert out[q].tolist() == oracle.philox(ctr[q], key).tolist()
+    # published known-answer vector
+    z = wmc.philox4x32_10(torch.zeros((1, 4), dtype=torch.int32, device="cuda"), 0, 0).cpu().numpy().view(np.uint32)
+    assert z[0].tolist() == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+
+
+# --------------------------------------------------------------------------- kernel
+def _half_from_full(w, full64):
+    h = w.Q // 2
+    return full64[:, w.n_M // 2: w.n_M // 2 + h] if w.n_M >= w.Q else None
+
+
+@pytest.mark.parametrize("wl", [wi.BARRIER_100, wi.BARRIER_2000])
+def test_kernel_eval_fp32_all_cells(wmc, wl):
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    occ = torch.arange(wl.n_x, dtype=torch.int32, device="cuda")
+    got = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), occ, ws).cpu().numpy()
+    ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, np.arange(wl.n_x))[:, wl.Q // 2:]
+    assert got.shape == ref.shape
+    assert normwise(got, ref) <= KERNEL_TOL
+    assert np.all(got[:, 0] == 0)
+
+
+def test_kernel_eval_fp32_double_barrier_sampled(wmc):
+    """Q = 1024 (8 column tiles, a 511-term contraction): a ragged set of 333
+    cells spread over the barrier region and the edges, with repeats."""
+    wl = wi.DOUBLE_BARRIER_16384
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    rng = np.random.default_rng(7)
+    cells = np.concatenate([rng.integers(8192 - 700, 8192 + 700, 300), [0, 1, 511, 512, 16383, 16382],
+                            rng.integers(0, wl.n_x, 24), [8192, 8192, 8192]]).astype(np.int32)
+    assert cells.size == 333
+    got = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), torch.from_numpy(cells).cuda(), ws).cpu().numpy()
+    ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, cells)[:, wl.Q // 2:]
+    e = normwise(got, ref)
+    assert e <= KERNEL_TOL, e
+    big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+    rel = np.abs(got[big] - ref[big]) / np.abs(ref[big])
+    assert np.median(rel) < 1e-6
+
+
+@pytest.mark.parametrize("n_occ", [0, 1, 63, 64, 65, 130])
+def test_kernel_eval_ragged_and_empty(wmc, n_occ):
+    wl = wi.BARRIER_2000
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    cells = (np.arange(n_occ) * 7 + 950) % wl.n_x
+    out = torch.full((n_occ, wl.Q // 2), 7.0, device="cuda")
+    wmc.kernel_eval(p, torch.from_numpy(V).cuda(), torch.from_numpy(cells.astype(np.int32)).cuda(), ws, out=out)
+    got = out.cpu().numpy()
+    if n_occ:
+        ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, cells)[:, wl.Q // 2:]
+        assert normwise(got, ref) <= KERNEL_TOL
+
+
+def test_kernel_eval_clamp_boundary(wmc):
+    """bc 1 (edge value outside the domain) on a rough potential."""
+    wl = wi.BARRIER_100.replace(bc_potential=1)
+    p = wmc.Params.of(wl)
+    V = np.random.default_rng(3).uniform(-0.2, 0.3, wl.n_x).astype(np.float32)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    occ = torch.arange(wl.n_x, dtype=torch.int32, device="cuda")
+    got = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), occ, ws).cpu().numpy()
+    ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, np.arange(wl.n_x))[:, wl.Q // 2:]
+    assert normwise(got, ref) <= KERNEL_TOL
+
+
+@pytest.mark.parametrize("wl", [wi.BARRIER_100, wi.BARRIER_2000, wi.DOUBLE_BARRIER_16384])
+def test_cdf_bit_exact_on_same_kernel_values(wmc, wl):
+    """gamma and the CDF from identical FP32 kernel values are identical."""
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    rows = np.arange(wl.n_x) if wl.n_x <= 2000 else np.arange(8192 - 160, 8192 + 160)
+    po = oracle.params(wl)
+    full = oracle.kernel_rows(po, V, rows).astype(np.float32)
+    half = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, rows)[:, wl.Q // 2:].astype(np.float32)
+    cdf, gamma = wmc.kernel_cdf(p, torch.from_numpy(np.ascontiguousarray(half)).cuda())
+    cdf, gamma = cdf.cpu().numpy(), gamma.cpu().numpy()
+    for r in range(rows.size):
+        c_ref, g_ref = oracle.cdf_row(full[r].astype(np.float64))
+        assert np.array_equal(cdf[r], c_ref)
+        assert gamma[r] == g_ref
+
+
+# --------------------------------------------------------------------------- steps, bit-exact
+def _compare_steps(wmc, wl, hist0, t_first, n_steps, V=None):
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl) if V is None else V
+    full, half = oracle_tables(wl, V)
+    ref, st = oracle.simulate(oracle.params(wl), hist0, t_first, n_steps, table=full)
+    got, c = gpu_run_table(wmc, torch, p, half, hist0, t_first, n_steps)
+    np.testing.assert_array_equal(got, ref)
+    assert c["pairs"] == st[oracle.ST_PAIRS]
+    assert c["absorbed"] == st[oracle.ST_ABSORBED]
+    assert c["absorbed_signed"] == st[oracle.ST_ABSORBED_SIGNED]
+    assert c["dropped"] == st[oracle.ST_DROPPED]
+    assert c["dropped_signed"] == st[oracle.ST_DROPPED_SIGNED]
+    assert c["particle_steps"] == st[oracle.ST_PARTICLE_STEPS]
+    return got, c, st
+
+
+def test_steps_bit_exact_barrier_100_all_steps(wmc):
+    """1e5 particles, 100 steps: every histogram count and counter identical."""
+    wl = wi.BARRIER_100
+    _, c, st = _compare_steps(wmc, wl, wi.initial_histogram(wl), 1, wl.steps)
+    assert st[oracle.ST_PAIRS] > 10000 and st[oracle.ST_DROPPED] > 1000
+
+
+def test_steps_bit_exact_packet_on_barrier(wmc):
+    """Packet centred on the barrier: pairs at the maximal rate, annihilation busy."""
+    wl = wi.BARRIER_100.replace(packet=wi.Packet(50e-9, 6e-9, 0.1, 200_000))
+    _, c, st = _compare_steps(wmc, wl, wi.initial_histogram(wl), 5, 20)
+    assert st[oracle.ST_PAIRS] > 50000
+
+
+def test_steps_bit_exact_wrap_and_clamp(wmc):
+    wl = wi.BARRIER_100.replace(child_wrap=1, bc_potential=1, sim=7, seed=123456789012345,
+                                packet=wi.Packet(45e-9, 6e-9, 0.12, 50_000))
+    _, c, st = _compare_steps(wmc, wl, wi.initial_histogram(wl), 1, 10)
+    assert st[oracle.ST_DROPPED] == 0 and st[oracle.ST_PAIRS] > 1000
+
+
+def test_steps_bit_exact_signed_random_and_edges(wmc):
+    """Random signed counts in every bucket, including the edge cells (absorption)."""
+    wl = wi.BARRIER_100
+    h0 = wi.random_histogram(wl, 300_000, seed=9)
+    _, c, st = _compare_steps(wmc, wl, h0, 3, 4)
+    assert st[oracle.ST_ABSORBED] > 0
+
+
+def test_steps_empty_and_single(wmc):
+    wl = wi.BARRIER_100
+    _compare_steps(wmc, wl, np.zeros((wl.n_x, wl.n_M), np.int32), 1, 2)
+    h = np.zeros((wl.n_x, wl.n_M), np.int32)
+    h[49, 40] = -1
+    _compare_steps(wmc, wl, h, 1, 5)
+    h = np.zeros((wl.n_x, wl.n_M), np.int32)
+    h[0, 0] = 5000       # fastest leftward momentum at the left edge
+    h[99, 63] = -5000    # fastest rightward momentum at the right edge
+    _compare_steps(wmc, wl, h, 1, 3)
+
+
+def test_steps_bit_exact_large_buckets(wmc):
+    """Cells with more particles than one work item (4096): items split a cell."""
+    wl = wi.BARRIER_100
+    h = np.zeros((wl.n_x, wl.n_M), np.int32)
+    h[44, 30:36] = 3000
+    h[45, 33] = -20000
+    h[46, 60] = 9000
+    _compare_steps(wmc, wl, h, 2, 3)
+
+
+def test_steps_bit_exact_barrier_2000_full_size(wmc):
+    """The 2000-cell, 1e7-particle workload at full size, 2 steps."""
+    wl = wi.BARRIER_2000
+    _compare_steps(wmc, wl, wi.initial_histogram(wl), 1, 2)
+
+
+def test_steps_bit_exact_double_barrier_near(wmc):
+    """Q = n_M = 1024 with the noisy double barrier: a packet next to it."""
+    wl = wi.DOUBLE_BARRIER_16384.replace(packet=wi.Packet(8192 * 0.1e-9 - 30e-9, 5e-9, 0.1, 100_000))
+    V = wi.potential(wl)
+    # kernel table only where particles can go (rows far away are never read)
+    full = np.zeros((wl.n_x, wl.n_M), np.float32)
+    half = np.zeros((wl.n_x, wl.Q // 2), np.float32)
+    rows = np.arange(8192 - 600, 8192 + 200)
+    full[rows] = oracle.kernel_rows(oracle.params(wl), V, rows).astype(np.float32)
+    half[rows] = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, rows)[:, wl.Q // 2:].astype(np.float32)
+    h0 = wi.initial_histogram(wl)
+    assert np.all(np.abs(h0).sum(axis=1)[:8192 - 590] == 0) and np.all(np.abs(h0).sum(axis=1)[8192 + 190:] == 0)
+    ref, st = oracle.simulate(oracle.params(wl), h0, 1, 3, table=full)
+    got, c = gpu_run_table(wmc, torch, wmc.Params.of(wl), half, h0, 1, 3)
+    np.testing.assert_array_equal(got, ref)
+    assert c["pairs"] == st[oracle.ST_PAIRS] > 1000
+
+
+# --------------------------------------------------------------------------- production loop
+def test_production_loop_density_barrier_100(wmc):
+    """wmc_run (FP32 kernel in the loop, CUDA graph) vs the oracle's FP64 run:
+    same seeds and counters, so densities agree within 1e-3 L1."""
+    wl = wi.BARRIER_100
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    h0 = wi.initial_histogram(wl)
+    ref, st = oracle.simulate(oracle.params(wl), h0, 1, wl.steps, V=V)
+    got, c = gpu_run(wmc, torch, p, V, h0, 1, wl.steps, use_graph=True)
+    rho_g, rho_o = got.sum(axis=1), ref.sum(axis=1)
+    l1 = np.abs(rho_g - rho_o).sum() / wl.packet.n0
+    assert l1 <= DENSITY_L1_TOL, l1
+    assert c["flags"] == 0
+    assert abs(int(c["pairs"]) - int(st[oracle.ST_PAIRS])) <= 0.01 * st[oracle.ST_PAIRS]
+    # graph and direct launches give the same bits
+    got2, _ = gpu_run(wmc, torch, p, V, h0, 1, wl.steps, use_graph=False)
+    np.testing.assert_array_equal(got, got2)
+
+
+def test_production_loop_barrier_2000_matches_oracle(wmc):
+    """At the 2000-cell workload the packet is farther than L_C / 2 from the
+    barrier, so the occupied cells have a zero kernel in both precisions and the
+    production loop matches the oracle bit for bit."""
+    wl = wi.BARRIER_2000
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    h0 = wi.initial_histogram(wl)
+    ref, st = oracle.simulate(oracle.params(wl), h0, 1, 3, V=V)
+    got, c = gpu_run(wmc, torch, p, V, h0, 1, 3)
+    np.testing.assert_array_equal(got, ref)
+    assert c["particle_steps"] == st[oracle.ST_PARTICLE_STEPS]
+
+
+def test_odd_step_count_and_continuation(wmc):
+    """7 steps in one call equal 3 + 4 steps (state and Philox counters resume)."""
+    wl = wi.BARRIER_100.replace(packet=wi.Packet(45e-9, 5e-9, 0.1, 50_000))
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    h0 = wi.initial_histogram(wl)
+    a, _ = gpu_run(wmc, torch, p, V, h0, 1, 7)
+    b1, _ = gpu_run(wmc, torch, p, V, h0, 1, 3)
+    b2, _ = gpu_run(wmc, torch, p, V, b1, 4, 4)
+    np.testing.assert_array_equal(a, b2)
+
+
+# --------------------------------------------------------------------------- rebuild, density, flags
+def test_materialize_matches_oracle(wmc):
+    wl = wi.BARRIER_100
+    p = wmc.Params.of(wl)
+    h = wi.random_histogram(wl, 40_000, seed=12)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    hd = torch.from_numpy(h).cuda()
+    rho = torch.empty(wl.n_x, dtype=torch.int64, device="cuda")
+    wmc.annihilate(p, hd, ws, rho=rho)
+    P = int(np.abs(h).sum())
+    cell, f, M, s = (x.cpu().numpy() for x in wmc.materialize(p, hd, 17, ws, P))
+    rc, rf, rM, rs = oracle.materialize(oracle.params(wl), h, 17)
+    np.testing.assert_array_equal(cell, rc)
+    np.testing.assert_array_equal(f, rf)
+    np.testing.assert_array_equal(M, rM)
+    np.testing.assert_array_equal(s, rs)
+    np.testing.assert_array_equal(rho.cpu().numpy(), oracle.density(oracle.params(wl), h))
+    np.testing.assert_array_equal(wmc.density(p, hd).cpu().numpy(), h.sum(axis=1))
+    assert wmc.get_counters(p, ws)["population"] == P
+    # too small a capacity: nothing written, flag set
+    wmc.materialize(p, hd, 17, ws, P - 1)
+    assert wmc.get_counters(p, ws)["flags"] & wmc.FLAG_CAPACITY
+
+
+def test_rate_flag(wmc):
+    """gamma dt >= 1 is flagged, never clamped silently."""
+    wl = wi.BARRIER_100.replace(dt_s=2e-15)
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl) * 50
+    h0 = wi.initial_histogram(wl.replace(packet=wi.Packet(50e-9, 3e-9, 0.1, 1000)))
+    _, c = gpu_run(wmc, torch, p, V, h0, 1, 1)
+    assert c["flags"] & wmc.FLAG_RATE
