@@ -147,6 +147,25 @@ wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* o
 wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
                            wmc_precision prec, float* VWh, void* ws, wmc_stream_t stream);
 
+/* Same evaluation as wmc_kernel_eval for callers that cannot allocate device
+ * memory or pass a workspace (the paper has no counterpart: this serves
+ * embedding).  Such callers are, for example, code inside an application whose
+ * device memory belongs to a pool allocator (a cudaMalloc there may fail,
+ * stall, synchronise the device or go unaccounted), or applications that
+ * allocate everything at start-up and forbid it afterwards.  The only scratch
+ * of the evaluation, the sine matrix, lives in a fixed 1 MiB array in the
+ * library's device memory, which every GPU that loads the library holds until
+ * the process exits; no call allocates.
+ *   Limit: Q <= 1024, else WMC_ERR_CAPACITY (nothing is launched).
+ *   V, occ, n_occ, VWh as for wmc_kernel_eval (FP32 form).
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.  All calls share the array and each refills what it reads, so
+ *   calls that overlap on the GPU (other streams, other threads) race on it:
+ *   serialise them. */
+wmc_status wmc_kernel_eval_noalloc(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
+                                   float* VWh, wmc_stream_t stream);
+
 /* gamma and the momentum CDF of kernel rows -- Eq. (momentum_integral): for each
  * row, cdf[row][k] = sum_{k' <= k} max(V_W(k'), 0) in FP64, summed in ascending
  * k, and gamma[row] = cdf[row][n_M - 1].

@@ -29,6 +29,7 @@ EXPORTS = (
     "wmc_version", "wmc_status_string", "wmc_workspace_size", "wmc_init", "wmc_reset_counters",
     "wmc_get_counters", "wmc_kernel_eval", "wmc_kernel_cdf", "wmc_annihilate", "wmc_kernel_eval_occupied",
     "wmc_kernel_table_occupied", "wmc_step", "wmc_run", "wmc_density", "wmc_materialize", "wmc_philox4x32_10",
+    "wmc_kernel_eval_noalloc",
 )
 
 
@@ -120,6 +121,7 @@ def load(path: str | None = None):
             "wmc_density": ([pp, vp, vp, vp], i32),
             "wmc_materialize": ([pp, vp, u32, vp, vp, vp, vp, i64, vp, vp], i32),
             "wmc_philox4x32_10": ([vp, u32, u32, i64, vp, vp], i32),
+            "wmc_kernel_eval_noalloc": ([pp, vp, vp, i32, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -184,6 +186,14 @@ def kernel_eval(p: Params, V: torch.Tensor, occ: torch.Tensor, ws: torch.Tensor,
         out = torch.empty((n, p.h), dtype=torch.float32, device=V.device)
     _check("wmc_kernel_eval", load().wmc_kernel_eval(ctypes.byref(p), _ptr(V), _ptr(occ), n, prec, _ptr(out),
                                                      _ptr(ws), _stream()))
+    return out
+
+
+def kernel_eval_noalloc(p: Params, V: torch.Tensor, occ: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+    """wmc_kernel_eval_noalloc: no workspace, the library allocates nothing
+    (scratch in a fixed device array, Q <= 1024); out is [n_occ, Q/2] FP32."""
+    _check("wmc_kernel_eval_noalloc", load().wmc_kernel_eval_noalloc(ctypes.byref(p), _ptr(V), _ptr(occ),
+                                                                     occ.numel(), _ptr(out), _stream()))
     return out
 
 
