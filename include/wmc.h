@@ -28,21 +28,23 @@
  * Ensemble: the state is the net signed histogram hist[i][k] (int32,
  * row-major [n_x][n_M]) left by annihilation (rule 2: opposite signs in one
  * (cell, M) cancel).  Its survivors are numbered row-major over (i, k); the
- * particle with number id sits in cell i at offset f = u24(Philox(id, t-1,
- * REPOS, sim).w0) in [0, 1), where t-1 is the step that rebuilt it.
+ * particle with number id sits in cell i at a uniform offset f in [0, 1) drawn
+ * at step t-1, the step that rebuilt it (see Random numbers below).
  * Step t (postulate, Sec. 2.1): every particle drifts, f' = fl32(f + D[M]) with
  * D[M] = fl32(M hbar pi dt / (m Q dx^2)) cells, and moves to the next or
  * previous cell when f' >= 1 or f' < 0 (leaving [0, n_x) absorbs it); in its new
  * cell c it creates a pair with probability gamma(c) dt, gamma = sum_M V_W^+
- * (Eq. momentum_integral), drawn as u53(w0, w1) < gamma dt from
- * Philox(id, t, GEN, sim); the pair sits in c with signs +s, -s and momenta
- * M + M', M - M', M' drawn from V_W^+(c; .) / gamma(c) as the smallest k with
- * CDF[k] > u53(w2, w3) gamma; children outside the momentum grid are dropped
- * (or wrapped).  Counts of parents and children in each (cell, M) are summed
- * with their signs: that sum is the annihilated state of step t.
- * Philox4x32-10 (Salmon et al., SC'11), key (seed_lo, seed_hi), counter
- * (id, step, purpose, sim); u24(w) = (w >> 8) 2^-24;
- * u53(a, b) = ((a >> 5) 2^26 + (b >> 6)) 2^-53.
+ * (Eq. momentum_integral), drawn as w 2^-32 < gamma dt; the pair sits in c with
+ * signs +s, -s and momenta M + M', M - M', M' drawn from V_W^+(c; .) / gamma(c)
+ * through the fixed-point CDF of wmc_kernel_cdf; children outside the momentum
+ * grid are dropped (or wrapped).  Counts of parents and children in each
+ * (cell, M) are summed with their signs: that sum is the annihilated state of
+ * step t.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key (seed_lo, seed_hi).
+ * Particle id takes word id % 4 of counter (id / 4, step, purpose, sim): the
+ * offset with purpose REPOS = 2, u24(w) = (w >> 8) 2^-24, at the step that
+ * rebuilt it; the pair-creation word with purpose GEN = 1 at step t.  A created
+ * pair draws U2 = (w0 >> 5) 2^26 + (w1 >> 6) from counter (id, t, PICK = 3, sim).
  */
 #ifndef WMC_H_
 #define WMC_H_
@@ -166,14 +168,23 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
 wmc_status wmc_kernel_eval_noalloc(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
                                    float* VWh, wmc_stream_t stream);
 
-/* gamma and the momentum CDF of kernel rows -- Eq. (momentum_integral): for each
- * row, cdf[row][k] = sum_{k' <= k} max(V_W(k'), 0) in FP64, summed in ascending
- * k, and gamma[row] = cdf[row][n_M - 1].
+/* gamma and the momentum CDF of kernel rows -- Eq. (momentum_integral) and the
+ * postulate's draw of p' with probability V_W^+ / gamma.  The positive parts
+ * x_k = max(V_W(k), 0) of a row are quantised relative to the row maximum:
+ *   e = floor(log2 max_k x_k),  s = 61 - ceil(log2 n_M) - e,
+ *   q_k = x_k 2^s rounded to the nearest integer (ties to even),
+ * so that the CDF is the exact integer running sum
+ *   cdf[row][k] = sum_{k' <= k} q_k'  (< 2^62)
+ * and gamma[row] = fl64(cdf[row][n_M - 1] 2^-s) (resolution 2^-52 of the row
+ * maximum, like an FP64 sum, but exact and independent of summation order).
+ * p' takes the smallest k with cdf[k] > floor(U2 cdf[n_M-1] / 2^53) for a
+ * 53-bit uniform integer U2.  A row without positive entries has gamma = 0.
  *   VWh   [dev] float[n_rows][Q/2].
- *   cdf   [dev] double[n_rows][n_M] (row-major) or NULL.
- *   gamma [dev] double[n_rows]. */
-wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows, double* cdf,
-                          double* gamma, void* ws, wmc_stream_t stream);
+ *   cdf   [dev] int64[n_rows][n_M] (row-major) or NULL.
+ *   gamma [dev] double[n_rows].
+ *   scale [dev] int32[n_rows] (receives s) or NULL. */
+wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows, int64_t* cdf, double* gamma,
+                          int32_t* scale, wmc_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * The simulation step, as three stream-ordered calls on one workspace:
@@ -222,7 +233,7 @@ wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t
 wmc_status wmc_density(const wmc_params* p, const int32_t* hist, int64_t* rho, wmc_stream_t stream);
 
 /* Explicit survivors of the last wmc_annihilate, as rebuilt at step t (the
- * offset of id is u24(Philox(id, t, REPOS, sim).w0)): SoA arrays [dev] of
+ * offset of id is u24 of word id % 4 of Philox(id / 4, t, REPOS, sim)): SoA arrays [dev] of
  * capacity elements, written in id order.  If the population exceeds capacity
  * nothing is written and WMC_FLAG_CAPACITY is set. */
 wmc_status wmc_materialize(const wmc_params* p, const int32_t* hist, uint32_t t, int32_t* cell, float* f,

@@ -9,8 +9,9 @@ Functions and the passages they follow:
 
 - :func:`kernel_rows` -- Eq. (wigner-1d-discrete): the finite-window discrete
   Wigner kernel, summed over m = -h..h (h = L_C / (2 dx)) in FP64.
-- :func:`cdf_row` -- Eq. (momentum_integral): gamma as the sum of V_W^+ over M,
-  built as the running sum that also serves as the CDF for drawing p'.
+- :func:`cdf_row` -- Eq. (momentum_integral): gamma as the sum of V_W^+ over M
+  and the CDF for drawing p' ~ V_W^+ / gamma, as exact sums of V_W^+ quantised
+  to 62-bit fixed point relative to the row maximum.
 - :func:`philox` -- Philox4x32-10 from Salmon et al., SC'11.
 - :func:`materialize` -- rule 2 survivors re-emitted in (cell, M) order.
 - :func:`simulate` -- the postulate of Sec. 2.1 (free drift, pair creation with
@@ -89,15 +90,19 @@ def _load():
         lib.wmco_u53.restype = ctypes.c_double
         lib.wmco_u24.argtypes = [ctypes.c_uint32]
         lib.wmco_u24.restype = ctypes.c_float
+        lib.wmco_u32.argtypes = [ctypes.c_uint32]
+        lib.wmco_u32.restype = ctypes.c_double
         lib.wmco_sine.argtypes = [ctypes.c_int32, ctypes.c_int64]
         lib.wmco_sine.restype = ctypes.c_double
         lib.wmco_kernel_value.argtypes = [pp, f64p, ctypes.c_int32, ctypes.c_int32]
         lib.wmco_kernel_value.restype = ctypes.c_double
         lib.wmco_kernel_rows.argtypes = [pp, f64p, ctypes.c_int32, i32p, f64p]
-        lib.wmco_cdf_row.argtypes = [ctypes.c_int32, f64p, f64p]
+        lib.wmco_cdf_row.argtypes = [ctypes.c_int32, f64p, i64p, i32p]
         lib.wmco_cdf_row.restype = ctypes.c_double
-        lib.wmco_sample_row.argtypes = [ctypes.c_int32, f64p, f64p, ctypes.c_double]
+        lib.wmco_sample_row.argtypes = [ctypes.c_int32, i64p, ctypes.c_uint64]
         lib.wmco_sample_row.restype = ctypes.c_int32
+        lib.wmco_u53_bits.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        lib.wmco_u53_bits.restype = ctypes.c_uint64
         lib.wmco_drift_table.argtypes = [pp, f32p]
         lib.wmco_population.argtypes = [pp, i32p]
         lib.wmco_population.restype = ctypes.c_int64
@@ -133,6 +138,10 @@ def u24(a: int) -> float:
     return _load().wmco_u24(a)
 
 
+def u32(a: int) -> float:
+    return _load().wmco_u32(a)
+
+
 def sine(Q: int, t: int) -> float:
     """sin(2 pi t / Q) with exact integer reduction."""
     return _load().wmco_sine(Q, t)
@@ -153,18 +162,24 @@ def kernel_rows(p: Params, V: np.ndarray, rows) -> np.ndarray:
     return out
 
 
-def cdf_row(vw_row: np.ndarray):
-    """(cdf, gamma) of one kernel row."""
+def cdf_row(vw_row: np.ndarray, with_scale: bool = False):
+    """(cdf, gamma) of one kernel row: the exact running sum of V_W^+ quantised
+    to 62-bit fixed point (int64 array) and gamma; with_scale adds the scale s."""
     v = np.ascontiguousarray(vw_row, dtype=np.float64)
-    cdf = np.zeros_like(v)
-    g = _load().wmco_cdf_row(v.size, _ptr(v, ctypes.c_double), _ptr(cdf, ctypes.c_double))
-    return cdf, g
+    cdf = np.zeros(v.size, dtype=np.int64)
+    s = ctypes.c_int32(0)
+    g = _load().wmco_cdf_row(v.size, _ptr(v, ctypes.c_double), _ptr(cdf, ctypes.c_int64), ctypes.byref(s))
+    return (cdf, g, s.value) if with_scale else (cdf, g)
 
 
-def sample_row(vw_row: np.ndarray, cdf: np.ndarray, target: float) -> int:
-    v = np.ascontiguousarray(vw_row, dtype=np.float64)
-    c = np.ascontiguousarray(cdf, dtype=np.float64)
-    return _load().wmco_sample_row(v.size, _ptr(v, ctypes.c_double), _ptr(c, ctypes.c_double), target)
+def sample_row(cdf: np.ndarray, U2: int) -> int:
+    """Index of p' for the 53-bit uniform integer U2."""
+    c = np.ascontiguousarray(cdf, dtype=np.int64)
+    return _load().wmco_sample_row(c.size, _ptr(c, ctypes.c_int64), U2)
+
+
+def u53_bits(a: int, b: int) -> int:
+    return _load().wmco_u53_bits(a, b)
 
 
 def drift_table(p: Params) -> np.ndarray:

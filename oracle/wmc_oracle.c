@@ -11,9 +11,10 @@
  * Everything is FP64 unless the method fixes another precision:
  *   - Wigner kernel: the discrete finite-window sum of Eq. (wigner-1d-discrete),
  *     summed over m = -h..h in ascending order, h = floor(L_C / (2 dx)).
- *   - gamma(x) = sum over M of V_W^+(x; M) (Eq. momentum_integral), as the
- *     running (inclusive) sum over ascending M, which is also the CDF used to
- *     draw p' (postulate, Sec. 2.1).
+ *   - gamma(x) = sum over M of V_W^+(x; M) (Eq. momentum_integral), and the
+ *     CDF used to draw p' with probability V_W^+ / gamma (postulate, Sec. 2.1),
+ *     both as exact sums of V_W^+ quantised to 62-bit fixed point relative to
+ *     the row maximum (see wmco_cdf_row).
  *   - Particles follow the postulate of Sec. 2.1 (free drift, pair creation
  *     with probability gamma dt, children at p +- p') and rules 1 and 2
  *     (density from signed counts; annihilation of opposite signs in the same
@@ -27,8 +28,11 @@
  *   is f' = fl32(f + D[M]) on the within-cell offset f in [0, 1), with
  *   D[M] = fl32(M * hbar pi dt / (m Q dx^2)); after annihilation survivors are
  *   re-emitted row-major over (cell, M) with a fresh uniform offset; random
- *   numbers are Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
- *   counter (id, step, purpose, sim) and key (seed_lo, seed_hi).
+ *   numbers are Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with key
+ *   (seed_lo, seed_hi): particle id draws its offset from word id mod 4 of
+ *   counter (id / 4, step, REPOS, sim), its pair-creation uniform u1 from word
+ *   id mod 4 of (id / 4, step, GEN, sim) as a 32-bit fraction, and, only when
+ *   a pair is created, p' from u53 of words 0, 1 of (id, step, PICK, sim).
  *
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no FMA contraction, so the
  * FP32 drift is one rounded addition).
@@ -44,6 +48,7 @@
 
 #define WMCO_PURPOSE_GEN 1u
 #define WMCO_PURPOSE_REPOS 2u
+#define WMCO_PURPOSE_PICK 3u
 
 typedef struct {
   double dx_m;
@@ -93,8 +98,11 @@ double wmco_u53(uint32_t a, uint32_t b) {
 /* Uniform float in [0,1) on the 2^-24 grid from one word. */
 float wmco_u24(uint32_t a) { return (float)(a >> 8) * (1.0f / 16777216.0f); }
 
-static void draw(const wmco_params* p, uint32_t id, uint32_t step, uint32_t purpose, uint32_t out[4]) {
-  uint32_t ctr[4] = {id, step, purpose, p->sim};
+/* Uniform double in [0,1) on the 2^-32 grid from one word. */
+double wmco_u32(uint32_t a) { return (double)a * (1.0 / 4294967296.0); }
+
+static void draw(const wmco_params* p, uint32_t c0, uint32_t step, uint32_t purpose, uint32_t out[4]) {
+  uint32_t ctr[4] = {c0, step, purpose, p->sim};
   uint32_t key[2] = {(uint32_t)(p->seed & 0xffffffffu), (uint32_t)(p->seed >> 32)};
   wmco_philox4x32_10(ctr, key, out);
 }
@@ -147,26 +155,58 @@ void wmco_kernel_rows(const wmco_params* p, const double* V, int32_t n_rows, con
       out[(int64_t)r * p->n_M + k] = wmco_kernel_value(p, V, rows[r], k - p->n_M / 2);
 }
 
-/* Running sum of V_W^+ over ascending M: cdf[k] = sum_{k' <= k} max(V_W[k'], 0).
- * Returns gamma = cdf[n_M - 1] (Eq. momentum_integral). */
-double wmco_cdf_row(int32_t n_M, const double* vw, double* cdf) {
-  double s = 0.0;
-  for (int32_t k = 0; k < n_M; ++k) {
-    s = s + (vw[k] > 0.0 ? vw[k] : 0.0);
-    cdf[k] = s;
-  }
-  return s;
+/* Smallest L with 2^L >= n. */
+static int32_t ceil_log2(int32_t n) {
+  int32_t L = 0;
+  while ((1 << L) < n) ++L;
+  return L;
 }
 
-/* Index k of p' drawn from V_W^+ / gamma: the smallest k with cdf[k] > target;
- * if rounding leaves none, the largest k with V_W^+ > 0. */
-int32_t wmco_sample_row(int32_t n_M, const double* vw, const double* cdf, double target) {
+/* gamma and the momentum CDF of one kernel row (Eq. momentum_integral and the
+ * postulate's p' ~ V_W^+ / gamma).  The positive parts x_k = max(V_W[k], 0)
+ * are quantised to integers relative to the row maximum,
+ *   e = floor(log2(max_k x_k)),  s = 61 - ceil(log2(n_M)) - e,
+ *   q_k = x_k 2^s rounded to the nearest integer (ties to even),
+ * so that every q_k < 2^(62 - ceil(log2 n_M)) and their sum fits 62 bits; the
+ * CDF is the exact running sum cdf[k] = sum_{k' <= k} q_k', the row total is
+ * Qtot = cdf[n_M - 1], and gamma = fl64(Qtot 2^-s).  A row with no positive
+ * entry has gamma = 0 and a zero CDF.  *scale receives s.  Returns gamma. */
+double wmco_cdf_row(int32_t n_M, const double* vw, int64_t* cdf, int32_t* scale) {
+  double xmax = 0.0;
+  for (int32_t k = 0; k < n_M; ++k)
+    if (vw[k] > xmax) xmax = vw[k];
+  if (xmax == 0.0) {
+    for (int32_t k = 0; k < n_M; ++k) cdf[k] = 0;
+    if (scale) *scale = 0;
+    return 0.0;
+  }
+  int fe;
+  frexp(xmax, &fe);                 /* xmax = f 2^fe, f in [1/2, 1) */
+  const int32_t e = fe - 1;
+  const int32_t s = 61 - ceil_log2(n_M) - e;
+  int64_t run = 0;
+  for (int32_t k = 0; k < n_M; ++k) {
+    const double x = vw[k] > 0.0 ? vw[k] : 0.0;
+    run += (int64_t)rint(ldexp(x, s)); /* exact scaling, round half to even */
+    cdf[k] = run;
+  }
+  if (scale) *scale = s;
+  return ldexp((double)run, -s);
+}
+
+/* Index k of p' drawn from V_W^+ / gamma with the 53-bit uniform integer U2:
+ * target = floor(U2 Qtot / 2^53) < Qtot, and k is the smallest index with
+ * cdf[k] > target (it always exists). */
+int32_t wmco_sample_row(int32_t n_M, const int64_t* cdf, uint64_t U2) {
+  const unsigned __int128 prod = (unsigned __int128)U2 * (unsigned __int128)(uint64_t)cdf[n_M - 1];
+  const int64_t target = (int64_t)(prod >> 53);
   for (int32_t k = 0; k < n_M; ++k)
     if (cdf[k] > target) return k;
-  for (int32_t k = n_M - 1; k >= 0; --k)
-    if (vw[k] > 0.0) return k;
   return -1;
 }
+
+/* The 53-bit integer behind wmco_u53(a, b). */
+uint64_t wmco_u53_bits(uint32_t a, uint32_t b) { return ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6); }
 
 /* Drift per step in cells, D[M] = fl32(M * hbar pi dt / (m Q dx^2)). */
 void wmco_drift_table(const wmco_params* p, float* D) {
@@ -199,8 +239,8 @@ int64_t wmco_population(const wmco_params* p, const int32_t* hist) {
 }
 
 /* Survivors of a net signed histogram, in row-major (cell, M) order, each
- * with a fresh offset f = u24(Philox(id, step, REPOS, sim).w0).  Returns the
- * count written, or -1 if it exceeds capacity or 2^32. */
+ * with a fresh offset f = u24(word id mod 4 of Philox(id / 4, step, REPOS, sim)).
+ * Returns the count written, or -1 if it exceeds capacity or 2^32. */
 int64_t wmco_materialize(const wmco_params* p, const int32_t* hist, uint32_t step, int64_t capacity,
                          int32_t* cell, float* f, int16_t* M, int8_t* s) {
   int64_t id = 0;
@@ -211,9 +251,9 @@ int64_t wmco_materialize(const wmco_params* p, const int32_t* hist, uint32_t ste
       for (int32_t c = 0; c < a; ++c) {
         if (id >= capacity || id >= ((int64_t)1 << 32)) return -1;
         uint32_t w[4];
-        draw(p, (uint32_t)id, step, WMCO_PURPOSE_REPOS, w);
+        draw(p, (uint32_t)(id >> 2), step, WMCO_PURPOSE_REPOS, w);
         cell[id] = i;
-        f[id] = wmco_u24(w[0]);
+        f[id] = wmco_u24(w[id & 3]);
         M[id] = (int16_t)(k - p->n_M / 2);
         s[id] = (int8_t)(n > 0 ? 1 : -1);
         ++id;
@@ -267,7 +307,7 @@ int32_t wmco_simulate(const wmco_params* p, const double* V, const float* table,
   int64_t* acc = (int64_t*)malloc(sizeof(int64_t) * G);
   memcpy(cur, hist, sizeof(int32_t) * G);
   double* vw = (double*)malloc(sizeof(double) * G);   /* rows computed on demand */
-  double* cdf = (double*)malloc(sizeof(double) * G);
+  int64_t* cdf = (int64_t*)malloc(sizeof(int64_t) * G);
   double* gam = (double*)malloc(sizeof(double) * nx);
   char* have = (char*)malloc(nx);
   int32_t err = 0;
@@ -300,24 +340,24 @@ int32_t wmco_simulate(const wmco_params* p, const double* V, const float* table,
       }
       /* kernel on an occupied cell, evaluated when first needed this step */
       double* row = vw + (int64_t)c * nM;
-      double* crow = cdf + (int64_t)c * nM;
+      int64_t* crow = cdf + (int64_t)c * nM;
       if (!have[c]) {
         if (table) {
           for (int64_t q = 0; q < nM; ++q) row[q] = (double)table[(int64_t)c * nM + q];
         } else {
           wmco_kernel_rows(p, V, 1, &c, row);
         }
-        gam[c] = wmco_cdf_row(p->n_M, row, crow);
+        gam[c] = wmco_cdf_row(p->n_M, row, crow, NULL);
         if (gam[c] * p->dt_s >= 1.0) stats[ST_RATE] += 1;
         have[c] = 1;
       }
       /* pair creation with probability gamma dt */
       uint32_t w[4];
-      draw(p, (uint32_t)id, t, WMCO_PURPOSE_GEN, w);
-      double u1 = wmco_u53(w[0], w[1]);
+      draw(p, (uint32_t)(id >> 2), t, WMCO_PURPOSE_GEN, w);
+      double u1 = wmco_u32(w[id & 3]);
       if (u1 < gam[c] * p->dt_s) {
-        double u2 = wmco_u53(w[2], w[3]);
-        int32_t kp = wmco_sample_row(p->n_M, row, crow, u2 * gam[c]);
+        draw(p, (uint32_t)id, t, WMCO_PURPOSE_PICK, w);
+        int32_t kp = wmco_sample_row(p->n_M, crow, wmco_u53_bits(w[0], w[1]));
         int32_t Mp = kp - p->n_M / 2;
         int32_t Mc[2] = {e.M[id] + Mp, e.M[id] - Mp};
         int32_t sc[2] = {sgn, -sgn};

@@ -43,10 +43,15 @@ Layout layout(const wmc_params& p) {
   L.occ = o; o = align256(o + sizeof(int) * nx);
   L.row_map = o; o = align256(o + sizeof(int) * nx);
   L.VWh = o; o = align256(o + sizeof(float) * nx * (size_t)L.h);
-  L.cdf = o; o = align256(o + sizeof(double) * nx * nM);
+  L.cdf = o; o = align256(o + sizeof(long long) * nx * nM);
   L.gamma = o; o = align256(o + sizeof(double) * nx);
   L.gthr = o; o = align256(o + sizeof(unsigned long long) * nx);
+  L.thr_cell = o; o = align256(o + sizeof(unsigned long long) * nx);
   L.D = o; o = align256(o + sizeof(float) * nM);
+  L.xlo = o; o = align256(o + sizeof(uint32_t) * nM);
+  L.xhi = o; o = align256(o + sizeof(uint32_t) * nM);
+  L.max_items = kMaxItemsBase + 2 * (long long)nx;
+  L.items = o; o = align256(o + sizeof(int2) * (size_t)L.max_items);
   L.B = o; o = align256(o + sizeof(float) * (size_t)L.Kp * (size_t)L.Np);
   L.total = o;
   return L;
@@ -64,10 +69,14 @@ View view(const wmc_params& p, void* ws) {
   v.occ = reinterpret_cast<int*>(b + L.occ);
   v.row_map = reinterpret_cast<int*>(b + L.row_map);
   v.VWh = reinterpret_cast<float*>(b + L.VWh);
-  v.cdf = reinterpret_cast<double*>(b + L.cdf);
+  v.cdf = reinterpret_cast<long long*>(b + L.cdf);
   v.gamma = reinterpret_cast<double*>(b + L.gamma);
   v.gthr = reinterpret_cast<unsigned long long*>(b + L.gthr);
   v.D = reinterpret_cast<float*>(b + L.D);
+  v.xlo = reinterpret_cast<uint32_t*>(b + L.xlo);
+  v.xhi = reinterpret_cast<uint32_t*>(b + L.xhi);
+  v.thr_cell = reinterpret_cast<unsigned long long*>(b + L.thr_cell);
+  v.items = reinterpret_cast<int2*>(b + L.items);
   v.B = reinterpret_cast<float*>(b + L.B);
   return v;
 }
@@ -108,7 +117,8 @@ static wmc_status one_step(const wmc_params& p, const View& v, const float* V, c
   (void)prec;
   e = launch_kernel_eval(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
-  e = launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, L.ld, 1, v.gamma, v.gthr, &v.hdr->flags, s);
+  e = launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, L.ld, 1, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
+                 &v.hdr->flags, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
   e = cudaMemsetAsync(out, 0, sizeof(int32_t) * (size_t)p.n_x * (size_t)p.n_M, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
@@ -204,13 +214,12 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
   return cuda_status(launch_kernel_eval(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, (cudaStream_t)stream));
 }
 
-wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows, double* cdf, double* gamma,
-                          void* ws, wmc_stream_t stream) {
+wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows, int64_t* cdf, double* gamma,
+                          int32_t* scale, wmc_stream_t stream) {
   if (!params_ok(p) || n_rows < 0 || (n_rows > 0 && (!VWh || !gamma))) return WMC_ERR_ARG;
-  (void)ws;
   if (n_rows == 0) return WMC_OK;
-  return cuda_status(launch_cdf(*p, VWh, nullptr, n_rows, n_rows, cdf, 1, p->n_M, gamma, nullptr, nullptr,
-                                (cudaStream_t)stream));
+  return cuda_status(launch_cdf(*p, VWh, nullptr, n_rows, n_rows, reinterpret_cast<long long*>(cdf), 1, p->n_M,
+                                gamma, scale, nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream));
 }
 
 wmc_status wmc_annihilate(const wmc_params* p, const int32_t* hist, int64_t* rho, void* ws, wmc_stream_t stream) {
@@ -228,7 +237,8 @@ wmc_status wmc_kernel_eval_occupied(const wmc_params* p, const float* V, wmc_pre
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_kernel_eval(*p, V, v.occ, &v.hdr->n_occ, 0, p->n_x, v.B, v.VWh, s);
   if (e == cudaSuccess)
-    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, L.ld, 1, v.gamma, v.gthr, &v.hdr->flags, s);
+    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, L.ld, 1, v.gamma, nullptr, v.gthr, v.occ,
+                   v.thr_cell, &v.hdr->flags, s);
   return cuda_status(e);
 }
 
@@ -239,7 +249,8 @@ wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, vo
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_gather_table(*p, table, v.occ, &v.hdr->n_occ, p->n_x, v.VWh, s);
   if (e == cudaSuccess)
-    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, L.ld, 1, v.gamma, v.gthr, &v.hdr->flags, s);
+    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, L.ld, 1, v.gamma, nullptr, v.gthr, v.occ,
+                   v.thr_cell, &v.hdr->flags, s);
   return cuda_status(e);
 }
 

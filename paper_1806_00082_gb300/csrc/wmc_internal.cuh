@@ -13,15 +13,26 @@ constexpr double kHbarEVs = 6.582119569e-16;  // hbar [eV s]
 constexpr double kHbarJs = 1.054571817e-34;   // hbar [J s]
 constexpr double kPi = 3.14159265358979323846;
 
-constexpr uint32_t kPurposeGen = 1u;    // Philox counter word 2 of the pair-creation draw
-constexpr uint32_t kPurposeRepos = 2u;  // ... of the offset a survivor is re-emitted at
+// Philox counter word 2 of each draw.  A particle with number id takes word
+// id % 4 of counter (id / 4, step, purpose, sim) for its offset (REPOS) and its
+// pair-creation uniform (GEN); a created pair draws p' from words 0, 1 of
+// (id, step, PICK, sim).
+constexpr uint32_t kPurposeGen = 1u;
+constexpr uint32_t kPurposeRepos = 2u;
+constexpr uint32_t kPurposePick = 3u;
 
-// Step work decomposition: a work item is up to kChunk consecutive particles of
-// one cell; a block of kStepThreads threads handles one item at a time and
-// each thread kPerThread consecutive particles of it.
+// Step work decomposition: the survivors of cell i (ids R[i] .. R[i] + T[i] - 1)
+// are cut into work items on a grid of kChunk ids aligned to A = R[i] rounded
+// down to a multiple of 4: item c of cell i holds the ids in
+// [A + c kChunk, A + (c+1) kChunk) that belong to the cell, so every Philox
+// call of a thread (four consecutive ids) stays within one item.  A cell has
+// ceil((T[i] + 3) / kChunk) items (the last may be empty).  A block takes one
+// item at a time, each of its threads kPerThread consecutive ids.
 constexpr int kStepThreads = 256;
 constexpr int kPerThread = 16;
 constexpr int kChunk = kStepThreads * kPerThread;
+constexpr int kMaxStepBlocks = 8192;
+constexpr long long kMaxItemsBase = 1ll << 20;   // item descriptors: 2^32 / kChunk + n_x
 
 constexpr unsigned kMagic = 0x574d4331u;  // "WMC1": set by wmc_init
 
@@ -44,7 +55,8 @@ struct DevHeader {
 
 // Byte offsets of the workspace regions (all 256-aligned).
 struct Layout {
-  size_t header, T, R, IP, reach, occ, row_map, VWh, cdf, gamma, gthr, D, B, total;
+  size_t header, T, R, IP, reach, occ, row_map, VWh, cdf, gamma, gthr, thr_cell, D, xlo, xhi, items, B, total;
+  long long max_items;
   int h;     // Q / 2
   int Kp;    // contraction length h - 1 padded to a multiple of 32
   int Np;    // output columns h padded to a multiple of 64
@@ -64,10 +76,14 @@ struct View {
   int* occ;                // [n_x] occupied-cell list (ascending)
   int* row_map;            // [n_x] cell -> row of occ, or -1
   float* VWh;              // [n_x][h] kernel half-period rows, by occ row
-  double* cdf;             // [n_M][ld] CDF, transposed (column k, row)
+  long long* cdf;          // [n_M][ld] fixed-point CDF, transposed (column k, row)
   double* gamma;           // [n_x] gamma by occ row
-  unsigned long long* gthr;// [n_x] event threshold: u53 integer < gthr <=> u53 < gamma dt
+  unsigned long long* gthr;// [n_x] event threshold by occ row: word < gthr <=> word 2^-32 < gamma dt
+  unsigned long long* thr_cell;  // [n_x] the same by cell (0 for cells without a kernel row)
   float* D;                // [n_M] drift per step in cells
+  uint32_t* xlo;           // [n_M] offset word w crosses left iff w < xlo[k]
+  uint32_t* xhi;           // [n_M] ... crosses right iff w > xhi[k]
+  int2* items;             // [max_items] work items (cell, chunk)
   float* B;                // [Kp][Np] sine matrix S[m][r], m = kk + 1
 };
 View view(const wmc_params& p, void* ws);
@@ -90,18 +106,26 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// Work items of a cell holding t survivors (an upper bound when its first id
+// is not a multiple of 4; surplus items are empty).
+__host__ __device__ __forceinline__ int items_of_cell(unsigned long long t) {
+  return t ? (int)((t + 3 + kChunk - 1) / kChunk) : 0;
+}
+
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t s);
 cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, int advance_step,
                         cudaStream_t s);
+int step_grid(int n_M);
 cudaError_t launch_kernel_eval(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
                                int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s);
 cudaError_t launch_gather_table(const wmc_params& p, const float* table, const int* occ, const int* n_occ_dev,
                                 int max_rows, float* VWh, cudaStream_t s);
-// CDF of rows: cdf[k * ldk + row * ldr]; gthr/flags may be null.
+// CDF of rows: cdf[k * ldk + row * ldr]; cdf/scale/gthr/flags may be null.
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host,
-                       int max_rows, double* cdf, long long ldk, long long ldr, double* gamma,
-                       unsigned long long* gthr, unsigned int* flags, cudaStream_t s);
+                       int max_rows, long long* cdf, long long ldk, long long ldr, double* gamma, int* scale,
+                       unsigned long long* gthr, const int* occ, unsigned long long* thr_cell, unsigned int* flags,
+                       cudaStream_t s);
 cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_in, uint32_t t, int t_from_device,
                         int32_t* hist_out, cudaStream_t s);
 cudaError_t launch_materialize(const wmc_params& p, const View& v, const int32_t* hist, uint32_t t, int32_t* cell,

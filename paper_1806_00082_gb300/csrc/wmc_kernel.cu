@@ -142,52 +142,129 @@ cudaError_t launch_gather_table(const wmc_params& p, const float* table, const i
 }
 
 // ---------------------------------------------------------------- gamma and CDF
-// One thread per kernel row: the running FP64 sum of V_W^+ over ascending M
-// (the order is part of the result: the pair sampler compares against these
-// exact partial sums).  gthr[row] = ceil(gamma dt 2^53), so that for a 53-bit
-// integer U, U < gthr  <=>  U 2^-53 < gamma dt.
-__global__ void k_cdf(int n_M, int Q, const float* __restrict__ VWh, const int* __restrict__ n_rows_dev,
-                      int n_rows_host, double* __restrict__ cdf, long long ldk, long long ldr,
-                      double* __restrict__ gamma, unsigned long long* __restrict__ gthr,
-                      unsigned int* __restrict__ flags, double dt) {
+// gamma and the momentum CDF of one kernel row per warp.  The positive parts
+// x_k = max(V_W(k), 0) are quantised relative to the row maximum,
+//   e = floor(log2 max x),  s = 61 - ceil(log2 n_M) - e,
+//   q_k = x_k 2^s rounded to the nearest integer, ties to even,
+// so that the CDF C[k] = sum_{k' <= k} q_k' is an exact int64 running sum (any
+// summation order gives the same bits, so a warp scan computes it) and
+// gamma = fl64(C[n_M-1] 2^-s).  gthr[row] = ceil(fl64(gamma dt) 2^32): for a
+// 32-bit word w, w < gthr  <=>  w 2^-32 < gamma dt.
+
+// x 2^s rounded to the nearest integer (ties to even), from the bits of x >= 0.
+__device__ __forceinline__ long long quantise(float x, int s) {
+  const uint32_t b = __float_as_uint(x);
+  if (b == 0u) return 0;
+  const uint32_t E = b >> 23;
+  uint32_t m = b & 0x7fffffu;
+  int ex = -149;                 // value = m 2^ex
+  if (E) {
+    m |= 0x800000u;
+    ex = (int)E - 150;
+  }
+  const int sh = ex + s;
+  if (sh >= 0) return (long long)((unsigned long long)m << sh);
+  const int r = -sh;
+  if (r > 25) return 0;          // m < 2^24: below half a unit
+  const uint32_t q = m >> r;
+  const uint32_t rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
+  return (long long)(q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u));
+}
+
+__device__ __forceinline__ int floor_log2_pos(float x) {  // x > 0
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t E = b >> 23;
+  if (E) return (int)E - 127;
+  return (31 - __clz(b & 0x7fffffu)) - 149;
+}
+
+__device__ __forceinline__ float positive_part(const float* __restrict__ v, int Q, int r) {
+  const int h = Q / 2;
+  float x = 0.f;
+  if (r != 0 && r != h) x = r < h ? __ldg(v + r) : -__ldg(v + (Q - r));
+  return x > 0.f ? x : 0.f;
+}
+
+constexpr int kCdfWarps = 8;
+
+__global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2_nM, const float* __restrict__ VWh,
+                                                       const int* __restrict__ n_rows_dev, int n_rows_host,
+                                                       long long* __restrict__ cdf, long long ldk, long long ldr,
+                                                       double* __restrict__ gamma, int* __restrict__ scale,
+                                                       unsigned long long* __restrict__ gthr,
+                                                       const int* __restrict__ occ,
+                                                       unsigned long long* __restrict__ thr_cell,
+                                                       unsigned int* __restrict__ flags, double dt) {
   const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_host;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kCdfWarps + (threadIdx.x >> 5);
   if (row >= n_rows) return;
   const int h = Q / 2;
   const float* v = VWh + (size_t)row * h;
-  int r = (-(n_M / 2)) % Q;
-  if (r < 0) r += Q;
-  double acc = 0.0;
-  double* out = cdf ? cdf + row * ldr : nullptr;
-  for (int k = 0; k < n_M; ++k) {
-    float x = 0.f;
-    if (r != 0 && r != h) x = r < h ? __ldg(v + r) : -__ldg(v + (Q - r));
-    const double xd = (double)x;
-    acc = __dadd_rn(acc, xd > 0.0 ? xd : 0.0);
-    if (out) out[k * ldk] = acc;
-    if (++r == Q) r = 0;
-  }
-  gamma[row] = acc;
-  if (gthr) {
-    const double g = __dmul_rn(acc, dt);
-    unsigned long long thr;
-    if (g >= 1.0) {
-      atomicOr(flags, WMC_FLAG_RATE);
-      thr = 1ull << 53;
-    } else {
-      thr = (unsigned long long)ceil(g * 9007199254740992.0);
+  const int r0 = ((-(n_M / 2)) % Q + Q) % Q;   // r of column k = 0
+  // row maximum of the positive parts (non-negative floats order as their bits)
+  uint32_t mx = 0u;
+  for (int k = lane; k < n_M; k += 32) mx = max(mx, __float_as_uint(positive_part(v, Q, (r0 + k) % Q)));
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  long long* out = cdf ? cdf + row * ldr : nullptr;
+  if (mx == 0u) {
+    if (out)
+      for (int k = lane; k < n_M; k += 32) out[k * ldk] = 0;
+    if (lane == 0) {
+      gamma[row] = 0.0;
+      if (scale) scale[row] = 0;
+      if (gthr) gthr[row] = 0ull;
+      if (thr_cell) thr_cell[__ldg(occ + row)] = 0ull;
     }
-    gthr[row] = thr;
+    return;
+  }
+  const int s = 61 - log2_nM - floor_log2_pos(__uint_as_float(mx));
+  long long carry = 0;
+  for (int k0 = 0; k0 < n_M; k0 += 32) {
+    const int k = k0 + lane;
+    long long q = k < n_M ? quantise(positive_part(v, Q, (r0 + k) % Q), s) : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const long long u = __shfl_up_sync(0xffffffffu, q, off);
+      if (lane >= off) q += u;
+    }
+    q += carry;
+    if (out && k < n_M) out[k * ldk] = q;
+    carry = __shfl_sync(0xffffffffu, q, 31);
+  }
+  if (lane == 0) {
+    const double g = ldexp((double)carry, -s);
+    gamma[row] = g;
+    if (scale) scale[row] = s;
+    if (gthr) {
+      const double gd = __dmul_rn(g, dt);
+      unsigned long long thr;
+      if (gd >= 1.0) {
+        atomicOr(flags, WMC_FLAG_RATE);
+        thr = 1ull << 32;
+      } else {
+        thr = (unsigned long long)ceil(gd * 4294967296.0);
+      }
+      gthr[row] = thr;
+      if (thr_cell) thr_cell[__ldg(occ + row)] = thr;
+    }
   }
 }
 
+static int ceil_log2(int n) {
+  int L = 0;
+  while ((1 << L) < n) ++L;
+  return L;
+}
+
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host, int max_rows,
-                       double* cdf, long long ldk, long long ldr, double* gamma, unsigned long long* gthr,
-                       unsigned int* flags, cudaStream_t s) {
+                       long long* cdf, long long ldk, long long ldr, double* gamma, int* scale,
+                       unsigned long long* gthr, const int* occ, unsigned long long* thr_cell, unsigned int* flags,
+                       cudaStream_t s) {
   if (max_rows <= 0) return cudaSuccess;
-  const int threads = 128;
-  k_cdf<<<(max_rows + threads - 1) / threads, threads, 0, s>>>(p.n_M, p.Q, VWh, n_rows_dev, n_rows_host, cdf, ldk,
-                                                               ldr, gamma, gthr, flags, p.dt_s);
+  k_cdf<<<(max_rows + kCdfWarps - 1) / kCdfWarps, kCdfWarps * 32, 0, s>>>(
+      p.n_M, p.Q, ceil_log2(p.n_M), VWh, n_rows_dev, n_rows_host, cdf, ldk, ldr, gamma, scale, gthr, occ, thr_cell,
+      flags, p.dt_s);
   return cudaGetLastError();
 }
 

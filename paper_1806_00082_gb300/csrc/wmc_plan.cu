@@ -7,12 +7,26 @@
 namespace wmc {
 
 // ---------------------------------------------------------------- constant tables
+// Smallest j in [0, 2^24] with fl32(j 2^-24 + d) >= edge (2^24 if none); the
+// predicate is monotone in j because rounding is.
+__device__ int first_offset_reaching(float d, float edge) {
+  int lo = 0, hi = 1 << 24;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__fadd_rn((float)mid * 0x1p-24f, d) >= edge) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
 // D[k] = fl32(M * d1), d1 = hbar pi dt / (m Q dx^2), M = k - n_M/2: the free
-// drift of momentum M dp over dt, in cells.  B[kk][r] = sin(2 pi ((kk+1) r mod Q) / Q)
-// for kk < h-1, r < h (zero padding elsewhere): the integer-indexed sine matrix
-// of the network's hidden layer (Sec. 2.2).
-__global__ void k_init_tables(int n_M, int Q, double d1, float* __restrict__ D, float* __restrict__ B, int Kp,
-                              int Np, DevHeader* hdr) {
+// drift of momentum M dp over dt, in cells.  Crossing thresholds on the offset
+// word w (f = (w >> 8) 2^-24): a particle of column k moves right iff
+// fl32(f + D) >= 1 iff w > xhi[k], left iff fl32(f + D) < 0 iff w < xlo[k].
+// B[kk][r] = sin(2 pi ((kk+1) r mod Q) / Q) for kk < h-1, r < h (zero padding
+// elsewhere): the integer-indexed sine matrix of the network's hidden layer
+// (Sec. 2.2).
+__global__ void k_init_tables(int n_M, int Q, double d1, float* __restrict__ D, uint32_t* __restrict__ xlo,
+                              uint32_t* __restrict__ xhi, float* __restrict__ B, int Kp, int Np, DevHeader* hdr) {
   const int h = Q / 2;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
@@ -21,7 +35,15 @@ __global__ void k_init_tables(int n_M, int Q, double d1, float* __restrict__ D, 
     z.magic = kMagic;
     *hdr = z;
   }
-  for (long long k = tid; k < n_M; k += nthreads) D[k] = __double2float_rn((double)(k - n_M / 2) * d1);
+  for (long long k = tid; k < n_M; k += nthreads) {
+    const float d = __double2float_rn((double)(k - n_M / 2) * d1);
+    D[k] = d;
+    uint32_t lo = 0u, hi = 0xffffffffu;
+    if (d > 0.f) hi = (uint32_t)(((unsigned long long)first_offset_reaching(d, 1.f) << 8) - 1ull);
+    if (d < 0.f) lo = (uint32_t)((unsigned long long)first_offset_reaching(d, 0.f) << 8);
+    xlo[k] = lo;
+    xhi[k] = hi;
+  }
   for (long long q = tid; q < (long long)Kp * Np; q += nthreads) {
     const int kk = (int)(q / Np), r = (int)(q % Np);
     float v = 0.f;
@@ -36,7 +58,7 @@ __global__ void k_init_tables(int n_M, int Q, double d1, float* __restrict__ D, 
 cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t s) {
   const Layout L = layout(p);
   const double d1 = ((kHbarJs * kPi) * p.dt_s) / ((p.mass_kg * (double)p.Q) * (p.dx_m * p.dx_m));
-  k_init_tables<<<256, 256, 0, s>>>(p.n_M, p.Q, d1, v.D, v.B, L.Kp, L.Np, v.hdr);
+  k_init_tables<<<256, 256, 0, s>>>(p.n_M, p.Q, d1, v.D, v.xlo, v.xhi, v.B, L.Kp, L.Np, v.hdr);
   return cudaGetLastError();
 }
 
@@ -98,10 +120,10 @@ __device__ __forceinline__ int needs_kernel(const unsigned char* reach, int i, i
   return (reach[i] & 1) || (i > 0 && (reach[i - 1] & 2)) || (i + 1 < n_x && (reach[i + 1] & 4));
 }
 
-__device__ __forceinline__ int items_of(unsigned long long t) { return (int)((t + kChunk - 1) / kChunk); }
-
 // One block: exclusive prefix sums of survivors (ids), work items and needed
-// cells, then the occupied list and row map.  Single block because n_x is at
+// cells, then the occupied list, row map and work-item descriptors; the
+// per-cell event thresholds are cleared (the kernel stage fills the occupied
+// cells).  Single block because n_x is at
 // most a few 10^4 in the workloads and this runs once per step.
 constexpr int kPlanThreads = 1024;
 
@@ -109,7 +131,9 @@ __global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned l
                                                        const unsigned char* __restrict__ reach,
                                                        unsigned long long* __restrict__ R, int* __restrict__ IP,
                                                        int* __restrict__ occ, int* __restrict__ row_map,
-                                                       DevHeader* hdr, int advance_step) {
+                                                       int2* __restrict__ items, long long max_items,
+                                                       unsigned long long* __restrict__ thr_cell, DevHeader* hdr,
+                                                       int advance_step) {
   __shared__ unsigned long long wT[32];
   __shared__ int wI[32], wN[32], wBig[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -120,7 +144,7 @@ __global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned l
   for (int i = lo; i < hi; ++i) {
     const unsigned long long t = T[i];
     aT += t;
-    aI += items_of(t);
+    aI += items_of_cell(t);
     aN += needs_kernel(reach, i, n_x);
     big |= t > 0x7fffffffull;
   }
@@ -170,9 +194,15 @@ __global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned l
   const unsigned long long baseT = (wid ? wT[wid - 1] : 0ull) + iT - aT;
   int baseI = (wid ? wI[wid - 1] : 0) + iI - aI;
   int baseN = (wid ? wN[wid - 1] : 0) + iN - aN;
+  const int ok = !wBig[31] && wT[31] < (1ull << 32) && (long long)wI[31] <= max_items;
   unsigned long long r = baseT;
   for (int i = lo; i < hi; ++i) {
     const unsigned long long t = T[i];
+    if (ok) {
+      const int ni = items_of_cell(t);
+      for (int c = 0; c < ni; ++c) items[baseI + c] = make_int2(i, c);
+    }
+    thr_cell[i] = 0ull;
     R[i] = r;
     IP[i] = baseI;
     if (needs_kernel(reach, i, n_x)) {
@@ -183,11 +213,11 @@ __global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned l
       row_map[i] = -1;
     }
     r += t;
-    baseI += items_of(t);
+    baseI += items_of_cell(t);
   }
   if (tid == kPlanThreads - 1) {
     const unsigned long long P = wT[31];
-    const int too_big = wBig[31] || P >= (1ull << 32);
+    const int too_big = !ok;
     R[n_x] = P;
     IP[n_x] = wI[31];
     hdr->population = P;
@@ -204,7 +234,8 @@ cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist,
   const int blocks = (p.n_x + warps_per_block - 1) / warps_per_block;
   k_rows<<<blocks, warps_per_block * 32, 0, s>>>(hist, p.n_x, p.n_M, v.D, v.T, v.reach,
                                                  reinterpret_cast<long long*>(rho));
-  k_plan<<<1, kPlanThreads, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.hdr, advance_step);
+  k_plan<<<1, kPlanThreads, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.items,
+                                    layout(p).max_items, v.thr_cell, v.hdr, advance_step);
   return cudaGetLastError();
 }
 

@@ -6,10 +6,13 @@
 // The survivors are never stored: after annihilation every particle of bucket
 // (i, M) carries the same cell, momentum and sign, and its offset is a Philox
 // draw of its id, so the histogram and the id prefix describe the ensemble
-// exactly.  A block takes a work item (up to kChunk consecutive ids of one
-// cell), privatises the three histogram rows its particles can land in
-// (i-1, i, i+1) in shared memory, and flushes them with one global atomic per
-// non-zero bucket.
+// exactly.  A block takes a work item (up to kChunk ids of one cell, aligned
+// so that each Philox call serves four consecutive ids of one thread),
+// privatises the three histogram rows its particles can land in (i-1, i, i+1)
+// in shared memory, and flushes them with one global atomic per non-zero
+// bucket.  A particle moves iff its offset word passes the integer threshold
+// of its momentum column, so a quad of ids inside one bucket costs one Philox
+// call and a handful of compares.
 #include "wmc_internal.cuh"
 
 namespace wmc {
@@ -18,14 +21,13 @@ struct StepArgs {
   const int32_t* hist_in;
   int32_t* hist_out;
   const unsigned long long* R;
-  const int* IP;
+  const int2* items;
   const int* row_map;
-  const double* cdf;  // [n_M][ld]
+  const long long* cdf;  // [n_M][ld] fixed-point CDF
   long long ld;
-  const double* gamma;
-  const unsigned long long* gthr;
-  const float* D;
-  const float* VWh;
+  const unsigned long long* thr_cell;
+  const uint32_t* xlo;
+  const uint32_t* xhi;
   DevHeader* hdr;
   int n_x, n_M, Q, child_wrap;
   uint32_t sim, k0, k1, t;
@@ -83,30 +85,52 @@ __device__ __forceinline__ int bucket_of(const int* s_pre, int n_M, int lid) {
   return lo;
 }
 
-// V_W(row; M = k - n_M/2) from a half-period row.
-__device__ __forceinline__ float kernel_at(const float* __restrict__ v, int Q, int n_M, int k) {
-  const int h = Q / 2;
-  int r = (k - n_M / 2) % Q;
-  if (r < 0) r += Q;
-  if (r == 0 || r == h) return 0.f;
-  return r < h ? __ldg(v + r) : -__ldg(v + (Q - r));
-}
-
-// Index of p': the smallest k with cdf[k] > target, else the largest k with
-// V_W^+ > 0 (a target equal to gamma after rounding).
-__device__ __forceinline__ int sample_momentum(const StepArgs& a, int orow, double target) {
-  const double* c = a.cdf + orow;
-  int lo = 0, hi = a.n_M;
+// Index of p' for the 53-bit uniform integer U2: target = floor(U2 Qtot / 2^53),
+// Qtot = C[n_M - 1], and the smallest k with C[k] > target (always exists,
+// since target < Qtot).
+__device__ __forceinline__ int sample_momentum(const StepArgs& a, int orow, unsigned long long U2) {
+  const long long* c = a.cdf + orow;
+  const unsigned long long Qtot = (unsigned long long)__ldg(c + (long long)(a.n_M - 1) * a.ld);
+  const long long target = (long long)((__umul64hi(U2, Qtot) << 11) | ((U2 * Qtot) >> 53));
+  int lo = 0, hi = a.n_M - 1;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (__ldg(c + (long long)mid * a.ld) > target) hi = mid; else lo = mid + 1;
   }
-  if (lo < a.n_M) return lo;
-  const float* v = a.VWh + (size_t)orow * (a.Q / 2);
-  for (int k = a.n_M - 1; k >= 0; --k)
-    if (kernel_at(v, a.Q, a.n_M, k) > 0.f) return k;
-  return -1;
+  return lo;
 }
+
+// A pair created by particle id (column k, sign sgn) that lands in cell c = i - 1 + d:
+// p' from the PICK draw, children into the block's private row d.
+__device__ __forceinline__ void create_pair(const StepArgs& a, uint32_t id, uint32_t t, int i, int d, int k,
+                                            int sgn, int* s_acc, unsigned long long& pairs,
+                                            unsigned long long& dropped, long long& drop_signed) {
+  const int n_M = a.n_M;
+  const int orow = __ldg(a.row_map + i - 1 + d);
+  const uint4 wp = philox4x32_10(make_uint4(id, t, kPurposePick, a.sim), a.k0, a.k1);
+  const unsigned long long U2 = ((unsigned long long)(wp.x >> 5) << 26) | (unsigned long long)(wp.y >> 6);
+  const int kp = sample_momentum(a, orow, U2);
+  ++pairs;
+  const int Mp = kp - n_M / 2;
+  const int kc2[2] = {k + Mp, k - Mp};
+  const int sc2[2] = {sgn, -sgn};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int kc = kc2[q];
+    if (kc < 0 || kc >= n_M) {
+      if (!a.child_wrap) {
+        ++dropped;
+        drop_signed += sc2[q];
+        continue;
+      }
+      kc = ((kc % n_M) + n_M) % n_M;
+    }
+    atomicAdd(&s_acc[d * n_M + kc], sc2[q]);
+  }
+}
+
+// Drift direction of column k from its thresholds: +1, -1, or 0 (never moves).
+__device__ __forceinline__ int drift_dir(uint32_t lo, uint32_t hi) { return hi != 0xffffffffu ? 1 : (lo ? -1 : 0); }
 
 __global__ __launch_bounds__(kStepThreads) void k_step(StepArgs a) {
   extern __shared__ int smem[];
@@ -114,118 +138,125 @@ __global__ __launch_bounds__(kStepThreads) void k_step(StepArgs a) {
   int* s_pre = smem;                 // n_M + 1
   int* s_n = s_pre + (n_M + 1);      // n_M
   int* s_acc = s_n + n_M;            // 3 n_M: rows i-1, i, i+1
-  float* s_D = reinterpret_cast<float*>(s_acc + 3 * n_M);  // n_M
+  uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_acc + 3 * n_M);  // n_M
+  uint32_t* s_hi = s_lo + n_M;                                     // n_M
   __shared__ int s_wsum[kStepThreads / 32];
-  __shared__ int s_row;
   __shared__ unsigned long long s_red[5][kStepThreads / 32];
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t t = a.t_from_device ? a.hdr->step : a.t;
   const int n_items = a.hdr->n_items;
-  for (int k = tid; k < n_M; k += kStepThreads) s_D[k] = a.D[k];
+  for (int k = tid; k < n_M; k += kStepThreads) {
+    s_lo[k] = a.xlo[k];
+    s_hi[k] = a.xhi[k];
+  }
 
   unsigned long long pairs = 0, absorbed = 0, dropped = 0;
   long long abs_signed = 0, drop_signed = 0;
 
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    __syncthreads();  // previous item fully flushed
-    if (tid == 0) {
-      int lo = 0, hi = a.n_x;  // largest i with IP[i] <= item
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(a.IP + mid) <= item) lo = mid; else hi = mid;
-      }
-      s_row = lo;
-    }
+    const int2 it = __ldg(a.items + item);
+    const int i = it.x, ch = it.y;
+    const uint32_t base = (uint32_t)__ldg(a.R + i);
+    const unsigned long long thr_m = i > 0 ? __ldg(a.thr_cell + i - 1) : 0ull;
+    const unsigned long long thr_0 = __ldg(a.thr_cell + i);
+    const unsigned long long thr_p = i + 1 < a.n_x ? __ldg(a.thr_cell + i + 1) : 0ull;
+    __syncthreads();  // the previous item is flushed
     for (int q = tid; q < 3 * n_M; q += kStepThreads) s_acc[q] = 0;
-    __syncthreads();
-    const int i = s_row;
-    const int chunk = item - __ldg(a.IP + i);
     load_row_prefix(a.hist_in, i, n_M, s_n, s_pre, s_wsum);
     __syncthreads();
 
-    const int Ti = s_pre[n_M];
-    const uint32_t base = (uint32_t)__ldg(a.R + i);
-    int orow[3];
-    unsigned long long thr[3];
-    double gam[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int c = i - 1 + d;
-      orow[d] = (c >= 0 && c < a.n_x) ? __ldg(a.row_map + c) : -1;
-      thr[d] = orow[d] >= 0 ? __ldg(a.gthr + orow[d]) : 0ull;
-      gam[d] = orow[d] >= 0 ? __ldg(a.gamma + orow[d]) : 0.0;
-    }
+    const uint32_t Ti = (uint32_t)s_pre[n_M];
+    const unsigned long long A = base & ~3u;
+    const unsigned long long lo64 = A + (unsigned long long)ch * kChunk + (unsigned long long)tid * kPerThread;
+    const unsigned long long row_end = (unsigned long long)base + Ti;
+    const unsigned long long g0_64 = lo64 > base ? lo64 : base;
+    const unsigned long long g1_64 = lo64 + kPerThread < row_end ? lo64 + kPerThread : row_end;
+    // ids stay below 2^32 (the plan guarantees it); compare in 64 bits first
+    const uint32_t g0 = g0_64 < g1_64 ? (uint32_t)g0_64 : 0u;
+    const uint32_t g1 = g0_64 < g1_64 ? (uint32_t)g1_64 : 0u;
+    const bool need_gen = (thr_m | thr_0 | thr_p) != 0ull;
 
-    const int lo = chunk * kChunk + tid * kPerThread;
-    const int hi = min(lo + kPerThread, Ti);
-    if (lo < hi) {
-      int k = bucket_of(s_pre, n_M, lo);
-      int end_k = s_pre[k + 1];
-      int sgn = s_n[k] > 0 ? 1 : -1;
-      float Dk = s_D[k];
-      int cnt[3] = {0, 0, 0};
-      for (int lid = lo; lid < hi; ++lid) {
-        if (lid >= end_k) {
+    int k = 0, n_tot = 0, n_mov = 0, sgn = 1, dir = 0;
+    if (g0 < g1) {
+      k = bucket_of(s_pre, n_M, (int)(g0 - base));
+      uint32_t end_g = base + (uint32_t)s_pre[k + 1];
+      sgn = s_n[k] > 0 ? 1 : -1;
+      uint32_t lo = s_lo[k], hi = s_hi[k];
+      dir = drift_dir(lo, hi);
+      unsigned long long thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
+      for (uint32_t q = g0 >> 2; q <= (g1 - 1u) >> 2; ++q) {
+        const uint32_t qa = q << 2;
+        const uint4 wr = philox4x32_10(make_uint4(q, t - 1u, kPurposeRepos, a.sim), a.k0, a.k1);
+        uint4 wg = make_uint4(0u, 0u, 0u, 0u);
+        if (need_gen) wg = philox4x32_10(make_uint4(q, t, kPurposeGen, a.sim), a.k0, a.k1);
+        if (qa >= g0 && qa + 3u < g1 && qa + 3u < end_g) {
+          // four consecutive ids of bucket k
+          const int m0 = (wr.x > hi) | (wr.x < lo), m1 = (wr.y > hi) | (wr.y < lo);
+          const int m2 = (wr.z > hi) | (wr.z < lo), m3 = (wr.w > hi) | (wr.w < lo);
+          n_mov += m0 + m1 + m2 + m3;
+          n_tot += 4;
+          if (need_gen) {
+            const int mv[4] = {m0, m1, m2, m3};
+            const uint32_t u[4] = {wg.x, wg.y, wg.z, wg.w};
 #pragma unroll
-          for (int d = 0; d < 3; ++d)
-            if (cnt[d]) {
-              atomicAdd(&s_acc[d * n_M + k], sgn * cnt[d]);
-              cnt[d] = 0;
-            }
-          do { ++k; } while (s_pre[k + 1] <= lid);
-          end_k = s_pre[k + 1];
-          sgn = s_n[k] > 0 ? 1 : -1;
-          Dk = s_D[k];
-        }
-        const uint32_t id = base + (uint32_t)lid;
-        int dc = 0;
-        if (Dk != 0.f) {
-          const uint4 w = philox4x32_10(make_uint4(id, t - 1u, kPurposeRepos, a.sim), a.k0, a.k1);
-          const float f = (float)(w.x >> 8) * 0x1p-24f;
-          const float fn = __fadd_rn(f, Dk);
-          dc = fn >= 1.f ? 1 : (fn < 0.f ? -1 : 0);
-        }
-        const int c = i + dc;
-        if (c < 0 || c >= a.n_x) {
-          ++absorbed;
-          abs_signed += sgn;
-          continue;
-        }
-        const int d = dc + 1;
-        ++cnt[d];
-        if (thr[d]) {
-          const uint4 w = philox4x32_10(make_uint4(id, t, kPurposeGen, a.sim), a.k0, a.k1);
-          const unsigned long long U = ((unsigned long long)(w.x >> 5) << 26) | (unsigned long long)(w.y >> 6);
-          if (U < thr[d]) {
-            const unsigned long long U2 = ((unsigned long long)(w.z >> 5) << 26) | (unsigned long long)(w.w >> 6);
-            const double target = __dmul_rn((double)U2 * 0x1p-53, gam[d]);
-            const int kp = sample_momentum(a, orow[d], target);
-            if (kp >= 0) {
-              ++pairs;
-              const int Mp = kp - n_M / 2;
-              const int kc2[2] = {k + Mp, k - Mp};
-              const int sc2[2] = {sgn, -sgn};
-#pragma unroll
-              for (int q = 0; q < 2; ++q) {
-                int kc = kc2[q];
-                if (kc < 0 || kc >= n_M) {
-                  if (!a.child_wrap) {
-                    ++dropped;
-                    drop_signed += sc2[q];
-                    continue;
-                  }
-                  kc = ((kc % n_M) + n_M) % n_M;
-                }
-                atomicAdd(&s_acc[d * n_M + kc], sc2[q]);
-              }
+            for (int j = 0; j < 4; ++j) {
+              if ((unsigned long long)u[j] < (mv[j] ? thr_move : thr_0))
+                create_pair(a, qa + (uint32_t)j, t, i, mv[j] ? dir + 1 : 1, k, sgn, s_acc, pairs, dropped,
+                            drop_signed);
             }
           }
+          continue;
+        }
+        const uint32_t w4[4] = {wr.x, wr.y, wr.z, wr.w};
+        const uint32_t u4[4] = {wg.x, wg.y, wg.z, wg.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t id = qa + (uint32_t)j;
+          if (id < g0 || id >= g1) continue;
+          if (id >= end_g) {  // next non-empty bucket
+            const int stay = n_tot - n_mov;
+            if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
+            if (n_mov) {
+              if ((unsigned)(i + dir) < (unsigned)a.n_x) {
+                atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * n_mov);
+              } else {
+                absorbed += n_mov;
+                abs_signed += sgn * n_mov;
+              }
+            }
+            n_tot = n_mov = 0;
+            do { ++k; } while (base + (uint32_t)s_pre[k + 1] <= id);
+            end_g = base + (uint32_t)s_pre[k + 1];
+            sgn = s_n[k] > 0 ? 1 : -1;
+            lo = s_lo[k];
+            hi = s_hi[k];
+            dir = drift_dir(lo, hi);
+            thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
+          }
+          const int mv = (w4[j] > hi) | (w4[j] < lo);
+          n_mov += mv;
+          ++n_tot;
+          if (need_gen && (unsigned long long)u4[j] < (mv ? thr_move : thr_0))
+            create_pair(a, id, t, i, mv ? dir + 1 : 1, k, sgn, s_acc, pairs, dropped, drop_signed);
         }
       }
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-        if (cnt[d]) atomicAdd(&s_acc[d * n_M + k], sgn * cnt[d]);
+    }
+    // last bucket of each thread: lanes holding the same bucket combine first
+    const int key = n_tot ? k : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int stay = __reduce_add_sync(peers, n_tot - n_mov);
+    const int mov = __reduce_add_sync(peers, n_mov);
+    if (key >= 0 && lane == __ffs(peers) - 1) {
+      if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
+      if (mov) {
+        if ((unsigned)(i + dir) < (unsigned)a.n_x) {
+          atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * mov);
+        } else {
+          absorbed += mov;
+          abs_signed += sgn * mov;
+        }
+      }
     }
     __syncthreads();
     for (int q = tid; q < 3 * n_M; q += kStepThreads) {
@@ -238,7 +269,7 @@ __global__ __launch_bounds__(kStepThreads) void k_step(StepArgs a) {
   }
 
   // block totals of the counters, one atomic each
-  const int lane = tid & 31, wid = tid >> 5;
+  const int wid = tid >> 5;
   unsigned long long vals[5] = {pairs, absorbed, (unsigned long long)abs_signed, dropped,
                                 (unsigned long long)drop_signed};
 #pragma unroll
@@ -262,9 +293,9 @@ __global__ __launch_bounds__(kStepThreads) void k_step(StepArgs a) {
   if (blockIdx.x == 0 && tid == 0 && n_items > 0) atomicAdd(&a.hdr->particle_steps, a.hdr->population);
 }
 
-static size_t step_smem(int n_M) { return sizeof(int) * (size_t)(n_M + 1 + n_M + 3 * n_M) + sizeof(float) * n_M; }
+static size_t step_smem(int n_M) { return sizeof(int) * (size_t)(n_M + 1 + n_M + 3 * n_M) + 2 * sizeof(uint32_t) * n_M; }
 
-static int step_grid(int n_M) {
+int step_grid(int n_M) {
   static int cached_nM[8] = {0};
   static int cached_grid[8] = {0};
   int dev = 0;
@@ -276,7 +307,8 @@ static int step_grid(int n_M) {
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, kStepThreads, sm);
   if (per_sm < 1) per_sm = 1;
-  const int g = per_sm * num_sms();
+  int g = per_sm * num_sms();
+  if (g > kMaxStepBlocks) g = kMaxStepBlocks;
   cached_nM[slot] = n_M;
   cached_grid[slot] = g;
   return g;
@@ -290,14 +322,13 @@ cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_
   a.hist_in = hist_in;
   a.hist_out = hist_out;
   a.R = v.R;
-  a.IP = v.IP;
+  a.items = v.items;
   a.row_map = v.row_map;
   a.cdf = v.cdf;
   a.ld = layout(p).ld;
-  a.gamma = v.gamma;
-  a.gthr = v.gthr;
-  a.D = v.D;
-  a.VWh = v.VWh;
+  a.thr_cell = v.thr_cell;
+  a.xlo = v.xlo;
+  a.xhi = v.xhi;
   a.hdr = v.hdr;
   a.n_x = p.n_x;
   a.n_M = p.n_M;
@@ -355,9 +386,10 @@ __global__ __launch_bounds__(kStepThreads) void k_materialize(const int32_t* __r
       for (int lid = lo; lid < hi; ++lid) {
         while (s_pre[k + 1] <= lid) ++k;
         const uint32_t id = base + (uint32_t)lid;
-        const uint4 w = philox4x32_10(make_uint4(id, t, kPurposeRepos, sim), k0, k1);
+        const uint4 w = philox4x32_10(make_uint4(id >> 2, t, kPurposeRepos, sim), k0, k1);
+        const uint32_t wj = (id & 3u) == 0u ? w.x : ((id & 3u) == 1u ? w.y : ((id & 3u) == 2u ? w.z : w.w));
         cell[id] = i;
-        f[id] = (float)(w.x >> 8) * 0x1p-24f;
+        f[id] = (float)(wj >> 8) * 0x1p-24f;
         M[id] = (int16_t)(k - n_M / 2);
         sign[id] = (int8_t)(s_n[k] > 0 ? 1 : -1);
       }

@@ -197,13 +197,15 @@ def kernel_eval_noalloc(p: Params, V: torch.Tensor, occ: torch.Tensor, out: torc
     return out
 
 
-def kernel_cdf(p: Params, VWh: torch.Tensor, ws: torch.Tensor | None = None, with_cdf: bool = True):
+def kernel_cdf(p: Params, VWh: torch.Tensor, with_cdf: bool = True):
+    """(cdf int64 [n, n_M] or None, gamma float64 [n], scale int32 [n])."""
     n = VWh.shape[0]
-    cdf = torch.empty((n, p.n_M), dtype=torch.float64, device=VWh.device) if with_cdf else None
+    cdf = torch.empty((n, p.n_M), dtype=torch.int64, device=VWh.device) if with_cdf else None
     gamma = torch.empty(n, dtype=torch.float64, device=VWh.device)
+    scale = torch.empty(n, dtype=torch.int32, device=VWh.device)
     _check("wmc_kernel_cdf", load().wmc_kernel_cdf(ctypes.byref(p), _ptr(VWh), n, _ptr(cdf), _ptr(gamma),
-                                                   _ptr(ws), _stream()))
-    return cdf, gamma
+                                                   _ptr(scale), _stream()))
+    return cdf, gamma, scale
 
 
 def annihilate(p: Params, hist: torch.Tensor, ws: torch.Tensor, rho: torch.Tensor | None = None):

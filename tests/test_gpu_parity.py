@@ -114,19 +114,24 @@ def test_kernel_eval_clamp_boundary(wmc):
 
 @pytest.mark.parametrize("wl", [wi.BARRIER_100, wi.BARRIER_2000, wi.DOUBLE_BARRIER_16384])
 def test_cdf_bit_exact_on_same_kernel_values(wmc, wl):
-    """gamma and the CDF from identical FP32 kernel values are identical."""
+    """gamma, the fixed-point CDF and its scale from identical FP32 kernel values
+    are identical."""
     p = wmc.Params.of(wl)
     V = wi.potential(wl)
     rows = np.arange(wl.n_x) if wl.n_x <= 2000 else np.arange(8192 - 160, 8192 + 160)
     po = oracle.params(wl)
     full = oracle.kernel_rows(po, V, rows).astype(np.float32)
     half = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, rows)[:, wl.Q // 2:].astype(np.float32)
-    cdf, gamma = wmc.kernel_cdf(p, torch.from_numpy(np.ascontiguousarray(half)).cuda())
-    cdf, gamma = cdf.cpu().numpy(), gamma.cpu().numpy()
+    cdf, gamma, scale = wmc.kernel_cdf(p, torch.from_numpy(np.ascontiguousarray(half)).cuda())
+    cdf, gamma, scale = cdf.cpu().numpy(), gamma.cpu().numpy(), scale.cpu().numpy()
+    npos = 0
     for r in range(rows.size):
-        c_ref, g_ref = oracle.cdf_row(full[r].astype(np.float64))
+        c_ref, g_ref, s_ref = oracle.cdf_row(full[r].astype(np.float64), with_scale=True)
         assert np.array_equal(cdf[r], c_ref)
         assert gamma[r] == g_ref
+        assert scale[r] == s_ref
+        npos += g_ref > 0
+    assert npos > 0
 
 
 # --------------------------------------------------------------------------- steps, bit-exact

@@ -49,6 +49,8 @@ def test_uniform_conversions_exact():
     assert oracle.u24(0xFFFFFFFF) == np.float32(1 - 2.0 ** -24)
     assert oracle.u24(0x100) == np.float32(2.0 ** -24)
     assert oracle.u24(0xFF) == 0.0
+    assert oracle.u32(0) == 0.0 and oracle.u32(1) == 2.0 ** -32
+    assert oracle.u32(0xFFFFFFFF) == 1 - 2.0 ** -32
 
 
 # --------------------------------------------------------------------------- sine table
@@ -241,12 +243,20 @@ def test_gamma_even_in_potential_and_cdf():
     K = oracle.kernel_rows(p, V, np.arange(w.n_x))
     Kn = oracle.kernel_rows(p, -V, np.arange(w.n_x))
     for i in range(0, w.n_x, 3):
-        cdf, g = oracle.cdf_row(K[i])
+        cdf, g, sc = oracle.cdf_row(K[i], with_scale=True)
         _, gn = oracle.cdf_row(Kn[i])
         assert np.all(np.diff(cdf) >= 0)
-        assert g == cdf[-1]
-        assert abs(g - np.sum(np.maximum(K[i], 0))) <= 1e-14 * max(g, 1)
-        assert abs(g - gn) <= 1e-13 * max(g, 1)
+        assert cdf[-1] < 2 ** 62
+        assert g == math.ldexp(float(cdf[-1]), -sc)
+        # gamma is the sum of V_W^+ to within the fixed-point resolution
+        assert abs(g - math.fsum(np.maximum(K[i], 0))) <= 1e-14 * max(g, 1)
+        # each CDF increment is the positive part in units of 2^-s
+        inc = np.diff(np.concatenate([[0], cdf])).astype(np.float64)
+        pos = np.maximum(K[i], 0)
+        if g > 0:
+            assert np.all(np.abs(np.ldexp(inc, -sc) - pos) <= np.ldexp(0.5, -sc))
+        # V -> -V mirrors the positive parts in M: the exact sums are equal
+        assert g == gn
     # far from the barrier (beyond L_C / 2 from it) the kernel and gamma vanish
     _, g0 = oracle.cdf_row(K[5])
     assert g0 == 0.0
@@ -262,17 +272,18 @@ def test_momentum_sampling_law():
     rng = np.random.default_rng(3)
     n = 40000
     counts = np.zeros(w.n_M)
-    for u in rng.random(n):
-        counts[oracle.sample_row(row, cdf, u * g)] += 1
+    for U2 in rng.integers(0, 2 ** 53, size=n, dtype=np.uint64):
+        counts[oracle.sample_row(cdf, int(U2))] += 1
     prob = np.maximum(row, 0) / g
     assert np.all(counts[prob == 0] == 0)
     sel = prob * n > 5
     chi2 = np.sum((counts[sel] - n * prob[sel]) ** 2 / (n * prob[sel]))
     dof = sel.sum() - 1
     assert chi2 < dof + 6 * math.sqrt(2 * dof)
-    # a target at or beyond gamma falls back to the last positive entry
-    last = np.nonzero(row > 0)[0][-1]
-    assert oracle.sample_row(row, cdf, g) == last
+    # the extreme uniforms land on the first and last positive entries
+    pos = np.nonzero(row > 0)[0]
+    assert oracle.sample_row(cdf, 0) == pos[0]
+    assert oracle.sample_row(cdf, 2 ** 53 - 1) == pos[-1]
 
 
 def test_drift_is_free_flight():
@@ -298,10 +309,10 @@ def test_materialize_order_and_offsets():
     assert np.all(np.diff(key) >= 0)
     np.testing.assert_array_equal(np.bincount(key, weights=s, minlength=w.n_x * w.n_M).reshape(h.shape), h)
     assert np.all((f >= 0) & (f < 1)) and np.all(f * 2 ** 24 == np.floor(f * 2 ** 24))
-    # offsets are the REPOS draw of each id at this step
-    for i in [0, 17, cell.size - 1]:
-        wds = oracle.philox([i, 9, 2, 0], [w.seed & 0xFFFFFFFF, w.seed >> 32])
-        assert f[i] == oracle.u24(int(wds[0]))
+    # offsets: word id mod 4 of the REPOS draw of counter id / 4 at this step
+    for i in [0, 1, 2, 3, 17, cell.size - 1]:
+        wds = oracle.philox([i >> 2, 9, 2, 0], [w.seed & 0xFFFFFFFF, w.seed >> 32])
+        assert f[i] == oracle.u24(int(wds[i & 3]))
 
 
 def test_density_is_signed_row_sum():
@@ -394,7 +405,7 @@ def test_pair_creation_rate_and_momentum_law():
 
 def test_single_particle_hand_trace():
     """One particle traced by hand through the counter layout: REPOS draw of
-    step t-1 for the offset, GEN draw of step t for the event."""
+    step t-1 for the offset, GEN draw of step t for the event, PICK draw for p'."""
     w = wi.BARRIER_100
     p = oracle.params(w)
     V = wi.potential(w)
@@ -411,8 +422,9 @@ def test_single_particle_hand_trace():
         wd = oracle.philox([0, t, 1, 0], key)
         expect = np.zeros_like(h0)
         expect[c, k] += 1
-        if oracle.u53(int(wd[0]), int(wd[1])) < g * w.dt_s:
-            kp = oracle.sample_row(row, cdf, oracle.u53(int(wd[2]), int(wd[3])) * g)
+        if oracle.u32(int(wd[0])) < g * w.dt_s:
+            wp = oracle.philox([0, t, 3, 0], key)
+            kp = oracle.sample_row(cdf, oracle.u53_bits(int(wp[0]), int(wp[1])))
             for (kc, sg) in [(k + kp - w.n_M // 2, 1), (k - (kp - w.n_M // 2), -1)]:
                 if 0 <= kc < w.n_M:
                     expect[c, kc] += sg
