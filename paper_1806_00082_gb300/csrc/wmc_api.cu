@@ -33,7 +33,6 @@ Layout layout(const wmc_params& p) {
   L.Kp = ((L.h - 1 + 31) / 32) * 32;
   if (L.Kp == 0) L.Kp = 32;
   L.Np = ((L.h + 63) / 64) * 64;
-  L.ld = p.n_x;
   size_t o = 0;
   L.header = o; o = align256(o + sizeof(DevHeader));
   L.T = o; o = align256(o + sizeof(unsigned long long) * nx);
@@ -108,6 +107,18 @@ __global__ void k_reset_counters(DevHeader* hdr) {
 
 static wmc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WMC_OK : WMC_ERR_CUDA; }
 
+// Kernel rows, CDFs and thresholds of the occupied list in the workspace:
+// fused for small windows, tiled contraction + CDF kernel otherwise.
+static cudaError_t kernel_and_cdf_occupied(const wmc_params& p, const View& v, const float* V, cudaStream_t s) {
+  if (small_window(p))
+    return launch_kernel_rows_small(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, v.cdf, v.gamma, v.gthr,
+                                    v.thr_cell, &v.hdr->flags, s);
+  cudaError_t e = launch_kernel_eval(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, s);
+  if (e != cudaSuccess) return e;
+  return launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
+                    &v.hdr->flags, s);
+}
+
 // drift + kernel + step for one step, state in -> out, step number on the device
 static wmc_status one_step(const wmc_params& p, const View& v, const float* V, const int32_t* in, int32_t* out,
                            wmc_precision prec, int device_step, uint32_t t, cudaStream_t s) {
@@ -115,10 +126,7 @@ static wmc_status one_step(const wmc_params& p, const View& v, const float* V, c
   cudaError_t e = launch_plan(p, v, in, nullptr, device_step, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
   (void)prec;
-  e = launch_kernel_eval(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, s);
-  if (e != cudaSuccess) return WMC_ERR_CUDA;
-  e = launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, L.ld, 1, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
-                 &v.hdr->flags, s);
+  e = kernel_and_cdf_occupied(p, v, V, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
   e = cudaMemsetAsync(out, 0, sizeof(int32_t) * (size_t)p.n_x * (size_t)p.n_M, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
@@ -211,6 +219,9 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
   if (prec != WMC_FP32) return WMC_ERR_UNSUPPORTED;
   if (n_occ == 0) return WMC_OK;
   const View v = view(*p, ws);
+  if (small_window(*p))
+    return cuda_status(launch_kernel_rows_small(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, nullptr, nullptr,
+                                                nullptr, nullptr, nullptr, (cudaStream_t)stream));
   return cuda_status(launch_kernel_eval(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, (cudaStream_t)stream));
 }
 
@@ -218,8 +229,8 @@ wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows,
                           int32_t* scale, wmc_stream_t stream) {
   if (!params_ok(p) || n_rows < 0 || (n_rows > 0 && (!VWh || !gamma))) return WMC_ERR_ARG;
   if (n_rows == 0) return WMC_OK;
-  return cuda_status(launch_cdf(*p, VWh, nullptr, n_rows, n_rows, reinterpret_cast<long long*>(cdf), 1, p->n_M,
-                                gamma, scale, nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream));
+  return cuda_status(launch_cdf(*p, VWh, nullptr, n_rows, n_rows, reinterpret_cast<long long*>(cdf), gamma, scale,
+                                nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream));
 }
 
 wmc_status wmc_annihilate(const wmc_params* p, const int32_t* hist, int64_t* rho, void* ws, wmc_stream_t stream) {
@@ -234,12 +245,7 @@ wmc_status wmc_kernel_eval_occupied(const wmc_params* p, const float* V, wmc_pre
   if (prec != WMC_FP32) return WMC_ERR_UNSUPPORTED;
   const View v = view(*p, ws);
   const Layout L = layout(*p);
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_kernel_eval(*p, V, v.occ, &v.hdr->n_occ, 0, p->n_x, v.B, v.VWh, s);
-  if (e == cudaSuccess)
-    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, L.ld, 1, v.gamma, nullptr, v.gthr, v.occ,
-                   v.thr_cell, &v.hdr->flags, s);
-  return cuda_status(e);
+  return cuda_status(kernel_and_cdf_occupied(*p, v, V, (cudaStream_t)stream));
 }
 
 wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, void* ws, wmc_stream_t stream) {
@@ -249,8 +255,8 @@ wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, vo
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_gather_table(*p, table, v.occ, &v.hdr->n_occ, p->n_x, v.VWh, s);
   if (e == cudaSuccess)
-    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, L.ld, 1, v.gamma, nullptr, v.gthr, v.occ,
-                   v.thr_cell, &v.hdr->flags, s);
+    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
+                   &v.hdr->flags, s);
   return cuda_status(e);
 }
 

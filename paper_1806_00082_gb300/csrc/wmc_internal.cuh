@@ -29,7 +29,7 @@ constexpr uint32_t kPurposePick = 3u;
 // ceil((T[i] + 3) / kChunk) items (the last may be empty).  A block takes one
 // item at a time, each of its threads kPerThread consecutive ids.
 constexpr int kStepThreads = 256;
-constexpr int kPerThread = 16;
+constexpr int kPerThread = 32;
 constexpr int kChunk = kStepThreads * kPerThread;
 constexpr int kMaxStepBlocks = 8192;
 constexpr long long kMaxItemsBase = 1ll << 20;   // item descriptors: 2^32 / kChunk + n_x
@@ -50,7 +50,9 @@ struct DevHeader {
   unsigned int flags;
   unsigned int step;    // device step counter (wmc_run)
   unsigned int magic;
-  unsigned int pad[5];
+  unsigned int item_ticket;  // next work item of the running step launch
+  unsigned int blocks_done;  // step blocks finished (the last one resets both)
+  unsigned int pad[3];
 };
 
 // Byte offsets of the workspace regions (all 256-aligned).
@@ -60,7 +62,6 @@ struct Layout {
   int h;     // Q / 2
   int Kp;    // contraction length h - 1 padded to a multiple of 32
   int Np;    // output columns h padded to a multiple of 64
-  int ld;    // leading dimension of the transposed CDF (= n_x)
 };
 
 bool params_ok(const wmc_params* p);
@@ -76,7 +77,7 @@ struct View {
   int* occ;                // [n_x] occupied-cell list (ascending)
   int* row_map;            // [n_x] cell -> row of occ, or -1
   float* VWh;              // [n_x][h] kernel half-period rows, by occ row
-  long long* cdf;          // [n_M][ld] fixed-point CDF, transposed (column k, row)
+  long long* cdf;          // [n_x][n_M] fixed-point CDF by occ row
   double* gamma;           // [n_x] gamma by occ row
   unsigned long long* gthr;// [n_x] event threshold by occ row: word < gthr <=> word 2^-32 < gamma dt
   unsigned long long* thr_cell;  // [n_x] the same by cell (0 for cells without a kernel row)
@@ -119,13 +120,19 @@ cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist,
 int step_grid(int n_M);
 cudaError_t launch_kernel_eval(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
                                int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s);
+// Fused kernel row + fixed-point CDF for small windows (Q/2 <= 128); the CDF
+// outputs may all be null (kernel rows only).
+bool small_window(const wmc_params& p);
+cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
+                                     int n_occ_host, int max_rows, const float* B, float* VWh, long long* cdf,
+                                     double* gamma, unsigned long long* gthr, unsigned long long* thr_cell,
+                                     unsigned int* flags, cudaStream_t s);
 cudaError_t launch_gather_table(const wmc_params& p, const float* table, const int* occ, const int* n_occ_dev,
                                 int max_rows, float* VWh, cudaStream_t s);
-// CDF of rows: cdf[k * ldk + row * ldr]; cdf/scale/gthr/flags may be null.
+// CDF of rows, row-major cdf[row][n_M]; cdf/scale/gthr/thr_cell/flags may be null.
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host,
-                       int max_rows, long long* cdf, long long ldk, long long ldr, double* gamma, int* scale,
-                       unsigned long long* gthr, const int* occ, unsigned long long* thr_cell, unsigned int* flags,
-                       cudaStream_t s);
+                       int max_rows, long long* cdf, double* gamma, int* scale, unsigned long long* gthr,
+                       const int* occ, unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s);
 cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_in, uint32_t t, int t_from_device,
                         int32_t* hist_out, cudaStream_t s);
 cudaError_t launch_materialize(const wmc_params& p, const View& v, const int32_t* hist, uint32_t t, int32_t* cell,

@@ -185,13 +185,72 @@ __device__ __forceinline__ float positive_part(const float* __restrict__ v, int 
   return x > 0.f ? x : 0.f;
 }
 
+__device__ __forceinline__ float positive_part_smem(const float* v, int Q, int r) {
+  const int h = Q / 2;
+  float x = 0.f;
+  if (r != 0 && r != h) x = r < h ? v[r] : -v[Q - r];
+  return x > 0.f ? x : 0.f;
+}
+
 constexpr int kCdfWarps = 8;
+
+// The fixed-point CDF of one row held in a warp: lane l takes the contiguous
+// columns k in [l E, (l+1) E), E = ceil(n_M / 32), so a row needs one warp
+// reduction (maximum), one warp scan of the lane totals and E sequential
+// integer additions per lane; lanes write contiguous runs of the row-major CDF.
+// xpos(k) returns max(V_W(k), 0) for column k.
+template <class XPos>
+__device__ __forceinline__ void warp_row_cdf(XPos xpos, int n_M, int log2_nM, int lane, long long* __restrict__ out,
+                                             double& gamma_out, int& scale_out, long long& total_out) {
+  const int E = (n_M + 31) >> 5;
+  const int k0 = lane * E, k1 = min(k0 + E, n_M);
+  uint32_t mx = 0u;
+  for (int k = k0; k < k1; ++k) mx = max(mx, __float_as_uint(xpos(k)));
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (mx == 0u) {
+    if (out)
+      for (int k = k0; k < k1; ++k) out[k] = 0;
+    gamma_out = 0.0;
+    scale_out = 0;
+    total_out = 0;
+    return;
+  }
+  const int s = 61 - log2_nM - floor_log2_pos(__uint_as_float(mx));
+  long long local = 0;
+  for (int k = k0; k < k1; ++k) local += quantise(xpos(k), s);
+  long long incl = local;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const long long u = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += u;
+  }
+  const long long total = __shfl_sync(0xffffffffu, incl, 31);
+  if (out) {
+    long long run = incl - local;
+    for (int k = k0; k < k1; ++k) {
+      run += quantise(xpos(k), s);
+      out[k] = run;
+    }
+  }
+  gamma_out = ldexp((double)total, -s);
+  scale_out = s;
+  total_out = total;
+}
+
+// gthr = ceil(fl64(gamma dt) 2^32), flagging gamma dt >= 1.
+__device__ __forceinline__ unsigned long long event_threshold(double g, double dt, unsigned int* flags) {
+  const double gd = __dmul_rn(g, dt);
+  if (gd >= 1.0) {
+    atomicOr(flags, WMC_FLAG_RATE);
+    return 1ull << 32;
+  }
+  return (unsigned long long)ceil(gd * 4294967296.0);
+}
 
 __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2_nM, const float* __restrict__ VWh,
                                                        const int* __restrict__ n_rows_dev, int n_rows_host,
-                                                       long long* __restrict__ cdf, long long ldk, long long ldr,
-                                                       double* __restrict__ gamma, int* __restrict__ scale,
-                                                       unsigned long long* __restrict__ gthr,
+                                                       long long* __restrict__ cdf, double* __restrict__ gamma,
+                                                       int* __restrict__ scale, unsigned long long* __restrict__ gthr,
                                                        const int* __restrict__ occ,
                                                        unsigned long long* __restrict__ thr_cell,
                                                        unsigned int* __restrict__ flags, double dt) {
@@ -199,52 +258,18 @@ __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * kCdfWarps + (threadIdx.x >> 5);
   if (row >= n_rows) return;
-  const int h = Q / 2;
-  const float* v = VWh + (size_t)row * h;
+  const float* v = VWh + (size_t)row * (Q / 2);
   const int r0 = ((-(n_M / 2)) % Q + Q) % Q;   // r of column k = 0
-  // row maximum of the positive parts (non-negative floats order as their bits)
-  uint32_t mx = 0u;
-  for (int k = lane; k < n_M; k += 32) mx = max(mx, __float_as_uint(positive_part(v, Q, (r0 + k) % Q)));
-  mx = __reduce_max_sync(0xffffffffu, mx);
-  long long* out = cdf ? cdf + row * ldr : nullptr;
-  if (mx == 0u) {
-    if (out)
-      for (int k = lane; k < n_M; k += 32) out[k * ldk] = 0;
-    if (lane == 0) {
-      gamma[row] = 0.0;
-      if (scale) scale[row] = 0;
-      if (gthr) gthr[row] = 0ull;
-      if (thr_cell) thr_cell[__ldg(occ + row)] = 0ull;
-    }
-    return;
-  }
-  const int s = 61 - log2_nM - floor_log2_pos(__uint_as_float(mx));
-  long long carry = 0;
-  for (int k0 = 0; k0 < n_M; k0 += 32) {
-    const int k = k0 + lane;
-    long long q = k < n_M ? quantise(positive_part(v, Q, (r0 + k) % Q), s) : 0;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const long long u = __shfl_up_sync(0xffffffffu, q, off);
-      if (lane >= off) q += u;
-    }
-    q += carry;
-    if (out && k < n_M) out[k * ldk] = q;
-    carry = __shfl_sync(0xffffffffu, q, 31);
-  }
+  auto xpos = [&](int k) { return positive_part(v, Q, (r0 + k) % Q); };
+  double g;
+  int sc;
+  long long tot;
+  warp_row_cdf(xpos, n_M, log2_nM, lane, cdf ? cdf + (size_t)row * n_M : nullptr, g, sc, tot);
   if (lane == 0) {
-    const double g = ldexp((double)carry, -s);
     gamma[row] = g;
-    if (scale) scale[row] = s;
+    if (scale) scale[row] = sc;
     if (gthr) {
-      const double gd = __dmul_rn(g, dt);
-      unsigned long long thr;
-      if (gd >= 1.0) {
-        atomicOr(flags, WMC_FLAG_RATE);
-        thr = 1ull << 32;
-      } else {
-        thr = (unsigned long long)ceil(gd * 4294967296.0);
-      }
+      const unsigned long long thr = g > 0.0 ? event_threshold(g, dt, flags) : 0ull;
       gthr[row] = thr;
       if (thr_cell) thr_cell[__ldg(occ + row)] = thr;
     }
@@ -257,14 +282,137 @@ static int ceil_log2(int n) {
   return L;
 }
 
+// ---------------------------------------------------------------- fused row kernel (h <= 128)
+// For windows of up to 256 quadrature points one warp evaluates a whole kernel
+// row: lane l owns the differences dV(m) for m = l + 1 + 32 q and the output
+// columns r = l + 32 c; dV(m) is broadcast by shuffle and multiplied by the
+// sine matrix staged in shared memory, with the same compensated (32-term
+// chunk + TwoSum) FP32 accumulation as the tiled contraction.  When CDF
+// outputs are given the warp then builds the row's fixed-point CDF, gamma and
+// event threshold from the row it holds, saving a launch and a round trip.
+constexpr int kRowWarps = 8;
+constexpr int kRowMaxH = 128;
+
+template <int C>  // output columns per lane: h <= 32 C
+__global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
+    const float* __restrict__ V, int n_x, int bc, int Q, int n_M, int log2_nM, const int* __restrict__ occ,
+    const int* __restrict__ n_occ_dev, int n_occ_host, const float* __restrict__ B, int Np, float c,
+    float* __restrict__ VWh, long long* __restrict__ cdf, double* __restrict__ gamma,
+    unsigned long long* __restrict__ gthr, unsigned long long* __restrict__ thr_cell, unsigned int* __restrict__ flags,
+    double dt) {
+  extern __shared__ float s_mem[];
+  const int h = Q / 2;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* s_B = s_mem;                                   // (h - 1) x h, row m - 1
+  float* s_row = s_mem + (h - 1) * h + wid * 2 * 32 * C;  // kernel row (h floats)
+  float* s_dv = s_row + 32 * C;                         // dV(m) at s_dv[m - 1]
+  const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
+  if ((int)(blockIdx.x * kRowWarps) >= n_rows) return;
+  for (int q = threadIdx.x; q < (h - 1) * h; q += blockDim.x) {
+    const int m1 = q / h, r = q - m1 * h;
+    s_B[q] = __ldg(B + (size_t)m1 * Np + r);
+  }
+  __syncthreads();
+  const int r0 = ((-(n_M / 2)) % Q + Q) % Q;
+  for (int row = blockIdx.x * kRowWarps + wid; row < n_rows; row += gridDim.x * kRowWarps) {
+    const int i = __ldg(occ + row);
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      const int m = lane + 1 + 32 * q;
+      s_dv[m - 1] = m <= h - 1 ? __fsub_rn(pot(V, n_x, bc, (long long)i + m), pot(V, n_x, bc, (long long)i - m))
+                               : 0.f;
+    }
+    __syncwarp();
+    float sacc[C], eacc[C];
+#pragma unroll
+    for (int cc = 0; cc < C; ++cc) sacc[cc] = eacc[cc] = 0.f;
+    for (int m0 = 1; m0 <= h - 1; m0 += 32) {   // chunks of 32 window terms
+      float part[C];
+#pragma unroll
+      for (int cc = 0; cc < C; ++cc) part[cc] = 0.f;
+      const int m1 = min(m0 + 32, h);
+      for (int m = m0; m < m1; ++m) {
+        const float d = s_dv[m - 1];
+        const float* brow = s_B + (m - 1) * h;
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) {
+          const int r = lane + 32 * cc;
+          if (r < h) part[cc] = fmaf(d, brow[r], part[cc]);
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < C; ++cc) two_sum_acc(sacc[cc], eacc[cc], part[cc]);
+    }
+    float* out = VWh + (size_t)row * h;
+#pragma unroll
+    for (int cc = 0; cc < C; ++cc) {
+      const int r = lane + 32 * cc;
+      if (r < h) {
+        const float v = __fmul_rn(c, __fadd_rn(sacc[cc], eacc[cc]));
+        out[r] = v;
+        s_row[r] = v;
+      }
+    }
+    __syncwarp();
+    if (gamma) {
+      auto xpos = [&](int k) { return positive_part_smem(s_row, Q, (r0 + k) % Q); };
+      double g;
+      int sc;
+      long long tot;
+      warp_row_cdf(xpos, n_M, log2_nM, lane, cdf + (size_t)row * n_M, g, sc, tot);
+      if (lane == 0) {
+        gamma[row] = g;
+        const unsigned long long thr = g > 0.0 ? event_threshold(g, dt, flags) : 0ull;
+        gthr[row] = thr;
+        thr_cell[i] = thr;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+bool small_window(const wmc_params& p) { return p.Q / 2 <= kRowMaxH; }
+
+static size_t rows_small_smem(int h) {
+  const int C = h <= 32 ? 1 : (h <= 64 ? 2 : 4);
+  return sizeof(float) * ((size_t)(h - 1) * h + (size_t)kRowWarps * 2 * 32 * C);
+}
+
+cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
+                                     int n_occ_host, int max_rows, const float* B, float* VWh, long long* cdf,
+                                     double* gamma, unsigned long long* gthr, unsigned long long* thr_cell,
+                                     unsigned int* flags, cudaStream_t s) {
+  if (max_rows <= 0) return cudaSuccess;
+  const Layout L = layout(p);
+  const int h = L.h;
+  const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
+  const size_t sm = rows_small_smem(h);
+  int blocks = (max_rows + kRowWarps - 1) / kRowWarps;
+  if (blocks > 2 * num_sms()) blocks = 2 * num_sms();
+  const int lg = ceil_log2(p.n_M);
+#define WMC_LAUNCH_ROWS(CC)                                                                                         \
+  do {                                                                                                              \
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_kernel_rows_small<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)sm);                                                              \
+    k_kernel_rows_small<CC><<<blocks, kRowWarps * 32, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, p.n_M, lg, occ,       \
+                                                               n_occ_dev, n_occ_host, B, L.Np, c, VWh, cdf, gamma,  \
+                                                               gthr, thr_cell, flags, p.dt_s);                      \
+  } while (0)
+  if (h <= 32) WMC_LAUNCH_ROWS(1);
+  else if (h <= 64) WMC_LAUNCH_ROWS(2);
+  else WMC_LAUNCH_ROWS(4);
+#undef WMC_LAUNCH_ROWS
+  return cudaGetLastError();
+}
+
+
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host, int max_rows,
-                       long long* cdf, long long ldk, long long ldr, double* gamma, int* scale,
-                       unsigned long long* gthr, const int* occ, unsigned long long* thr_cell, unsigned int* flags,
-                       cudaStream_t s) {
+                       long long* cdf, double* gamma, int* scale, unsigned long long* gthr, const int* occ,
+                       unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s) {
   if (max_rows <= 0) return cudaSuccess;
   k_cdf<<<(max_rows + kCdfWarps - 1) / kCdfWarps, kCdfWarps * 32, 0, s>>>(
-      p.n_M, p.Q, ceil_log2(p.n_M), VWh, n_rows_dev, n_rows_host, cdf, ldk, ldr, gamma, scale, gthr, occ, thr_cell,
-      flags, p.dt_s);
+      p.n_M, p.Q, ceil_log2(p.n_M), VWh, n_rows_dev, n_rows_host, cdf, gamma, scale, gthr, occ, thr_cell, flags,
+      p.dt_s);
   return cudaGetLastError();
 }
 

@@ -23,8 +23,7 @@ struct StepArgs {
   const unsigned long long* R;
   const int2* items;
   const int* row_map;
-  const long long* cdf;  // [n_M][ld] fixed-point CDF
-  long long ld;
+  const long long* cdf;  // [rows][n_M] fixed-point CDF
   const unsigned long long* thr_cell;
   const uint32_t* xlo;
   const uint32_t* xhi;
@@ -35,7 +34,7 @@ struct StepArgs {
 };
 
 // Loads the signed counts of cell i into s_n and their exclusive prefix of
-// |n| into s_pre[0..n_M] (s_pre[n_M] = survivors of the cell).
+// |n| into s_pre[0..n_M] (s_pre[n_M] = survivors of the cell), block-wide.
 __device__ __forceinline__ void load_row_prefix(const int32_t* __restrict__ hist, int i, int n_M, int* s_n,
                                                 int* s_pre, int* s_wsum) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -75,6 +74,33 @@ __device__ __forceinline__ void load_row_prefix(const int32_t* __restrict__ hist
   if (tid == kStepThreads - 1) s_pre[n_M] = s_wsum[kStepThreads / 32 - 1];
 }
 
+// The same, by one warp (lane l takes the contiguous columns [l E, (l+1) E)).
+__device__ __forceinline__ void warp_row_prefix(const int32_t* __restrict__ hist, int i, int n_M, int* s_n,
+                                                int* s_pre, int lane) {
+  const int E = (n_M + 31) >> 5;
+  const int k0 = min(lane * E, n_M), k1 = min(k0 + E, n_M);
+  const int32_t* row = hist + (size_t)i * n_M;
+  int local = 0;
+  for (int k = k0; k < k1; ++k) {
+    const int n = __ldg(row + k);
+    s_n[k] = n;
+    local += n < 0 ? -n : n;
+  }
+  int incl = local;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += u;
+  }
+  int excl = incl - local;
+  for (int k = k0; k < k1; ++k) {
+    s_pre[k] = excl;
+    const int n = s_n[k];
+    excl += n < 0 ? -n : n;
+  }
+  if (lane == 31) s_pre[n_M] = incl;
+}
+
 // Largest k with s_pre[k] <= lid (so s_pre[k] <= lid < s_pre[k+1]).
 __device__ __forceinline__ int bucket_of(const int* s_pre, int n_M, int lid) {
   int lo = 0, hi = n_M;
@@ -89,13 +115,13 @@ __device__ __forceinline__ int bucket_of(const int* s_pre, int n_M, int lid) {
 // Qtot = C[n_M - 1], and the smallest k with C[k] > target (always exists,
 // since target < Qtot).
 __device__ __forceinline__ int sample_momentum(const StepArgs& a, int orow, unsigned long long U2) {
-  const long long* c = a.cdf + orow;
-  const unsigned long long Qtot = (unsigned long long)__ldg(c + (long long)(a.n_M - 1) * a.ld);
+  const long long* c = a.cdf + (size_t)orow * a.n_M;
+  const unsigned long long Qtot = (unsigned long long)__ldg(c + a.n_M - 1);
   const long long target = (long long)((__umul64hi(U2, Qtot) << 11) | ((U2 * Qtot) >> 53));
   int lo = 0, hi = a.n_M - 1;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (__ldg(c + (long long)mid * a.ld) > target) hi = mid; else lo = mid + 1;
+    if (__ldg(c + mid) > target) hi = mid; else lo = mid + 1;
   }
   return lo;
 }
@@ -132,7 +158,7 @@ __device__ __forceinline__ void create_pair(const StepArgs& a, uint32_t id, uint
 // Drift direction of column k from its thresholds: +1, -1, or 0 (never moves).
 __device__ __forceinline__ int drift_dir(uint32_t lo, uint32_t hi) { return hi != 0xffffffffu ? 1 : (lo ? -1 : 0); }
 
-__global__ __launch_bounds__(kStepThreads) void k_step(StepArgs a) {
+__global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
   extern __shared__ int smem[];
   const int n_M = a.n_M;
   int* s_pre = smem;                 // n_M + 1
@@ -140,7 +166,7 @@ __global__ __launch_bounds__(kStepThreads) void k_step(StepArgs a) {
   int* s_acc = s_n + n_M;            // 3 n_M: rows i-1, i, i+1
   uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_acc + 3 * n_M);  // n_M
   uint32_t* s_hi = s_lo + n_M;                                     // n_M
-  __shared__ int s_wsum[kStepThreads / 32];
+  __shared__ int s_item;
   __shared__ unsigned long long s_red[5][kStepThreads / 32];
 
   const int tid = threadIdx.x, lane = tid & 31;
@@ -154,16 +180,20 @@ __global__ __launch_bounds__(kStepThreads) void k_step(StepArgs a) {
   unsigned long long pairs = 0, absorbed = 0, dropped = 0;
   long long abs_signed = 0, drop_signed = 0;
 
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+  for (;;) {
+    // items are handed out in order to whichever block is free
+    if (tid == 0) s_item = (int)atomicAdd(&a.hdr->item_ticket, 1u);
+    __syncthreads();  // also: the previous item is flushed
+    const int item = s_item;
+    if (item >= n_items) break;
     const int2 it = __ldg(a.items + item);
     const int i = it.x, ch = it.y;
     const uint32_t base = (uint32_t)__ldg(a.R + i);
     const unsigned long long thr_m = i > 0 ? __ldg(a.thr_cell + i - 1) : 0ull;
     const unsigned long long thr_0 = __ldg(a.thr_cell + i);
     const unsigned long long thr_p = i + 1 < a.n_x ? __ldg(a.thr_cell + i + 1) : 0ull;
-    __syncthreads();  // the previous item is flushed
     for (int q = tid; q < 3 * n_M; q += kStepThreads) s_acc[q] = 0;
-    load_row_prefix(a.hist_in, i, n_M, s_n, s_pre, s_wsum);
+    if ((tid >> 5) == 0) warp_row_prefix(a.hist_in, i, n_M, s_n, s_pre, lane);
     __syncthreads();
 
     const uint32_t Ti = (uint32_t)s_pre[n_M];
@@ -291,6 +321,15 @@ __global__ __launch_bounds__(kStepThreads) void k_step(StepArgs a) {
     }
   }
   if (blockIdx.x == 0 && tid == 0 && n_items > 0) atomicAdd(&a.hdr->particle_steps, a.hdr->population);
+  if (tid == 0) {
+    // the last block to finish re-arms the item tickets for the next launch
+    __threadfence();
+    if (atomicAdd(&a.hdr->blocks_done, 1u) == gridDim.x - 1) {
+      a.hdr->item_ticket = 0u;
+      a.hdr->blocks_done = 0u;
+      __threadfence();
+    }
+  }
 }
 
 static size_t step_smem(int n_M) { return sizeof(int) * (size_t)(n_M + 1 + n_M + 3 * n_M) + 2 * sizeof(uint32_t) * n_M; }
@@ -325,7 +364,6 @@ cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_
   a.items = v.items;
   a.row_map = v.row_map;
   a.cdf = v.cdf;
-  a.ld = layout(p).ld;
   a.thr_cell = v.thr_cell;
   a.xlo = v.xlo;
   a.xhi = v.xhi;
