@@ -52,6 +52,7 @@ Layout layout(const wmc_params& p) {
   L.max_items = kMaxItemsBase + 2 * (long long)nx;
   L.items = o; o = align256(o + sizeof(int2) * (size_t)L.max_items);
   L.B = o; o = align256(o + sizeof(float) * (size_t)L.Kp * (size_t)L.Np);
+  L.tc = o; o = align256(o + tc_images_bytes(p));
   L.total = o;
   return L;
 }
@@ -77,6 +78,7 @@ View view(const wmc_params& p, void* ws) {
   v.thr_cell = reinterpret_cast<unsigned long long*>(b + L.thr_cell);
   v.items = reinterpret_cast<int2*>(b + L.items);
   v.B = reinterpret_cast<float*>(b + L.B);
+  v.tc = b + L.tc;
   return v;
 }
 
@@ -107,9 +109,22 @@ __global__ void k_reset_counters(DevHeader* hdr) {
 
 static wmc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WMC_OK : WMC_ERR_CUDA; }
 
+static bool prec_supported(wmc_precision prec) {
+  return prec == WMC_FP32 || prec == WMC_BF16 || prec == WMC_FP16 || prec == WMC_FP16_SPLIT;
+}
+
 // Kernel rows, CDFs and thresholds of the occupied list in the workspace:
-// fused for small windows, tiled contraction + CDF kernel otherwise.
-static cudaError_t kernel_and_cdf_occupied(const wmc_params& p, const View& v, const float* V, cudaStream_t s) {
+// tensor-core contraction + CDF kernel for the reduced-precision forms; for
+// FP32, fused for small windows, tiled contraction + CDF kernel otherwise.
+static cudaError_t kernel_and_cdf_occupied(const wmc_params& p, const View& v, const float* V, wmc_precision prec,
+                                           cudaStream_t s) {
+  if (prec != WMC_FP32) {
+    cudaError_t e = launch_kernel_eval_tc(p, (int)prec, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.tc, v.VWh,
+                                          &v.hdr->flags, s);
+    if (e != cudaSuccess) return e;
+    return launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
+                      &v.hdr->flags, s);
+  }
   if (small_window(p))
     return launch_kernel_rows_small(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, v.cdf, v.gamma, v.gthr,
                                     v.thr_cell, &v.hdr->flags, s);
@@ -125,8 +140,7 @@ static wmc_status one_step(const wmc_params& p, const View& v, const float* V, c
   const Layout L = layout(p);
   cudaError_t e = launch_plan(p, v, in, nullptr, device_step, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
-  (void)prec;
-  e = kernel_and_cdf_occupied(p, v, V, s);
+  e = kernel_and_cdf_occupied(p, v, V, prec, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
   e = cudaMemsetAsync(out, 0, sizeof(int32_t) * (size_t)p.n_x * (size_t)p.n_M, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
@@ -181,7 +195,9 @@ wmc_status wmc_init(const wmc_params* p, void* ws, size_t ws_bytes, wmc_stream_t
   const View v = view(*p, ws);
   (void)num_sms();
   prepare_step(*p);
-  return cuda_status(launch_init_tables(*p, v, (cudaStream_t)stream));
+  cudaError_t e = launch_init_tables(*p, v, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = launch_init_tc_images(*p, v.tc, (cudaStream_t)stream);
+  return cuda_status(e);
 }
 
 wmc_status wmc_reset_counters(const wmc_params* p, void* ws, wmc_stream_t stream) {
@@ -216,9 +232,12 @@ wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* o
 wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
                            wmc_precision prec, float* VWh, void* ws, wmc_stream_t stream) {
   if (!params_ok(p) || !V || !ws || n_occ < 0 || (n_occ > 0 && (!occ || !VWh))) return WMC_ERR_ARG;
-  if (prec != WMC_FP32) return WMC_ERR_UNSUPPORTED;
+  if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   if (n_occ == 0) return WMC_OK;
   const View v = view(*p, ws);
+  if (prec != WMC_FP32)
+    return cuda_status(launch_kernel_eval_tc(*p, (int)prec, V, occ, nullptr, n_occ, n_occ, v.tc, VWh, &v.hdr->flags,
+                                             (cudaStream_t)stream));
   if (small_window(*p))
     return cuda_status(launch_kernel_rows_small(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, nullptr, nullptr,
                                                 nullptr, nullptr, nullptr, (cudaStream_t)stream));
@@ -242,10 +261,9 @@ wmc_status wmc_annihilate(const wmc_params* p, const int32_t* hist, int64_t* rho
 wmc_status wmc_kernel_eval_occupied(const wmc_params* p, const float* V, wmc_precision prec, void* ws,
                                     wmc_stream_t stream) {
   if (!params_ok(p) || !V || !ws) return WMC_ERR_ARG;
-  if (prec != WMC_FP32) return WMC_ERR_UNSUPPORTED;
+  if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   const View v = view(*p, ws);
-  const Layout L = layout(*p);
-  return cuda_status(kernel_and_cdf_occupied(*p, v, V, (cudaStream_t)stream));
+  return cuda_status(kernel_and_cdf_occupied(*p, v, V, prec, (cudaStream_t)stream));
 }
 
 wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, void* ws, wmc_stream_t stream) {
@@ -274,7 +292,7 @@ wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t
                    int32_t n_steps, wmc_precision prec, int32_t use_graph, void* ws, wmc_stream_t stream) {
   if (!params_ok(p) || !V || !hist_a || !hist_b || hist_a == hist_b || !ws || n_steps < 0 || t_first == 0)
     return WMC_ERR_ARG;
-  if (prec != WMC_FP32) return WMC_ERR_UNSUPPORTED;
+  if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   if (n_steps == 0) return WMC_OK;
   const View v = view(*p, ws);
   cudaStream_t s = (cudaStream_t)stream;

@@ -57,7 +57,7 @@ struct DevHeader {
 
 // Byte offsets of the workspace regions (all 256-aligned).
 struct Layout {
-  size_t header, T, R, IP, reach, occ, row_map, VWh, cdf, gamma, gthr, thr_cell, D, xlo, xhi, items, B, total;
+  size_t header, T, R, IP, reach, occ, row_map, VWh, cdf, gamma, gthr, thr_cell, D, xlo, xhi, items, B, tc, total;
   long long max_items;
   int h;     // Q / 2
   int Kp;    // contraction length h - 1 padded to a multiple of 32
@@ -86,6 +86,7 @@ struct View {
   uint32_t* xhi;           // [n_M] ... crosses right iff w > xhi[k]
   int2* items;             // [max_items] work items (cell, chunk)
   float* B;                // [Kp][Np] sine matrix S[m][r], m = kk + 1
+  void* tc;                // tensor-core operand images of S (BF16, FP16 hi, FP16 lo)
 };
 View view(const wmc_params& p, void* ws);
 
@@ -129,6 +130,12 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
                                      unsigned int* flags, cudaStream_t s);
 cudaError_t launch_gather_table(const wmc_params& p, const float* table, const int* occ, const int* n_occ_dev,
                                 int max_rows, float* VWh, cudaStream_t s);
+// Tensor-core contraction (BF16, FP16, FP16 hi/lo split).
+size_t tc_images_bytes(const wmc_params& p);
+cudaError_t launch_init_tc_images(const wmc_params& p, void* images, cudaStream_t s);
+cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V, const int* occ, const int* n_occ_dev,
+                                  int n_occ_host, int max_rows, const void* images, float* VWh, unsigned int* flags,
+                                  cudaStream_t s);
 // CDF of rows, row-major cdf[row][n_M]; cdf/scale/gthr/thr_cell/flags may be null.
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host,
                        int max_rows, long long* cdf, double* gamma, int* scale, unsigned long long* gthr,

@@ -1,0 +1,94 @@
+"""Precision forms of the kernel contraction on the tcgen05 tensor cores,
+against the FP64 oracle (normwise error, reading 13), and the FP32 form.
+
+Expected input-rounding errors (numpy estimates at Q = 1024): BF16 about 3-6e-3,
+FP16 about 2e-4, FP16 hi/lo split at the FP32 level (the 1e-6 bar)."""
+import numpy as np
+import pytest
+
+import oracle
+import wmc_inputs as wi
+from tests._util import normwise
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16": 1.5e-2, "fp16": 1e-3, "fp16_split": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def wmc():
+    from paper_1806_00082_gb300 import build, wmc as w
+    build.build()
+    w.load()
+    return w
+
+
+def _cells(wl, n, seed):
+    rng = np.random.default_rng(seed)
+    c = np.concatenate([rng.integers(0, wl.n_x, n - 8), [0, wl.n_x - 1, wl.n_x // 2, wl.n_x // 2,
+                                                         1, 2, wl.n_x - 2, wl.n_x // 3]])
+    return c.astype(np.int32)
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16", "fp16_split"])
+@pytest.mark.parametrize("wl,n", [(wi.BARRIER_100, 100), (wi.BARRIER_2000, 333), (wi.DOUBLE_BARRIER_16384, 333)])
+def test_tensorcore_forms_vs_fp64(wmc, form, wl, n):
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    cells = _cells(wl, n, 17) if wl.n_x > 100 else np.arange(wl.n_x, dtype=np.int32)
+    if wl.n_x > 2000:  # concentrate on the barrier region
+        cells[:200] = np.arange(8192 - 100, 8192 + 100)
+    occ = torch.from_numpy(cells).cuda()
+    got = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), occ, ws, prec=wmc.PRECISIONS[form]).cpu().numpy()
+    ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, cells)[:, wl.Q // 2:]
+    err = normwise(got, ref)
+    assert np.all(np.isfinite(got))
+    assert err <= TOL[form], (form, wl.name, err)
+    assert wmc.get_counters(p, ws)["flags"] == 0
+
+
+def test_tensorcore_ragged_rows_and_tiles(wmc):
+    """Row counts around the 128-row tile and an empty list."""
+    wl = wi.DOUBLE_BARRIER_16384
+    p = wmc.Params.of(wl)
+    V = torch.from_numpy(wi.potential(wl)).cuda()
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    for n in (0, 1, 127, 128, 129, 300):
+        cells = (np.arange(n) * 37 + 8000) % wl.n_x
+        occ = torch.from_numpy(cells.astype(np.int32)).cuda()
+        out = torch.full((n, wl.Q // 2), 3.0, device="cuda")
+        wmc.kernel_eval(p, V, occ, ws, prec=wmc.FP16_SPLIT, out=out)
+        if n:
+            ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), wi.potential(wl), cells)[:, wl.Q // 2:]
+            assert normwise(out.cpu().numpy(), ref) <= TOL["fp16_split"]
+
+
+def test_tensorcore_in_production_loop(wmc):
+    """wmc_run with the BF16 and split kernels: the CDF and the step consume
+    the tensor-core rows; densities stay close to the FP64 oracle under common
+    random numbers (BF16 within its kernel error, split within the FP32 bar)."""
+    from tests._util import gpu_run
+    wl = wi.BARRIER_100
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    h0 = wi.initial_histogram(wl)
+    ref, _ = oracle.simulate(oracle.params(wl), h0, 1, 50, V=V)
+    for form, tol in (("fp16_split", 1e-3), ("bf16", 2e-2)):
+        ws = wmc.workspace(p)
+        wmc.init(p, ws)
+        Vd = torch.from_numpy(V).cuda()
+        a = torch.from_numpy(h0).cuda()
+        b = torch.empty_like(a)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            wmc.run(p, Vd, a, b, 1, 50, ws, prec=wmc.PRECISIONS[form])
+            c = wmc.get_counters(p, ws)
+        s.synchronize()
+        got = a.cpu().numpy()
+        l1 = np.abs(got.sum(axis=1) - ref.sum(axis=1)).sum() / wl.packet.n0
+        assert l1 <= tol, (form, l1)
+        assert c["flags"] == 0
