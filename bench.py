@@ -325,30 +325,50 @@ def end_to_end(wmc, torch, p, V, ws, stream, h0, t0, n=10):
 
 
 def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
+    """The contraction on all 16384 cells of the double barrier (Q = n_M = 1024)
+    in each precision form, timed alone with events (L2 flushed before each
+    launch).  Algorithmic work: 2 (h-1)^2 flop per cell (distinct columns); the
+    split form issues three products per output (pipe work 3x)."""
+    peaks, src = _peaks()
     w = wi.DOUBLE_BARRIER_16384
     p = wmc.Params.of(w)
     V = torch.from_numpy(wi.potential(w)).to(dev)
     ws = wmc.workspace(p, dev)
     occ = torch.arange(w.n_x, dtype=torch.int32, device=dev)
     out = torch.empty((w.n_x, w.Q // 2), dtype=torch.float32, device=dev)
-    with torch.cuda.stream(stream):
-        wmc.init(p, ws)
-        for _ in range(3):
-            wmc.kernel_eval(p, V, occ, ws, out=out)
-        tot = 0.0
-        for _ in range(reps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            wmc.kernel_eval(p, V, occ, ws, out=out)
-            e1.record(stream)
-            stream.synchronize()
-            tot += e0.elapsed_time(e1) * 1e-3
-    sec = tot / reps
     h = w.Q // 2
     flops = 2.0 * w.n_x * (h - 1) ** 2
-    return {"workload": f"{w.name}, all {w.n_x} cells", "prec": "fp32", "cellM_per_s": w.n_x * w.n_M / sec,
-            "seconds": sec, "tflops_algorithmic": flops / sec / 1e12, "err_bound_normwise": 1e-6}
+    # normwise error bounds asserted by tests/test_gpu_parity.py and tests/test_gpu_tensorcore.py
+    bounds = {"fp32": 1e-6, "bf16": 1.5e-2, "fp16": 1e-3, "fp16_split": 1e-6}
+    res = {}
+    with torch.cuda.stream(stream):
+        wmc.init(p, ws)
+        for form in ("fp32", "bf16", "fp16", "fp16_split"):
+            prec = wmc.PRECISIONS[form]
+            for _ in range(3):
+                wmc.kernel_eval(p, V, occ, ws, prec=prec, out=out)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                wmc.kernel_eval(p, V, occ, ws, prec=prec, out=out)
+                e1.record(stream)
+                stream.synchronize()
+                tot += e0.elapsed_time(e1) * 1e-3
+            sec = tot / reps
+            r = {"seconds": sec, "cellM_per_s": w.n_x * w.n_M / sec, "tflops_algorithmic": flops / sec / 1e12,
+                 "err_bound_normwise": bounds[form]}
+            if form == "fp32":
+                r["bound"] = "fp32 pipe (SIMT)"
+            else:
+                issued = flops * (3 if form == "fp16_split" else 1)
+                peak = peaks["bf16_tflops"] * 1e12
+                r["roofline"] = {"bound": "tensor", "achieved": issued / sec / 1e12, "peak": peak / 1e12,
+                                 "unit": "TFLOP/s", "frac": issued / sec / peak, "traffic": None,
+                                 "peak_source": f"{src} bf16 dense (fp16 same rate)"}
+            res[form] = r
+    return {"workload": f"{w.name}, all {w.n_x} cells, n_M = {w.n_M}", "forms": res}
 
 
 def main():

@@ -229,6 +229,47 @@ wmc_status wmc_step(const wmc_params* p, const int32_t* hist_in, uint32_t t, int
 wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t* hist_b, uint32_t t_first,
                    int32_t n_steps, wmc_precision prec, int32_t use_graph, void* ws, wmc_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: n_sims independent simulations of uneven size (each with its
+ * own wmc_params, potential, net histogram and Philox stream, counter word 3 =
+ * its sim field) advanced together, one launch per phase for the whole batch.
+ * Each simulation's result is bit-identical to running it alone.  Supported
+ * for the FP32 kernel and Q <= 256.  Concatenated buffers: the potentials
+ * V [dev] float[sum n_x] and histograms [dev] int32[sum n_x n_M], simulation s
+ * at the offsets wmc_batch_layout returns.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of batch workspace (0 if any parameter set is invalid or Q > 256). */
+size_t wmc_batch_workspace_size(const wmc_params* ps, int32_t n_sims);
+
+/* Offsets of simulation s in the concatenated potentials (cell_off[s]) and
+ * histograms (hist_off[s]); both [host] int64[n_sims + 1], the last entry is
+ * the total. */
+wmc_status wmc_batch_layout(const wmc_params* ps, int32_t n_sims, int64_t* cell_off, int64_t* hist_off);
+
+/* Fills the batch workspace (descriptors, tables, counters).  Synchronises the
+ * stream once (it copies the per-simulation descriptors from the host). */
+wmc_status wmc_batch_init(const wmc_params* ps, int32_t n_sims, void* ws, size_t ws_bytes, wmc_stream_t stream);
+
+/* n_steps steps of every simulation from hist_a (state after step
+ * t_first - 1), hist_b the second buffer, final state in hist_a.
+ * per_thread: survivor ids per thread of a work item (4, 8, 16, 32 or 64; 0 =
+ * 16), e.g. from wmc_batch_autotune; results do not depend on it.  use_graph
+ * as for wmc_run. */
+wmc_status wmc_batch_run(const wmc_params* ps, int32_t n_sims, const float* V, int32_t* hist_a, int32_t* hist_b,
+                         uint32_t t_first, int32_t n_steps, int32_t per_thread, int32_t use_graph, void* ws,
+                         wmc_stream_t stream);
+
+/* Times one batch step from hist (left unchanged; scratch [dev] receives the
+ * output) for each candidate work-item size and writes the fastest to
+ * *best_per_thread [host].  Synchronises. */
+wmc_status wmc_batch_autotune(const wmc_params* ps, int32_t n_sims, const float* V, int32_t* hist, int32_t* scratch,
+                              uint32_t t, void* ws, int32_t* best_per_thread, wmc_stream_t stream);
+
+/* Counters of the batch (totals over all simulations); synchronises. */
+wmc_status wmc_batch_get_counters(const wmc_params* ps, int32_t n_sims, const void* ws, wmc_counters* out,
+                                  wmc_stream_t stream);
+
 /* Rule 1: rho[i] = sum_k hist[i][k].  hist [dev] int32[n_x][n_M], rho [dev] int64[n_x]. */
 wmc_status wmc_density(const wmc_params* p, const int32_t* hist, int64_t* rho, wmc_stream_t stream);
 

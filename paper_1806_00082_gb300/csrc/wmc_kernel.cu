@@ -8,24 +8,9 @@
 //   S[m][r]     = sin(2 pi (m r mod Q) / Q)          (precomputed matrix B)
 #include <math.h>
 
-#include "wmc_internal.cuh"
+#include "wmc_device.cuh"
 
 namespace wmc {
-
-__device__ __forceinline__ float pot(const float* __restrict__ V, int n_x, int bc, long long l) {
-  if (l >= 0 && l < n_x) return __ldg(V + l);
-  if (!bc) return 0.f;
-  return __ldg(V + (l < 0 ? 0 : n_x - 1));
-}
-
-// Error-free transformation of a + b (Knuth's TwoSum): s + e == a + b exactly.
-__device__ __forceinline__ void two_sum_acc(float& s, float& e, float p) {
-  const float sn = __fadd_rn(s, p);
-  const float bp = __fsub_rn(sn, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bp)), __fsub_rn(p, bp));
-  s = sn;
-  e = __fadd_rn(e, err);
-}
 
 // ---------------------------------------------------------------- FP32 SIMT contraction
 // Tile BM x BN outputs per block of 256 threads (4 x 4 per thread), K chunks of
@@ -151,101 +136,7 @@ cudaError_t launch_gather_table(const wmc_params& p, const float* table, const i
 // gamma = fl64(C[n_M-1] 2^-s).  gthr[row] = ceil(fl64(gamma dt) 2^32): for a
 // 32-bit word w, w < gthr  <=>  w 2^-32 < gamma dt.
 
-// x 2^s rounded to the nearest integer (ties to even), from the bits of x >= 0.
-__device__ __forceinline__ long long quantise(float x, int s) {
-  const uint32_t b = __float_as_uint(x);
-  if (b == 0u) return 0;
-  const uint32_t E = b >> 23;
-  uint32_t m = b & 0x7fffffu;
-  int ex = -149;                 // value = m 2^ex
-  if (E) {
-    m |= 0x800000u;
-    ex = (int)E - 150;
-  }
-  const int sh = ex + s;
-  if (sh >= 0) return (long long)((unsigned long long)m << sh);
-  const int r = -sh;
-  if (r > 25) return 0;          // m < 2^24: below half a unit
-  const uint32_t q = m >> r;
-  const uint32_t rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
-  return (long long)(q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u));
-}
-
-__device__ __forceinline__ int floor_log2_pos(float x) {  // x > 0
-  const uint32_t b = __float_as_uint(x);
-  const uint32_t E = b >> 23;
-  if (E) return (int)E - 127;
-  return (31 - __clz(b & 0x7fffffu)) - 149;
-}
-
-__device__ __forceinline__ float positive_part(const float* __restrict__ v, int Q, int r) {
-  const int h = Q / 2;
-  float x = 0.f;
-  if (r != 0 && r != h) x = r < h ? __ldg(v + r) : -__ldg(v + (Q - r));
-  return x > 0.f ? x : 0.f;
-}
-
-__device__ __forceinline__ float positive_part_smem(const float* v, int Q, int r) {
-  const int h = Q / 2;
-  float x = 0.f;
-  if (r != 0 && r != h) x = r < h ? v[r] : -v[Q - r];
-  return x > 0.f ? x : 0.f;
-}
-
 constexpr int kCdfWarps = 8;
-
-// The fixed-point CDF of one row held in a warp: lane l takes the contiguous
-// columns k in [l E, (l+1) E), E = ceil(n_M / 32), so a row needs one warp
-// reduction (maximum), one warp scan of the lane totals and E sequential
-// integer additions per lane; lanes write contiguous runs of the row-major CDF.
-// xpos(k) returns max(V_W(k), 0) for column k.
-template <class XPos>
-__device__ __forceinline__ void warp_row_cdf(XPos xpos, int n_M, int log2_nM, int lane, long long* __restrict__ out,
-                                             double& gamma_out, int& scale_out, long long& total_out) {
-  const int E = (n_M + 31) >> 5;
-  const int k0 = lane * E, k1 = min(k0 + E, n_M);
-  uint32_t mx = 0u;
-  for (int k = k0; k < k1; ++k) mx = max(mx, __float_as_uint(xpos(k)));
-  mx = __reduce_max_sync(0xffffffffu, mx);
-  if (mx == 0u) {
-    if (out)
-      for (int k = k0; k < k1; ++k) out[k] = 0;
-    gamma_out = 0.0;
-    scale_out = 0;
-    total_out = 0;
-    return;
-  }
-  const int s = 61 - log2_nM - floor_log2_pos(__uint_as_float(mx));
-  long long local = 0;
-  for (int k = k0; k < k1; ++k) local += quantise(xpos(k), s);
-  long long incl = local;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const long long u = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += u;
-  }
-  const long long total = __shfl_sync(0xffffffffu, incl, 31);
-  if (out) {
-    long long run = incl - local;
-    for (int k = k0; k < k1; ++k) {
-      run += quantise(xpos(k), s);
-      out[k] = run;
-    }
-  }
-  gamma_out = ldexp((double)total, -s);
-  scale_out = s;
-  total_out = total;
-}
-
-// gthr = ceil(fl64(gamma dt) 2^32), flagging gamma dt >= 1.
-__device__ __forceinline__ unsigned long long event_threshold(double g, double dt, unsigned int* flags) {
-  const double gd = __dmul_rn(g, dt);
-  if (gd >= 1.0) {
-    atomicOr(flags, WMC_FLAG_RATE);
-    return 1ull << 32;
-  }
-  return (unsigned long long)ceil(gd * 4294967296.0);
-}
 
 __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2_nM, const float* __restrict__ VWh,
                                                        const int* __restrict__ n_rows_dev, int n_rows_host,

@@ -2,22 +2,11 @@
 // kernel, density (rule 1), constant tables and the Philox check kernel.
 #include <math.h>
 
-#include "wmc_internal.cuh"
+#include "wmc_device.cuh"
 
 namespace wmc {
 
 // ---------------------------------------------------------------- constant tables
-// Smallest j in [0, 2^24] with fl32(j 2^-24 + d) >= edge (2^24 if none); the
-// predicate is monotone in j because rounding is.
-__device__ int first_offset_reaching(float d, float edge) {
-  int lo = 0, hi = 1 << 24;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (__fadd_rn((float)mid * 0x1p-24f, d) >= edge) hi = mid; else lo = mid + 1;
-  }
-  return lo;
-}
-
 // D[k] = fl32(M * d1), d1 = hbar pi dt / (m Q dx^2), M = k - n_M/2: the free
 // drift of momentum M dp over dt, in cells.  Crossing thresholds on the offset
 // word w (f = (w >> 8) 2^-24): a particle of column k moves right iff

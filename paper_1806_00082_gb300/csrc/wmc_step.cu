@@ -13,7 +13,7 @@
 // bucket.  A particle moves iff its offset word passes the integer threshold
 // of its momentum column, so a quad of ids inside one bucket costs one Philox
 // call and a handful of compares.
-#include "wmc_internal.cuh"
+#include "wmc_device.cuh"
 
 namespace wmc {
 
@@ -74,56 +74,8 @@ __device__ __forceinline__ void load_row_prefix(const int32_t* __restrict__ hist
   if (tid == kStepThreads - 1) s_pre[n_M] = s_wsum[kStepThreads / 32 - 1];
 }
 
-// The same, by one warp (lane l takes the contiguous columns [l E, (l+1) E)).
-__device__ __forceinline__ void warp_row_prefix(const int32_t* __restrict__ hist, int i, int n_M, int* s_n,
-                                                int* s_pre, int lane) {
-  const int E = (n_M + 31) >> 5;
-  const int k0 = min(lane * E, n_M), k1 = min(k0 + E, n_M);
-  const int32_t* row = hist + (size_t)i * n_M;
-  int local = 0;
-  for (int k = k0; k < k1; ++k) {
-    const int n = __ldg(row + k);
-    s_n[k] = n;
-    local += n < 0 ? -n : n;
-  }
-  int incl = local;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += u;
-  }
-  int excl = incl - local;
-  for (int k = k0; k < k1; ++k) {
-    s_pre[k] = excl;
-    const int n = s_n[k];
-    excl += n < 0 ? -n : n;
-  }
-  if (lane == 31) s_pre[n_M] = incl;
-}
-
-// Largest k with s_pre[k] <= lid (so s_pre[k] <= lid < s_pre[k+1]).
-__device__ __forceinline__ int bucket_of(const int* s_pre, int n_M, int lid) {
-  int lo = 0, hi = n_M;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (s_pre[mid] <= lid) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// Index of p' for the 53-bit uniform integer U2: target = floor(U2 Qtot / 2^53),
-// Qtot = C[n_M - 1], and the smallest k with C[k] > target (always exists,
-// since target < Qtot).
 __device__ __forceinline__ int sample_momentum(const StepArgs& a, int orow, unsigned long long U2) {
-  const long long* c = a.cdf + (size_t)orow * a.n_M;
-  const unsigned long long Qtot = (unsigned long long)__ldg(c + a.n_M - 1);
-  const long long target = (long long)((__umul64hi(U2, Qtot) << 11) | ((U2 * Qtot) >> 53));
-  int lo = 0, hi = a.n_M - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(c + mid) > target) hi = mid; else lo = mid + 1;
-  }
-  return lo;
+  return sample_cdf_row(a.cdf + (size_t)orow * a.n_M, a.n_M, U2);
 }
 
 // A pair created by particle id (column k, sign sgn) that lands in cell c = i - 1 + d:
@@ -154,9 +106,6 @@ __device__ __forceinline__ void create_pair(const StepArgs& a, uint32_t id, uint
     atomicAdd(&s_acc[d * n_M + kc], sc2[q]);
   }
 }
-
-// Drift direction of column k from its thresholds: +1, -1, or 0 (never moves).
-__device__ __forceinline__ int drift_dir(uint32_t lo, uint32_t hi) { return hi != 0xffffffffu ? 1 : (lo ? -1 : 0); }
 
 __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
   extern __shared__ int smem[];

@@ -29,7 +29,8 @@ EXPORTS = (
     "wmc_version", "wmc_status_string", "wmc_workspace_size", "wmc_init", "wmc_reset_counters",
     "wmc_get_counters", "wmc_kernel_eval", "wmc_kernel_cdf", "wmc_annihilate", "wmc_kernel_eval_occupied",
     "wmc_kernel_table_occupied", "wmc_step", "wmc_run", "wmc_density", "wmc_materialize", "wmc_philox4x32_10",
-    "wmc_kernel_eval_noalloc",
+    "wmc_kernel_eval_noalloc", "wmc_batch_workspace_size", "wmc_batch_layout", "wmc_batch_init", "wmc_batch_run",
+    "wmc_batch_autotune", "wmc_batch_get_counters",
 )
 
 
@@ -122,6 +123,12 @@ def load(path: str | None = None):
             "wmc_materialize": ([pp, vp, u32, vp, vp, vp, vp, i64, vp, vp], i32),
             "wmc_philox4x32_10": ([vp, u32, u32, i64, vp, vp], i32),
             "wmc_kernel_eval_noalloc": ([pp, vp, vp, i32, vp, vp], i32),
+            "wmc_batch_workspace_size": ([pp, i32], ctypes.c_size_t),
+            "wmc_batch_layout": ([pp, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], i32),
+            "wmc_batch_init": ([pp, i32, vp, ctypes.c_size_t, vp], i32),
+            "wmc_batch_run": ([pp, i32, vp, vp, vp, u32, i32, i32, i32, vp, vp], i32),
+            "wmc_batch_autotune": ([pp, i32, vp, vp, vp, u32, vp, ctypes.POINTER(ctypes.c_int32), vp], i32),
+            "wmc_batch_get_counters": ([pp, i32, vp, ctypes.POINTER(Counters), vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -258,3 +265,51 @@ def philox4x32_10(ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
     _check("wmc_philox4x32_10", load().wmc_philox4x32_10(_ptr(c), key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF,
                                                          c.shape[0], _ptr(out), _stream()))
     return out
+
+
+# ---------------------------------------------------------------- batched form
+def params_array(ps) -> ctypes.Array:
+    arr = (Params * len(ps))()
+    for q, p in enumerate(ps):
+        arr[q] = p
+    return arr
+
+
+def batch_layout(ps_arr) -> tuple:
+    n = len(ps_arr)
+    co = (ctypes.c_int64 * (n + 1))()
+    ho = (ctypes.c_int64 * (n + 1))()
+    _check("wmc_batch_layout", load().wmc_batch_layout(ps_arr, n, co, ho))
+    return list(co), list(ho)
+
+
+def batch_workspace(ps_arr, device=None) -> torch.Tensor:
+    nbytes = load().wmc_batch_workspace_size(ps_arr, len(ps_arr))
+    if nbytes == 0:
+        raise WmcError("wmc_batch_workspace_size", 1)
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def batch_init(ps_arr, ws: torch.Tensor) -> None:
+    _check("wmc_batch_init", load().wmc_batch_init(ps_arr, len(ps_arr), _ptr(ws), ws.numel(), _stream()))
+
+
+def batch_run(ps_arr, V: torch.Tensor, hist_a: torch.Tensor, hist_b: torch.Tensor, t_first: int, n_steps: int,
+              ws: torch.Tensor, per_thread: int = 0, use_graph: bool = True) -> None:
+    _check("wmc_batch_run", load().wmc_batch_run(ps_arr, len(ps_arr), _ptr(V), _ptr(hist_a), _ptr(hist_b), t_first,
+                                                 n_steps, per_thread, 1 if use_graph else 0, _ptr(ws), _stream()))
+
+
+def batch_autotune(ps_arr, V: torch.Tensor, hist: torch.Tensor, scratch: torch.Tensor, t: int,
+                   ws: torch.Tensor) -> int:
+    best = ctypes.c_int32(0)
+    _check("wmc_batch_autotune", load().wmc_batch_autotune(ps_arr, len(ps_arr), _ptr(V), _ptr(hist), _ptr(scratch),
+                                                           t, _ptr(ws), ctypes.byref(best), _stream()))
+    return best.value
+
+
+def batch_get_counters(ps_arr, ws: torch.Tensor) -> dict:
+    c = Counters()
+    _check("wmc_batch_get_counters", load().wmc_batch_get_counters(ps_arr, len(ps_arr), _ptr(ws), ctypes.byref(c),
+                                                                   _stream()))
+    return c.as_dict()

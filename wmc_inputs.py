@@ -158,3 +158,28 @@ WORKLOADS = {w.name: w for w in (BARRIER_100, BARRIER_2000, DOUBLE_BARRIER_16384
 def scaled(w: Workload, n0: int) -> Workload:
     """The same workload with a different initial particle count."""
     return w.replace(packet=dataclasses.replace(w.packet, n0=n0))
+
+
+def batch_workloads(n_sims: int, seed: int = 2, n_x_range=(200, 4000), n0_range=(10_000, 1_000_000),
+                    dt_s: float = 0.05 * FS, steps: int = 500) -> list:
+    """The batched workload: n_sims independent barrier simulations with
+    per-simulation draws (PCG64 seed `seed`): cells U[n_x_range] at 0.5 nm,
+    n_M in {128, 256} with Q = n_M / 2, barrier height U[0.05, 0.5] eV and
+    width U[2, 20] nm at the domain midpoint, packet energy U[0.05, 0.3] eV at
+    L/4 with sigma = L/20, particle count U[n0_range]; Philox seed 1000 + s and
+    sim index s."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    dx = 0.5 * NM
+    for s in range(n_sims):
+        n_x = int(rng.integers(n_x_range[0], n_x_range[1] + 1))
+        n_M = int(rng.choice([128, 256]))
+        V0 = float(rng.uniform(0.05, 0.5))
+        width = float(rng.uniform(2, 20)) * NM
+        E = float(rng.uniform(0.05, 0.3))
+        n0 = int(rng.integers(n0_range[0], n0_range[1] + 1))
+        L = n_x * dx
+        out.append(Workload(
+            name=f"batch-{s}", n_x=n_x, dx_m=dx, Q=n_M // 2, n_M=n_M, dt_s=dt_s, steps=steps,
+            barriers=(Barrier(V0, width, L / 2),), packet=Packet(L / 4, L / 20, E, n0), seed=1000 + s, sim=s))
+    return out
