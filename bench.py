@@ -220,6 +220,7 @@ def native_arm(args, w):
     e2e = end_to_end(wmc, torch, p, V, ws, stream, h0, t + 4 * n_iter)
     # ---- kernel evaluation throughput, all cells of the 16384-cell double barrier
     kev = kernel_eval_rate(wmc, torch, dev, stream, flush) if rank == 0 else None
+    bat = batched_rate(wmc, torch, dev, stream) if rank == 0 and not args.no_batched else None
 
     if rank != 0:
         if world > 1:
@@ -243,6 +244,7 @@ def native_arm(args, w):
         "roofline": roof,
         "cpu_baseline": cpu,
         "kernel_eval": kev,
+        "batched": bat,
         "counters": {k: c[k] for k in ("pairs", "absorbed", "dropped", "n_occ", "flags")},
     }
     print(json.dumps(line), flush=True)
@@ -371,6 +373,35 @@ def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
     return {"workload": f"{w.name}, all {w.n_x} cells, n_M = {w.n_M}", "forms": res}
 
 
+def batched_rate(wmc, torch, dev, stream, n_sims=512, steps=20, warmup=2):
+    """The batched form: n_sims independent barrier simulations (per-simulation
+    draws, seed 2), all advanced by one launch per phase; particle-steps/s over
+    the batch, work-item size from the autotuner."""
+    wls = wi.batch_workloads(n_sims, seed=2)
+    ps = wmc.params_array([wmc.Params.of(w) for w in wls])
+    co, ho = wmc.batch_layout(ps)
+    V = torch.from_numpy(np.concatenate([wi.potential(w) for w in wls])).to(dev)
+    H = torch.from_numpy(np.concatenate([wi.initial_histogram(w).reshape(-1) for w in wls])).to(dev)
+    ws = wmc.batch_workspace(ps, dev)
+    b = torch.empty_like(H)
+    with torch.cuda.stream(stream):
+        wmc.batch_init(ps, ws)
+        per = wmc.batch_autotune(ps, V, H, b, 1, ws)
+        wmc.batch_run(ps, V, H, b, 1, 2 * warmup, ws, per_thread=per)
+        wmc.batch_init(ps, ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wmc.batch_run(ps, V, H, b, 1 + 2 * warmup, steps, ws, per_thread=per)
+        e1.record(stream)
+        stream.synchronize()
+        c = wmc.batch_get_counters(ps, ws)
+    sec = e0.elapsed_time(e1) * 1e-3
+    return {"workload": f"{n_sims} barrier simulations, cells U[200,4000], n_M in {{128,256}}, N0 U[1e4,1e6]",
+            "value": c["particle_steps"] / sec, "unit": UNIT, "steps": steps, "ms_per_step": 1e3 * sec / steps,
+            "cells": co[-1], "particles_at_start": int(sum(w.packet.n0 for w in wls)), "per_thread": per,
+            "pairs": c["pairs"], "flags": c["flags"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,6 +410,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="barrier-2000", choices=sorted(wi.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = wi.WORKLOADS[args.workload]

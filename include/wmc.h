@@ -270,6 +270,41 @@ wmc_status wmc_batch_autotune(const wmc_params* ps, int32_t n_sims, const float*
 wmc_status wmc_batch_get_counters(const wmc_params* ps, int32_t n_sims, const void* ws, wmc_counters* out,
                                   wmc_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Differentiation form: the kernel rows and gamma as functions of a smooth
+ * potential, and their adjoint.
+ *   V(x) = sum_b h_b T(x; c_b - w_b/2, c_b + w_b/2) + sum_s o_s T(x; s L/ns, (s+1) L/ns),
+ *   T(x; a, b) = (tanh((x - a)/eps) - tanh((x - b)/eps)) / 2,  x = (i + 1/2) dx,
+ * lengths in nm, energies in eV; theta [dev] float[n_pot][3 nb + ns] per
+ * potential = [h_0..h_{nb-1}, w_0.., c_0.., o_0..o_{ns-1}].
+ * ------------------------------------------------------------------------- */
+
+/* V [dev] float[n_pot][n_x] from theta. */
+wmc_status wmc_potential_tanh(const wmc_params* p, const float* theta, int32_t n_pot, int32_t n_barriers,
+                              int32_t n_segments, float eps_nm, float* V, wmc_stream_t stream);
+
+/* theta_bar [dev] float[n_pot][3 nb + ns] = sum_i Vbar[i] dV(x_i)/d theta. */
+wmc_status wmc_potential_tanh_vjp(const wmc_params* p, const float* theta, int32_t n_pot, int32_t n_barriers,
+                                  int32_t n_segments, float eps_nm, const float* Vbar, float* theta_bar,
+                                  wmc_stream_t stream);
+
+/* Kernel rows of every cell of n_pot potentials V [dev] float[n_pot][n_x]:
+ * VWh [dev] float[n_pot * n_x][Q/2] (row b n_x + i = cell i of potential b);
+ * gamma follows from wmc_kernel_cdf on these rows.  Any precision form. */
+wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_pot, wmc_precision prec, float* VWh,
+                                void* ws, wmc_stream_t stream);
+
+/* Adjoint of wmc_kernel_eval_rows and of gamma (Eq. wigner-1d-discrete and
+ * Eq. momentum_integral): for upstream gradients gVW [dev] float[rows][Q/2]
+ * and g_gamma [dev] float[rows] (either may be NULL; rows = n_pot n_x) of the
+ * rows VWh, writes Vbar [dev] float[n_pot][n_x] = dL/dV.
+ *   Gbar = gVW + g_gamma (cnt_pos(r) [VWh > 0] - cnt_neg(r) [VWh < 0]),
+ *   Abar[i][m] = c sum_r Gbar[i][r] S[m][r],  Vbar[l] = sum_m Abar[l-m][m] - Abar[l+m][m],
+ * cnt_pos(r) / cnt_neg(r) = momentum indices M of the grid with M = r / M = -r (mod Q).
+ * Abar [dev] float[rows][Q/2] is caller scratch.  bc_potential 0 and Q <= 256. */
+wmc_status wmc_kernel_vjp(const wmc_params* p, const float* VWh, const float* gVW, const float* g_gamma,
+                          int32_t n_pot, float* Abar, float* Vbar, void* ws, wmc_stream_t stream);
+
 /* Rule 1: rho[i] = sum_k hist[i][k].  hist [dev] int32[n_x][n_M], rho [dev] int64[n_x]. */
 wmc_status wmc_density(const wmc_params* p, const int32_t* hist, int64_t* rho, wmc_stream_t stream);
 

@@ -35,7 +35,10 @@ __global__ __launch_bounds__(256) void k_kernel_eval_fp32(const float* __restric
   // the A rows this thread builds: r = tid & 63, kk = (tid >> 6) + 4 q
   const int ar = tid & 63;
   const int a_row = row0 + ar;
-  const int a_cell = a_row < n_rows ? __ldg(occ + a_row) : 0;
+  // occ == nullptr: implicit rows over consecutive potentials (row r is cell
+  // r % n_x of the potential V + (r / n_x) n_x)
+  const int a_cell = a_row < n_rows ? (occ ? __ldg(occ + a_row) : a_row % n_x) : 0;
+  const float* Va = (occ || a_row >= n_rows) ? V : V + (size_t)(a_row / n_x) * n_x;
 
   float s[4][4], e[4][4];
 #pragma unroll
@@ -49,7 +52,7 @@ __global__ __launch_bounds__(256) void k_kernel_eval_fp32(const float* __restric
       const int kk = (tid >> 6) + 4 * q;
       const int m = k0 + kk + 1;
       float v = 0.f;
-      if (m <= h - 1) v = __fsub_rn(pot(V, n_x, bc, (long long)a_cell + m), pot(V, n_x, bc, (long long)a_cell - m));
+      if (m <= h - 1) v = __fsub_rn(pot(Va, n_x, bc, (long long)a_cell + m), pot(Va, n_x, bc, (long long)a_cell - m));
       As[kk][ar] = v;
     }
 #pragma unroll
@@ -206,11 +209,12 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
   __syncthreads();
   const int r0 = ((-(n_M / 2)) % Q + Q) % Q;
   for (int row = blockIdx.x * kRowWarps + wid; row < n_rows; row += gridDim.x * kRowWarps) {
-    const int i = __ldg(occ + row);
+    const int i = occ ? __ldg(occ + row) : row % n_x;
+    const float* Vr = occ ? V : V + (size_t)(row / n_x) * n_x;
 #pragma unroll
     for (int q = 0; q < C; ++q) {
       const int m = lane + 1 + 32 * q;
-      s_dv[m - 1] = m <= h - 1 ? __fsub_rn(pot(V, n_x, bc, (long long)i + m), pot(V, n_x, bc, (long long)i - m))
+      s_dv[m - 1] = m <= h - 1 ? __fsub_rn(pot(Vr, n_x, bc, (long long)i + m), pot(Vr, n_x, bc, (long long)i - m))
                                : 0.f;
     }
     __syncwarp();
@@ -255,7 +259,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
         gamma[row] = g;
         const unsigned long long thr = g > 0.0 ? event_threshold(g, dt, flags) : 0ull;
         gthr[row] = thr;
-        thr_cell[i] = thr;
+        if (thr_cell) thr_cell[i] = thr;
       }
     }
     __syncwarp();

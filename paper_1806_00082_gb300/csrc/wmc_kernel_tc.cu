@@ -225,7 +225,9 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
   const uint32_t accA = tmem, accB = tmem + (uint32_t)TN, accX = tmem + 2u * (uint32_t)TN;
 
   const int my_row = row0 + tid;
-  const int cell = my_row < n_rows ? __ldg(occ + my_row) : 0;
+  // occ == nullptr: implicit rows over consecutive potentials
+  const int cell = my_row < n_rows ? (occ ? __ldg(occ + my_row) : my_row % n_x) : 0;
+  const float* Vr = (occ || my_row >= n_rows) ? V : V + (size_t)(my_row / n_x) * n_x;
   const int half_kb = (KB + 1) / 2;
   const uint32_t tx_bytes = SPLIT ? 2u * kTileBytes : kTileBytes;
   // sine-matrix images of this column tile: the input-type (or FP16 hi) image
@@ -251,7 +253,7 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
           const int m = kb * TK + k8 * 8 + e + u + 1;
           float dv = 0.f;
           if (m <= h - 1 && my_row < n_rows)
-            dv = __fsub_rn(potential_at(V, n_x, bc, (long long)cell + m), potential_at(V, n_x, bc, (long long)cell - m));
+            dv = __fsub_rn(potential_at(Vr, n_x, bc, (long long)cell + m), potential_at(Vr, n_x, bc, (long long)cell - m));
           hb[u] = to_bits(dv, SPLIT ? WMC_FP16 : PREC);
           if (SPLIT) lb[u] = to_bits(__fmul_rn(__fsub_rn(dv, from_bits(hb[u], WMC_FP16)), 2048.f), WMC_FP16);
         }

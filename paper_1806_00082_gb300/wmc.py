@@ -30,7 +30,8 @@ EXPORTS = (
     "wmc_get_counters", "wmc_kernel_eval", "wmc_kernel_cdf", "wmc_annihilate", "wmc_kernel_eval_occupied",
     "wmc_kernel_table_occupied", "wmc_step", "wmc_run", "wmc_density", "wmc_materialize", "wmc_philox4x32_10",
     "wmc_kernel_eval_noalloc", "wmc_batch_workspace_size", "wmc_batch_layout", "wmc_batch_init", "wmc_batch_run",
-    "wmc_batch_autotune", "wmc_batch_get_counters",
+    "wmc_batch_autotune", "wmc_batch_get_counters", "wmc_potential_tanh", "wmc_potential_tanh_vjp",
+    "wmc_kernel_eval_rows", "wmc_kernel_vjp",
 )
 
 
@@ -129,6 +130,10 @@ def load(path: str | None = None):
             "wmc_batch_run": ([pp, i32, vp, vp, vp, u32, i32, i32, i32, vp, vp], i32),
             "wmc_batch_autotune": ([pp, i32, vp, vp, vp, u32, vp, ctypes.POINTER(ctypes.c_int32), vp], i32),
             "wmc_batch_get_counters": ([pp, i32, vp, ctypes.POINTER(Counters), vp], i32),
+            "wmc_potential_tanh": ([pp, vp, i32, i32, i32, ctypes.c_float, vp, vp], i32),
+            "wmc_potential_tanh_vjp": ([pp, vp, i32, i32, i32, ctypes.c_float, vp, vp, vp], i32),
+            "wmc_kernel_eval_rows": ([pp, vp, i32, i32, vp, vp, vp], i32),
+            "wmc_kernel_vjp": ([pp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -313,3 +318,37 @@ def batch_get_counters(ps_arr, ws: torch.Tensor) -> dict:
     _check("wmc_batch_get_counters", load().wmc_batch_get_counters(ps_arr, len(ps_arr), _ptr(ws), ctypes.byref(c),
                                                                    _stream()))
     return c.as_dict()
+
+
+# ---------------------------------------------------------------- differentiation form
+def potential_tanh(p: Params, theta: torch.Tensor, n_barriers: int, n_segments: int, eps_nm: float) -> torch.Tensor:
+    n_pot = theta.shape[0]
+    V = torch.empty((n_pot, p.n_x), dtype=torch.float32, device=theta.device)
+    _check("wmc_potential_tanh", load().wmc_potential_tanh(ctypes.byref(p), _ptr(theta), n_pot, n_barriers,
+                                                           n_segments, eps_nm, _ptr(V), _stream()))
+    return V
+
+
+def potential_tanh_vjp(p: Params, theta: torch.Tensor, n_barriers: int, n_segments: int, eps_nm: float,
+                       Vbar: torch.Tensor) -> torch.Tensor:
+    tb = torch.empty_like(theta)
+    _check("wmc_potential_tanh_vjp", load().wmc_potential_tanh_vjp(ctypes.byref(p), _ptr(theta), theta.shape[0],
+                                                                   n_barriers, n_segments, eps_nm, _ptr(Vbar),
+                                                                   _ptr(tb), _stream()))
+    return tb
+
+
+def kernel_eval_rows(p: Params, V: torch.Tensor, ws: torch.Tensor, prec: int = FP32) -> torch.Tensor:
+    n_pot = V.shape[0]
+    out = torch.empty((n_pot * p.n_x, p.h), dtype=torch.float32, device=V.device)
+    _check("wmc_kernel_eval_rows", load().wmc_kernel_eval_rows(ctypes.byref(p), _ptr(V), n_pot, prec, _ptr(out),
+                                                               _ptr(ws), _stream()))
+    return out
+
+
+def kernel_vjp(p: Params, VWh: torch.Tensor, gVW, g_gamma, n_pot: int, ws: torch.Tensor) -> torch.Tensor:
+    abar = torch.empty_like(VWh)
+    Vbar = torch.empty((n_pot, p.n_x), dtype=torch.float32, device=VWh.device)
+    _check("wmc_kernel_vjp", load().wmc_kernel_vjp(ctypes.byref(p), _ptr(VWh), _ptr(gVW), _ptr(g_gamma), n_pot,
+                                                   _ptr(abar), _ptr(Vbar), _ptr(ws), _stream()))
+    return Vbar

@@ -183,3 +183,26 @@ def batch_workloads(n_sims: int, seed: int = 2, n_x_range=(200, 4000), n0_range=
             name=f"batch-{s}", n_x=n_x, dx_m=dx, Q=n_M // 2, n_M=n_M, dt_s=dt_s, steps=steps,
             barriers=(Barrier(V0, width, L / 2),), packet=Packet(L / 4, L / 20, E, n0), seed=1000 + s, sim=s))
     return out
+
+
+TANH_BARRIERS_4096 = Workload(
+    name="tanh-barriers-4096", n_x=4096, dx_m=0.25 * NM, Q=256, n_M=512, dt_s=0.05 * FS, steps=1, seed=3)
+
+
+def tanh_parameters(n_pot: int, n_x: int = 4096, dx_nm: float = 0.25, n_barriers: int = 16, n_segments: int = 16,
+                    seed: int = 3) -> np.ndarray:
+    """Parameters [n_pot, 3 nb + ns] (FP32) of the smooth multi-barrier
+    potential: heights U[0.05, 0.3] eV, widths U[1, 5] nm, centres one per
+    1/nb of the domain with a uniform jitter of a quarter of that length,
+    segment offsets U[-0.02, 0.02] eV (PCG64 seed `seed`)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = n_x * dx_nm
+    slot = L / n_barriers
+    th = np.zeros((n_pot, 3 * n_barriers + n_segments))
+    for b in range(n_pot):
+        th[b, :n_barriers] = rng.uniform(0.05, 0.3, n_barriers)
+        th[b, n_barriers:2 * n_barriers] = rng.uniform(1.0, 5.0, n_barriers)
+        th[b, 2 * n_barriers:3 * n_barriers] = (np.arange(n_barriers) + 0.5) * slot + rng.uniform(
+            -slot / 4, slot / 4, n_barriers)
+        th[b, 3 * n_barriers:] = rng.uniform(-0.02, 0.02, n_segments)
+    return th.astype(np.float32)
