@@ -221,6 +221,7 @@ def native_arm(args, w):
     # ---- kernel evaluation throughput, all cells of the 16384-cell double barrier
     kev = kernel_eval_rate(wmc, torch, dev, stream, flush) if rank == 0 else None
     bat = batched_rate(wmc, torch, dev, stream) if rank == 0 and not args.no_batched else None
+    adjo = adjoint_rate(wmc, torch, dev, stream) if rank == 0 and not args.no_batched else None
 
     if rank != 0:
         if world > 1:
@@ -245,6 +246,7 @@ def native_arm(args, w):
         "cpu_baseline": cpu,
         "kernel_eval": kev,
         "batched": bat,
+        "adjoint": adjo,
         "counters": {k: c[k] for k in ("pairs", "absorbed", "dropped", "n_occ", "flags")},
     }
     print(json.dumps(line), flush=True)
@@ -400,6 +402,42 @@ def batched_rate(wmc, torch, dev, stream, n_sims=512, steps=20, warmup=2):
             "value": c["particle_steps"] / sec, "unit": UNIT, "steps": steps, "ms_per_step": 1e3 * sec / steps,
             "cells": co[-1], "particles_at_start": int(sum(w.packet.n0 for w in wls)), "per_thread": per,
             "pairs": c["pairs"], "flags": c["flags"]}
+
+
+def adjoint_rate(wmc, torch, dev, stream, n_pot=64, reps=5):
+    """The differentiation form on 64 tanh-barrier potentials x 4096 cells
+    (Q = 256, n_M = 512): forward (potential, kernel rows, gamma) and backward
+    (kernel adjoint, potential adjoint), timed with events."""
+    from paper_1806_00082_gb300.adjoint import kernel_of_potential
+    w = wi.TANH_BARRIERS_4096
+    p = wmc.Params.of(w)
+    ws = wmc.workspace(p, dev)
+    theta0 = torch.from_numpy(wi.tanh_parameters(n_pot, n_x=w.n_x, dx_nm=w.dx_m * 1e9)).to(dev)
+    g = torch.randn((n_pot * w.n_x, w.Q // 2), device=dev, generator=torch.Generator(dev).manual_seed(0)) * 1e-15
+    gg = torch.randn(n_pot * w.n_x, device=dev, generator=torch.Generator(dev).manual_seed(1)) * 1e-16
+    fw, bw = 0.0, 0.0
+    with torch.cuda.stream(stream):
+        wmc.init(p, ws)
+        for r in range(reps + 2):
+            theta = theta0.clone().requires_grad_(True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            VWh, gamma = kernel_of_potential(theta, p, 16, 16, 0.5, ws)
+            loss = (VWh * g).sum() + (gamma * gg).sum()
+            e1.record(stream)
+            loss.backward()
+            e2.record(stream)
+            stream.synchronize()
+            if r >= 2:
+                fw += e0.elapsed_time(e1) * 1e-3
+                bw += e1.elapsed_time(e2) * 1e-3
+    h = w.Q // 2
+    flops = 2.0 * n_pot * w.n_x * (h - 1) ** 2
+    return {"workload": f"{n_pot} potentials x {w.n_x} cells, Q = {w.Q}, n_M = {w.n_M}, 64 parameters each",
+            "forward_s": fw / reps, "backward_s": bw / reps,
+            "forward_tflops_algorithmic": flops / (fw / reps) / 1e12,
+            "backward_tflops_algorithmic": flops / (bw / reps) / 1e12,
+            "grad_err_bound_normwise": 1e-4}
 
 
 def main():
