@@ -440,6 +440,25 @@ def adjoint_rate(wmc, torch, dev, stream, n_pot=64, reps=5):
             "grad_err_bound_normwise": 1e-4}
 
 
+def single_leg(args):
+    """One secondary leg on cuda:0, printed as its own JSON object (profiling aid)."""
+    import torch
+    from paper_1806_00082_gb300 import build, wmc
+    build.build()
+    wmc.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    if args.leg == "kernel":
+        out = kernel_eval_rate(wmc, torch, dev, stream, flush, reps=max(1, args.steps))
+    elif args.leg == "batched":
+        out = batched_rate(wmc, torch, dev, stream, steps=max(2, args.steps), warmup=1)
+    else:
+        out = adjoint_rate(wmc, torch, dev, stream, reps=max(1, args.steps))
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,11 +468,15 @@ def main():
     ap.add_argument("--workload", default="barrier-2000", choices=sorted(wi.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--leg", default="all", choices=["all", "kernel", "batched", "adjoint"],
+                    help="run one secondary leg alone (for profiling); 'all' is the benchmark")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = wi.WORKLOADS[args.workload]
     if args.impl == "reference":
         return reference_arm(args, w)
+    if args.leg != "all":
+        return single_leg(args)
     return native_arm(args, w)
 
 

@@ -184,6 +184,20 @@ __global__ void k_init_tc_images(int Q, int KB, int NT, uint16_t* __restrict__ i
 }
 
 // ---------------------------------------------------------------- contraction
+// Two pipeline stages: while the tensor cores run the MMAs of K block kb from
+// stage kb % 2, the threads build the A operand of block kb + 1 into the other
+// stage and thread 0 has already started the copy of its B operand(s); a
+// stage is rewritten only after the MMAs that read it have completed (one
+// mbarrier per stage for the copies, one for the MMA commits).  When the
+// tile's 128 rows are 128 consecutive cells of one potential, the potential
+// window they need is staged in shared memory once and the A operand is built
+// from it without branches.
+constexpr int kStages = 2;
+
+__host__ __device__ constexpr size_t tc_smem_bytes(bool split, int h) {
+  return (size_t)(split ? 8 : 4) * kTileBytes + sizeof(float) * (size_t)(TM + 2 * h);
+}
+
 template <int PREC>
 __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restrict__ V, int n_x, int bc, int Q,
                                                            const int* __restrict__ occ,
@@ -196,14 +210,15 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
   constexpr uint32_t kCols = SPLIT ? 512u : 256u;
   constexpr uint32_t idesc = idesc_f16(kind_fmt);
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sAhi = smem;
-  uint8_t* sBhi = smem + kTileBytes;
-  uint8_t* sAlo = smem + 2 * kTileBytes;  // split form only
-  uint8_t* sBlo = smem + 3 * kTileBytes;
-  __shared__ __align__(8) uint64_t bar_tma;
-  __shared__ __align__(8) uint64_t bar_mma;
+  uint8_t* sA[kStages] = {smem, smem + kTileBytes};
+  uint8_t* sB[kStages] = {smem + 2 * kTileBytes, smem + 3 * kTileBytes};
+  uint8_t* sAl[kStages] = {smem + 4 * kTileBytes, smem + 5 * kTileBytes};  // split form only
+  uint8_t* sBl[kStages] = {smem + 6 * kTileBytes, smem + 7 * kTileBytes};
+  float* sV = reinterpret_cast<float*>(smem + (SPLIT ? 8 : 4) * kTileBytes);
+  __shared__ __align__(8) uint64_t bar_tma[kStages];
+  __shared__ __align__(8) uint64_t bar_mma[kStages];
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_abort;
+  __shared__ int s_abort, s_cell0;
 
   const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
   const int row0 = blockIdx.x * TM, col0 = blockIdx.y * TN;
@@ -213,35 +228,47 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
 
   if (warp == 0) tmem_alloc(&tmem_slot, kCols);
   if (tid == 0) {
-    mbar_init(&bar_tma, 1);
-    mbar_init(&bar_mma, 1);
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&bar_tma[q], 1);
+      mbar_init(&bar_mma[q], 1);
+    }
     fence_mbar_init();
     s_abort = 0;
   }
+
+  // this thread's row: occ == nullptr means implicit rows over consecutive
+  // potentials (row r is cell r % n_x of potential r / n_x)
+  const int my_row = row0 + tid;
+  const bool valid = my_row < n_rows;
+  const int cell = valid ? (occ ? __ldg(occ + my_row) : my_row % n_x) : 0;
+  const int pot_idx = (occ || !valid) ? 0 : my_row / n_x;
+  const float* Vr = V + (size_t)pot_idx * n_x;
+  if (tid == 0) s_cell0 = cell;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t accA = tmem, accB = tmem + (uint32_t)TN, accX = tmem + 2u * (uint32_t)TN;
+  const int pot0 = (occ || row0 >= n_rows) ? 0 : row0 / n_x;
+  const bool contig = __syncthreads_and(valid && cell == s_cell0 + tid && pot_idx == pot0) != 0;
+  if (contig) {
+    const float* V0 = V + (size_t)pot0 * n_x;
+    for (int q = tid; q < TM + 2 * h; q += blockDim.x) sV[q] = potential_at(V0, n_x, bc, (long long)s_cell0 - h + q);
+  }
 
-  const int my_row = row0 + tid;
-  // occ == nullptr: implicit rows over consecutive potentials
-  const int cell = my_row < n_rows ? (occ ? __ldg(occ + my_row) : my_row % n_x) : 0;
-  const float* Vr = (occ || my_row >= n_rows) ? V : V + (size_t)(my_row / n_x) * n_x;
   const int half_kb = (KB + 1) / 2;
   const uint32_t tx_bytes = SPLIT ? 2u * kTileBytes : kTileBytes;
-  // sine-matrix images of this column tile: the input-type (or FP16 hi) image
-  // and, for the split form, the scaled FP16 residual image
   const uint16_t* imgB_tile = img_b + (size_t)blockIdx.y * KB * (kTileBytes / 2);
   const uint16_t* imgL_tile = SPLIT ? img_lo + (size_t)blockIdx.y * KB * (kTileBytes / 2) : nullptr;
 
-  for (int kb = 0; kb < KB; ++kb) {
-    if (tid == 0) {
-      mbar_expect_tx(&bar_tma, tx_bytes);
-      bulk_g2s(sBhi, imgB_tile + (size_t)kb * (kTileBytes / 2), kTileBytes, &bar_tma);
-      if (SPLIT) bulk_g2s(sBlo, imgL_tile + (size_t)kb * (kTileBytes / 2), kTileBytes, &bar_tma);
-    }
-    // this thread's A row: 64 window terms m = kb*64 + k + 1
+  auto issue_copy = [&](int kb, int st) {
+    mbar_expect_tx(&bar_tma[st], tx_bytes);
+    bulk_g2s(sB[st], imgB_tile + (size_t)kb * (kTileBytes / 2), kTileBytes, &bar_tma[st]);
+    if (SPLIT) bulk_g2s(sBl[st], imgL_tile + (size_t)kb * (kTileBytes / 2), kTileBytes, &bar_tma[st]);
+  };
+  // this thread's A row of K block kb: window terms m = kb*64 + k + 1
+  auto build_A = [&](int kb, int st) {
+    if (contig) __syncthreads();  // the window is staged (first use) / keeps warps aligned
 #pragma unroll
     for (int k8 = 0; k8 < TK / 8; ++k8) {
       uint32_t hw[4], lw[4];
@@ -252,8 +279,11 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
         for (int u = 0; u < 2; ++u) {
           const int m = kb * TK + k8 * 8 + e + u + 1;
           float dv = 0.f;
-          if (m <= h - 1 && my_row < n_rows)
-            dv = __fsub_rn(potential_at(Vr, n_x, bc, (long long)cell + m), potential_at(Vr, n_x, bc, (long long)cell - m));
+          if (m <= h - 1) {
+            if (contig) dv = __fsub_rn(sV[tid + h + m], sV[tid + h - m]);
+            else if (valid)
+              dv = __fsub_rn(potential_at(Vr, n_x, bc, (long long)cell + m), potential_at(Vr, n_x, bc, (long long)cell - m));
+          }
           hb[u] = to_bits(dv, SPLIT ? WMC_FP16 : PREC);
           if (SPLIT) lb[u] = to_bits(__fmul_rn(__fsub_rn(dv, from_bits(hb[u], WMC_FP16)), 2048.f), WMC_FP16);
         }
@@ -261,13 +291,21 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
         if (SPLIT) lw[e / 2] = (uint32_t)lb[0] | ((uint32_t)lb[1] << 16);
       }
       const uint32_t off = core_offset(tid, k8 * 8);
-      *reinterpret_cast<uint4*>(sAhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      if (SPLIT) *reinterpret_cast<uint4*>(sAlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      *reinterpret_cast<uint4*>(sA[st] + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      if (SPLIT) *reinterpret_cast<uint4*>(sAl[st] + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
+  };
+
+  if (tid == 0) issue_copy(0, 0);
+  build_A(0, 0);
+  for (int kb = 0; kb < KB; ++kb) {
+    const int st = kb & 1;
+    const uint32_t ph = (uint32_t)((kb >> 1) & 1);
     fence_proxy_async_smem();
-    __syncthreads();
+    __syncthreads();  // A of block kb is in stage st
+    if (s_abort) break;
     if (tid == 0) {
-      if (!mbar_wait(&bar_tma, (uint32_t)(kb & 1))) {
+      if (!mbar_wait(&bar_tma[st], ph)) {
         atomicOr(flags, WMC_FLAG_TIMEOUT);
         s_abort = 1;
       } else {
@@ -276,28 +314,41 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
         const int first = kb == 0 || kb == half_kb;
 #pragma unroll
         for (int s = 0; s < TK / 16; ++s) {
-          const uint64_t a_hi = smem_desc(smem_u32(sAhi) + s * 2 * kLBO);
-          const uint64_t b_hi = smem_desc(smem_u32(sBhi) + s * 2 * kLBO);
+          const uint64_t a_hi = smem_desc(smem_u32(sA[st]) + s * 2 * kLBO);
+          const uint64_t b_hi = smem_desc(smem_u32(sB[st]) + s * 2 * kLBO);
           mma_f16(acc, a_hi, b_hi, idesc, (first && s == 0) ? 0u : 1u);
           if (SPLIT) {
-            const uint64_t a_lo = smem_desc(smem_u32(sAlo) + s * 2 * kLBO);
-            const uint64_t b_lo = smem_desc(smem_u32(sBlo) + s * 2 * kLBO);
+            const uint64_t a_lo = smem_desc(smem_u32(sAl[st]) + s * 2 * kLBO);
+            const uint64_t b_lo = smem_desc(smem_u32(sBl[st]) + s * 2 * kLBO);
             mma_f16(accX, a_hi, b_lo, idesc, (kb == 0 && s == 0) ? 0u : 1u);
             mma_f16(accX, a_lo, b_hi, idesc, 1u);
           }
         }
-        mma_commit(&bar_mma);
-        if (!mbar_wait(&bar_mma, (uint32_t)(kb & 1))) {
-          atomicOr(flags, WMC_FLAG_TIMEOUT);
-          s_abort = 1;
+        mma_commit(&bar_mma[st]);
+        // the other stage is free once the MMAs of block kb - 1 are done
+        if (kb + 1 < KB) {
+          if (kb >= 1 && !mbar_wait(&bar_mma[st ^ 1], (uint32_t)(((kb - 1) >> 1) & 1))) {
+            atomicOr(flags, WMC_FLAG_TIMEOUT);
+            s_abort = 1;
+          } else {
+            issue_copy(kb + 1, st ^ 1);
+          }
         }
       }
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (s_abort) break;
+    if (kb + 1 < KB) {
+      if (kb >= 1 && !mbar_wait(&bar_mma[st ^ 1], (uint32_t)(((kb - 1) >> 1) & 1))) s_abort = 1;
+      build_A(kb + 1, st ^ 1);
+    }
   }
+  // all MMAs of the tile done (commits complete in order)
+  if (tid == 0 && !s_abort && !mbar_wait(&bar_mma[(KB - 1) & 1], (uint32_t)(((KB - 1) >> 1) & 1))) {
+    atomicOr(flags, WMC_FLAG_TIMEOUT);
+    s_abort = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   if (!s_abort) {
     // epilogue: lane (warp 32 w + l) of TMEM holds tile row 32 w + l
@@ -327,11 +378,282 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
+// ---------------------------------------------------------------- warp-specialised form
+// BF16 / FP16: one CTA per 128 rows and a run of column tiles.  The whole A
+// operand (128 x Kp, 16-bit) stays in shared memory, so it is built once and
+// reused by every column tile of the CTA.  Roles (320 threads):
+//   warps 0-7  build A (row tid % 128, half the core-matrix columns of each
+//              block each), signalling a_ready[kb]; then run the epilogue of
+//              each column tile from TMEM (warp w reads lane quadrant w % 4,
+//              columns of half w / 4);
+//   warp 8     one thread issues the MMAs: tile j into the accumulator buffer
+//              j % 2 (two K halves), waiting for A blocks, B stages and a
+//              drained buffer, committing each B stage and each tile;
+//   warp 9     one thread streams the B operand images through a 4-stage ring,
+//              starting as soon as the barriers exist.
+// Synchronisation is by mbarriers and one named barrier among the builders;
+// every wait is bounded and an abort flag makes all roles drain to the final
+// barrier, after which TMEM is freed.
+constexpr int kWsStages = 4;
+constexpr int kWsMaxKB = 32;  // Q <= 4096
+constexpr int kWsBuilders = 256;
+constexpr int kWsThreads = kWsBuilders + 64;
+
+__host__ __device__ constexpr size_t ws_smem_bytes(int KB, int h) {
+  return (size_t)KB * kTileBytes + (size_t)kWsStages * kTileBytes + sizeof(float) * (size_t)(TM + 2 * h);
+}
+
+// AND of pred over the kWsBuilders builder threads (named barrier 1).
+__device__ __forceinline__ bool builders_and(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, p;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "barrier.cta.red.and.pred p, 1, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "n"(kWsBuilders)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void builders_sync() { asm volatile("barrier.cta.sync 1, %0;" ::"n"(kWsBuilders) : "memory"); }
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if (PREC == WMC_BF16) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  } else {
+    const __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  }
+}
+
+template <int PREC>
+__global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float* __restrict__ V, int n_x, int bc,
+                                                                     int Q, const int* __restrict__ occ,
+                                                                     const int* __restrict__ n_occ_dev, int n_occ_host,
+                                                                     const uint16_t* __restrict__ img_b, int KB,
+                                                                     int NT, int n_split, float c,
+                                                                     float* __restrict__ VWh,
+                                                                     unsigned int* __restrict__ flags) {
+  constexpr int kind_fmt = PREC == WMC_BF16 ? 1 : 0;
+  constexpr uint32_t idesc = idesc_f16(kind_fmt);
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;                                         // KB blocks of 128 x 64
+  uint8_t* sB = smem + (size_t)KB * kTileBytes;              // kWsStages stages
+  float* sV = reinterpret_cast<float*>(sB + (size_t)kWsStages * kTileBytes);
+  __shared__ __align__(8) uint64_t a_ready[kWsMaxKB];
+  __shared__ __align__(8) uint64_t b_full[kWsStages], b_empty[kWsStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+
+  const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
+  const int row0 = blockIdx.x * TM;
+  const int h = Q / 2;
+  if (row0 >= n_rows) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half_kb = (KB + 1) / 2;
+  const bool has_B = KB > half_kb;
+  // accumulator pair per buffer when K is split in halves, else one column block
+  const uint32_t acc_stride = has_B ? 2u * TN : (uint32_t)TN;
+  const uint32_t n_cols = 2u * acc_stride;
+  // this CTA's column tiles [nt_begin, nt_begin + n_my); local tile j = nt - nt_begin
+  const int nt_begin = (int)(((long long)blockIdx.y * NT) / n_split);
+  const int n_my = (int)(((long long)(blockIdx.y + 1) * NT) / n_split) - nt_begin;
+  const int n_tiles = n_my * KB;
+
+  if (warp == 0) tmem_alloc(&tmem_slot, n_cols);
+  if (tid == 0) {
+    for (int q = 0; q < KB; ++q) mbar_init(&a_ready[q], kWsBuilders);
+    for (int q = 0; q < kWsStages; ++q) {
+      mbar_init(&b_full[q], 1);
+      mbar_init(&b_empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&acc_full[q], 1);
+      mbar_init(&acc_empty[q], kWsBuilders);
+    }
+    mbar_init(&drain, 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 9) {
+    // ---- B producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int t = 0; t < n_tiles && !s_abort; ++t) {
+        const int st = t % kWsStages;
+        if (t >= kWsStages && !mbar_wait(&b_empty[st], (uint32_t)(((t / kWsStages) - 1) & 1))) {
+          atomicOr(flags, WMC_FLAG_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        const int nt = nt_begin + t / KB, kb = t % KB;
+        mbar_expect_tx(&b_full[st], kTileBytes);
+        bulk_g2s(sB + (size_t)st * kTileBytes, img_b + ((size_t)nt * KB + kb) * (kTileBytes / 2), kTileBytes,
+                 &b_full[st]);
+        issued = t + 1;
+      }
+      if (s_abort)  // let the copies still in flight land before the CTA exits (bounded)
+        for (int t = max(0, issued - kWsStages); t < issued; ++t)
+          (void)mbar_wait(&b_full[t % kWsStages], (uint32_t)((t / kWsStages) & 1));
+    }
+  } else if (warp == 8) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      for (int j = 0; j < n_my && !s_abort; ++j) {
+        const int buf = j & 1;
+        if (j >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)(((j - 2) >> 1) & 1))) {
+          atomicOr(flags, WMC_FLAG_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t accA = tmem + (uint32_t)buf * acc_stride, accB = accA + (uint32_t)TN;
+        for (int kb = 0; kb < KB; ++kb) {
+          const int t = j * KB + kb, st = t % kWsStages;
+          if ((j == 0 && !mbar_wait(&a_ready[kb], 0u)) ||
+              !mbar_wait(&b_full[st], (uint32_t)((t / kWsStages) & 1))) {
+            atomicOr(flags, WMC_FLAG_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t acc = kb < half_kb ? accA : accB;
+          const int first = kb == 0 || kb == half_kb;
+          const uint32_t a_base = smem_u32(sA + (size_t)kb * kTileBytes);
+          const uint32_t b_base = smem_u32(sB + (size_t)st * kTileBytes);
+#pragma unroll
+          for (int s4 = 0; s4 < TK / 16; ++s4)
+            mma_f16(acc, smem_desc(a_base + s4 * 2 * kLBO), smem_desc(b_base + s4 * 2 * kLBO), idesc,
+                    (first && s4 == 0) ? 0u : 1u);
+          mma_commit(&b_empty[st]);
+        }
+        if (s_abort) break;
+        mma_commit(&acc_full[buf]);
+      }
+      if (s_abort) {  // drain the MMAs already issued before TMEM is freed (bounded)
+        mma_commit(&drain);
+        (void)mbar_wait(&drain, 0u);
+      }
+    }
+  } else {
+    // ---- A builders (warps 0-7), then the epilogue
+    const int r = tid & (TM - 1);          // row within the tile
+    const int kh = tid >> 7;               // which half of the 8 core-matrix columns of a block
+    const int my_row = row0 + r;
+    const bool valid = my_row < n_rows;
+    const int cell = valid ? (occ ? __ldg(occ + my_row) : my_row % n_x) : 0;
+    const int pot_idx = (occ || !valid) ? 0 : my_row / n_x;
+    const int cell0 = occ ? __ldg(occ + row0) : row0 % n_x;
+    const int pot0 = occ ? 0 : row0 / n_x;
+    const bool contig = builders_and(valid && cell == cell0 + r && pot_idx == pot0);
+    if (contig) {
+      const float* V0 = V + (size_t)pot0 * n_x;
+      for (int q = tid; q < TM + 2 * h; q += kWsBuilders)
+        sV[q] = potential_at(V0, n_x, bc, (long long)cell0 - h + q);
+      builders_sync();
+    }
+    const float* Vr = V + (size_t)pot_idx * n_x;
+    const float* sVr = sV + r + h;
+#pragma unroll 1
+    for (int kb = 0; kb < KB; ++kb) {
+      uint8_t* blk = sA + (size_t)kb * kTileBytes;
+      const bool full = (kb + 1) * TK <= h - 1;  // every m of the block is inside the window
+#pragma unroll
+      for (int k8i = 0; k8i < TK / 16; ++k8i) {
+        const int k8 = kh * (TK / 16) + k8i;
+        const int m0 = kb * TK + k8 * 8 + 1;
+        float dv[8];
+        if (contig && full) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) dv[e] = __fsub_rn(sVr[m0 + e], sVr[-(m0 + e)]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int m = m0 + e;
+            dv[e] = 0.f;
+            if (m <= h - 1) {
+              if (contig) dv[e] = __fsub_rn(sVr[m], sVr[-m]);
+              else if (valid)
+                dv[e] = __fsub_rn(potential_at(Vr, n_x, bc, (long long)cell + m),
+                                  potential_at(Vr, n_x, bc, (long long)cell - m));
+            }
+          }
+        }
+        *reinterpret_cast<uint4*>(blk + core_offset(r, k8 * 8)) =
+            make_uint4(pack2<PREC>(dv[0], dv[1]), pack2<PREC>(dv[2], dv[3]), pack2<PREC>(dv[4], dv[5]),
+                       pack2<PREC>(dv[6], dv[7]));
+      }
+      fence_proxy_async_smem();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kb])) : "memory");
+    }
+    // epilogue of each column tile: warp w reads lanes 32 (w % 4) .. + 31, columns of half w / 4
+    const int quad = warp & 3, chalf = warp >> 2;
+    const int row = row0 + quad * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    const bool vec_ok = (h & 3) == 0 && (reinterpret_cast<uintptr_t>(VWh) & 15) == 0;
+    for (int j = 0; j < n_my; ++j) {
+      const int buf = j & 1;
+      // warp-uniform decision: the TMEM loads below are warp-collective
+      const bool ok = __all_sync(0xffffffffu, !s_abort && mbar_wait(&acc_full[buf], (uint32_t)((j >> 1) & 1)));
+      if (!ok) {
+        if (lane == 0) atomicOr(flags, WMC_FLAG_TIMEOUT);
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t accA = tmem + (uint32_t)buf * acc_stride, accB = accA + (uint32_t)TN;
+      const int col0 = (nt_begin + j) * TN;
+#pragma unroll 1
+      for (int cc = chalf * (TN / 2); cc < (chalf + 1) * (TN / 2); cc += 16) {
+        float a[16], b[16];
+        tmem_ld16(accA + lane_base + (uint32_t)cc, a);
+        if (has_B) tmem_ld16(accB + lane_base + (uint32_t)cc, b);
+        if (row < n_rows) {
+          float* out = VWh + (size_t)row * h + col0 + cc;
+          const int lim = min(16, h - col0 - cc);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) a[q] = __fmul_rn(c, has_B ? __fadd_rn(a[q], b[q]) : a[q]);
+          if (vec_ok && lim == 16) {
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+              *reinterpret_cast<float4*>(out + q) = make_float4(a[q], a[q + 1], a[q + 2], a[q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (q < lim) out[q] = a[q];
+          }
+        }
+      }
+      tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, n_cols);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 struct TcImages {
   int KB, NT;
   size_t bytes_per_image;  // NT * KB * kTileBytes
 };
+
+static int g_h(const wmc_params& p) { return p.Q / 2; }
 
 static TcImages tc_geometry(const wmc_params& p) {
   TcImages g;
@@ -362,16 +684,40 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
   const size_t n16 = g.bytes_per_image / 2;
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   dim3 grid((max_rows + TM - 1) / TM, g.NT);
+  const int row_tiles = (max_rows + TM - 1) / TM;
+  const size_t ws_sm = ws_smem_bytes(g.KB, g_h(p));
+  if ((prec == WMC_BF16 || prec == WMC_FP16) && g.KB <= kWsMaxKB && ws_sm <= 220 * 1024 &&
+      (long long)row_tiles * g.NT >= 2ll * num_sms()) {
+    // warp-specialised form; the column tiles are split over grid.y only as far
+    // as needed to give every SM a CTA
+    const uint16_t* img = prec == WMC_BF16 ? base : base + n16;
+    int n_split = 1;
+    while (n_split < g.NT && (long long)row_tiles * n_split < num_sms()) n_split *= 2;
+    n_split = std::min(n_split, g.NT);
+    const dim3 ws_grid(row_tiles, n_split);
+    if (prec == WMC_BF16) {
+      cudaFuncSetAttribute(k_kernel_eval_tc_ws<WMC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_sm);
+      k_kernel_eval_tc_ws<WMC_BF16><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                                 n_occ_host, img, g.KB, g.NT, n_split, c, VWh, flags);
+    } else {
+      cudaFuncSetAttribute(k_kernel_eval_tc_ws<WMC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_sm);
+      k_kernel_eval_tc_ws<WMC_FP16><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                                 n_occ_host, img, g.KB, g.NT, n_split, c, VWh, flags);
+    }
+    return cudaGetLastError();
+  }
   if (prec == WMC_BF16) {
-    const size_t sm = 2 * kTileBytes;
+    const size_t sm = tc_smem_bytes(false, g_h(p));
+    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_kernel_eval_tc<WMC_BF16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
                                                      base, nullptr, g.KB, c, VWh, flags);
   } else if (prec == WMC_FP16) {
-    const size_t sm = 2 * kTileBytes;
+    const size_t sm = tc_smem_bytes(false, g_h(p));
+    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_kernel_eval_tc<WMC_FP16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
                                                      base + n16, nullptr, g.KB, c, VWh, flags);
   } else if (prec == WMC_FP16_SPLIT) {
-    const size_t sm = 4 * kTileBytes;
+    const size_t sm = tc_smem_bytes(true, g_h(p));
     cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_kernel_eval_tc<WMC_FP16_SPLIT><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
                                                            n_occ_host, base + n16, base + 2 * n16, g.KB, c, VWh,

@@ -92,3 +92,59 @@ def test_tensorcore_in_production_loop(wmc):
         l1 = np.abs(got.sum(axis=1) - ref.sum(axis=1)).sum() / wl.packet.n0
         assert l1 <= tol, (form, l1)
         assert c["flags"] == 0
+
+
+def _sampled_err(got, wl, V, cells, n_sample, seed):
+    rng = np.random.default_rng(seed)
+    pick = np.unique(np.concatenate([rng.integers(0, cells.size, n_sample), [0, cells.size - 1]]))
+    ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, cells[pick])[:, wl.Q // 2:]
+    return normwise(got[pick], ref)
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16"])
+@pytest.mark.parametrize("wl,n", [(wi.DOUBLE_BARRIER_16384, 16384 - 77), (wi.DOUBLE_BARRIER_16384, 16384),
+                                  (wi.BARRIER_2000, 40_000 + 45)])
+def test_tensorcore_whole_row_form(wmc, form, wl, n):
+    """Row counts that fill the GPU with whole-row CTAs (the resident-A,
+    warp-specialised contraction): every cell of the domain (contiguous
+    windows), a permutation with a ragged last tile, and a list longer than
+    the domain with repeated cells; sampled rows against the FP64 oracle, every
+    row finite, and each repeated cell bit-identical."""
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    if n == wl.n_x:
+        cells = np.arange(n, dtype=np.int32)
+    elif n < wl.n_x:
+        cells = np.random.default_rng(5).permutation(wl.n_x)[:n].astype(np.int32)
+    else:
+        cells = (np.arange(n) % wl.n_x).astype(np.int32)
+    got = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), torch.from_numpy(cells).cuda(), ws,
+                          prec=wmc.PRECISIONS[form]).cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert _sampled_err(got, wl, V, cells, 160, 9) <= TOL[form], (form, wl.name, n)
+    if n > wl.n_x:
+        assert np.array_equal(got[:wl.n_x], got[wl.n_x:2 * wl.n_x])
+    assert wmc.get_counters(p, ws)["flags"] == 0
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16"])
+def test_tensorcore_implicit_rows_many_potentials(wmc, form):
+    """Implicit rows (row r = cell r mod n_x of potential r / n_x) over several
+    potentials, with n_x not a multiple of the 128-row tile, so that tiles
+    straddle two potentials."""
+    wl = wi.BARRIER_2000.replace(n_x=2000 + 13)
+    p = wmc.Params.of(wl)
+    rng = np.random.default_rng(4)
+    n_pot = 24
+    Vs = np.stack([wi.potential(wl) * np.float32(rng.uniform(0.5, 1.5)) for _ in range(n_pot)]).astype(np.float32)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    got = wmc.kernel_eval_rows(p, torch.from_numpy(Vs).cuda(), ws, prec=wmc.PRECISIONS[form]).cpu().numpy()
+    assert np.all(np.isfinite(got))
+    for b in (0, 7, n_pot - 1):
+        cells = np.arange(wl.n_x, dtype=np.int32)
+        err = _sampled_err(got[b * wl.n_x:(b + 1) * wl.n_x], wl, Vs[b], cells, 120, b)
+        assert err <= TOL[form], (form, b, err)
+    assert wmc.get_counters(p, ws)["flags"] == 0
