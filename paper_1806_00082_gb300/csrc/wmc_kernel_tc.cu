@@ -132,6 +132,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane, waited for.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 __device__ __forceinline__ float potential_at(const float* __restrict__ V, int n_x, int bc, long long l) {
   if (l >= 0 && l < n_x) return __ldg(V + l);
   if (!bc) return 0.f;
@@ -381,26 +393,35 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
 // ---------------------------------------------------------------- warp-specialised form
 // BF16 / FP16: one CTA per 128 rows and a run of column tiles.  The whole A
 // operand (128 x Kp, 16-bit) stays in shared memory, so it is built once and
-// reused by every column tile of the CTA.  Roles (320 threads):
-//   warps 0-7  build A (row tid % 128, half the core-matrix columns of each
-//              block each), signalling a_ready[kb]; then run the epilogue of
-//              each column tile from TMEM (warp w reads lane quadrant w % 4,
-//              columns of half w / 4);
-//   warp 8     one thread issues the MMAs: tile j into the accumulator buffer
-//              j % 2 (two K halves), waiting for A blocks, B stages and a
-//              drained buffer, committing each B stage and each tile;
-//   warp 9     one thread streams the B operand images through a 4-stage ring,
+// reused by every column tile of the CTA.  Roles (576 threads):
+//   warps 0-15 build A (four rows and one core-matrix column of every other
+//              block each), signalling a_ready[kb]; then run the epilogue
+//              of each column tile from TMEM (warp w reads lane quadrant w % 4,
+//              32 columns at 32 (w / 4)), transposing each 32 x 16 piece
+//              through shared memory so that global stores are whole 64-byte
+//              row segments;
+//   warp 16    one thread issues the MMAs: tile j into the FP32 accumulator
+//              buffer j % 2, waiting for A blocks, B stages and a drained
+//              buffer, committing each B stage and each tile;
+//   warp 17    one thread streams the B operand images through a 4-stage ring,
 //              starting as soon as the barriers exist.
 // Synchronisation is by mbarriers and one named barrier among the builders;
 // every wait is bounded and an abort flag makes all roles drain to the final
 // barrier, after which TMEM is freed.
 constexpr int kWsStages = 4;
 constexpr int kWsMaxKB = 32;  // Q <= 4096
-constexpr int kWsBuilders = 256;
+constexpr int kWsBuilders = 512;
 constexpr int kWsThreads = kWsBuilders + 64;
 
+constexpr int kWsStageFloats = 32 * 16;  // epilogue staging per warp: 32 rows x 16 columns
+
+// A blocks, B ring, then one region used first for the potential window
+// (TM + 2h floats, building A) and then for the epilogue staging.
 __host__ __device__ constexpr size_t ws_smem_bytes(int KB, int h) {
-  return (size_t)KB * kTileBytes + (size_t)kWsStages * kTileBytes + sizeof(float) * (size_t)(TM + 2 * h);
+  return (size_t)KB * kTileBytes + (size_t)kWsStages * kTileBytes +
+         sizeof(float) * (size_t)((TM + 2 * h) > (kWsBuilders / 32) * kWsStageFloats
+                                      ? (TM + 2 * h)
+                                      : (kWsBuilders / 32) * kWsStageFloats);
 }
 
 // AND of pred over the kWsBuilders builder threads (named barrier 1).
@@ -443,7 +464,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                                         // KB blocks of 128 x 64
   uint8_t* sB = smem + (size_t)KB * kTileBytes;              // kWsStages stages
-  float* sV = reinterpret_cast<float*>(sB + (size_t)kWsStages * kTileBytes);
+  float* sV = reinterpret_cast<float*>(sB + (size_t)kWsStages * kTileBytes);  // shared with the staging
   __shared__ __align__(8) uint64_t a_ready[kWsMaxKB];
   __shared__ __align__(8) uint64_t b_full[kWsStages], b_empty[kWsStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
@@ -456,11 +477,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
   const int h = Q / 2;
   if (row0 >= n_rows) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int half_kb = (KB + 1) / 2;
-  const bool has_B = KB > half_kb;
-  // accumulator pair per buffer when K is split in halves, else one column block
-  const uint32_t acc_stride = has_B ? 2u * TN : (uint32_t)TN;
-  const uint32_t n_cols = 2u * acc_stride;
+  const uint32_t n_cols = 2u * TN;  // two accumulator buffers of 128 columns
   // this CTA's column tiles [nt_begin, nt_begin + n_my); local tile j = nt - nt_begin
   const int nt_begin = (int)(((long long)blockIdx.y * NT) / n_split);
   const int n_my = (int)(((long long)(blockIdx.y + 1) * NT) / n_split) - nt_begin;
@@ -486,7 +503,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 9) {
+  if (warp == kWsBuilders / 32 + 1) {
     // ---- B producer
     if (lane == 0) {
       int issued = 0;
@@ -507,7 +524,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
         for (int t = max(0, issued - kWsStages); t < issued; ++t)
           (void)mbar_wait(&b_full[t % kWsStages], (uint32_t)((t / kWsStages) & 1));
     }
-  } else if (warp == 8) {
+  } else if (warp == kWsBuilders / 32) {
     // ---- MMA issuer
     if (lane == 0) {
       for (int j = 0; j < n_my && !s_abort; ++j) {
@@ -518,7 +535,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
           break;
         }
         tc_fence_after();
-        const uint32_t accA = tmem + (uint32_t)buf * acc_stride, accB = accA + (uint32_t)TN;
+        const uint32_t acc = tmem + (uint32_t)(buf * TN);
         for (int kb = 0; kb < KB; ++kb) {
           const int t = j * KB + kb, st = t % kWsStages;
           if ((j == 0 && !mbar_wait(&a_ready[kb], 0u)) ||
@@ -528,8 +545,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
             break;
           }
           tc_fence_after();
-          const uint32_t acc = kb < half_kb ? accA : accB;
-          const int first = kb == 0 || kb == half_kb;
+          const int first = kb == 0;
           const uint32_t a_base = smem_u32(sA + (size_t)kb * kTileBytes);
           const uint32_t b_base = smem_u32(sB + (size_t)st * kTileBytes);
 #pragma unroll
@@ -547,59 +563,105 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
       }
     }
   } else {
-    // ---- A builders (warps 0-7), then the epilogue
-    const int r = tid & (TM - 1);          // row within the tile
-    const int kh = tid >> 7;               // which half of the 8 core-matrix columns of a block
-    const int my_row = row0 + r;
-    const bool valid = my_row < n_rows;
-    const int cell = valid ? (occ ? __ldg(occ + my_row) : my_row % n_x) : 0;
-    const int pot_idx = (occ || !valid) ? 0 : my_row / n_x;
+    // ---- A builders (warps 0-15), then the epilogue
+    // contiguity of the tile's rows (row row0 + tid % 128, each checked by four threads)
+    const int rc = tid & (TM - 1);
+    const int rowc = row0 + rc;
+    const bool validc = rowc < n_rows;
+    const int cellc = validc ? (occ ? __ldg(occ + rowc) : rowc % n_x) : 0;
+    const int potc = (occ || !validc) ? 0 : rowc / n_x;
     const int cell0 = occ ? __ldg(occ + row0) : row0 % n_x;
     const int pot0 = occ ? 0 : row0 / n_x;
-    const bool contig = builders_and(valid && cell == cell0 + r && pot_idx == pot0);
+    const bool contig = builders_and(validc && cellc == cell0 + rc && potc == pot0);
     if (contig) {
       const float* V0 = V + (size_t)pot0 * n_x;
-      for (int q = tid; q < TM + 2 * h; q += kWsBuilders)
-        sV[q] = potential_at(V0, n_x, bc, (long long)cell0 - h + q);
+      constexpr int kU = 4;  // loads issued together
+      for (int q0 = tid; q0 < TM + 2 * h; q0 += kU * kWsBuilders) {
+        float v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int q = q0 + u * kWsBuilders;
+          v[u] = q < TM + 2 * h ? potential_at(V0, n_x, bc, (long long)cell0 - h + q) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (q0 + u * kWsBuilders < TM + 2 * h) sV[q0 + u * kWsBuilders] = v[u];
+      }
       builders_sync();
     }
-    const float* Vr = V + (size_t)pot_idx * n_x;
-    const float* sVr = sV + r + h;
+    // Build mapping: thread (rg, k8, par) fills rows 4 rg .. 4 rg + 3 of core-matrix
+    // column k8 in every block of parity par.  With contiguous rows the four rows
+    // share their potential windows: 12 + 12 values (three 16-byte loads each)
+    // serve 32 differences.  It arrives at once on the blocks of the other parity.
+    const int rg = tid & 31, k8 = (tid >> 5) & 7, par = tid >> 8;
+    for (int kb = 1 - par; kb < KB; kb += 2)
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kb])) : "memory");
+    int cell_d[4];
+    bool valid_d[4];
+    const float* V_d[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int row = row0 + 4 * rg + d;
+      valid_d[d] = row < n_rows;
+      cell_d[d] = (contig || !valid_d[d]) ? 0 : (occ ? __ldg(occ + row) : row % n_x);
+      V_d[d] = V + (size_t)((occ || !valid_d[d]) ? 0 : row / n_x) * n_x;
+    }
+    const bool fast = contig && (h & 3) == 0;
 #pragma unroll 1
-    for (int kb = 0; kb < KB; ++kb) {
+    for (int kb = par; kb < KB; kb += 2) {
       uint8_t* blk = sA + (size_t)kb * kTileBytes;
-      const bool full = (kb + 1) * TK <= h - 1;  // every m of the block is inside the window
+      const int m0 = kb * TK + k8 * 8 + 1;
+      float dv[4][8];
+      if (fast && m0 + 7 <= h - 1) {
+        // P[j] = V at offset m0 - 1 + j right of row 4 rg, N[j] = V at offset m0 + 7 - j left of it
+        float P[12], N[12];
+        const float* pp = sV + 4 * rg + h + m0 - 1;
+        const float* pn = sV + 4 * rg + h - m0 - 7;
 #pragma unroll
-      for (int k8i = 0; k8i < TK / 16; ++k8i) {
-        const int k8 = kh * (TK / 16) + k8i;
-        const int m0 = kb * TK + k8 * 8 + 1;
-        float dv[8];
-        if (contig && full) {
+        for (int q = 0; q < 3; ++q) {
+          const float4 a = *reinterpret_cast<const float4*>(pp + 4 * q);
+          const float4 b = *reinterpret_cast<const float4*>(pn + 4 * q);
+          P[4 * q] = a.x, P[4 * q + 1] = a.y, P[4 * q + 2] = a.z, P[4 * q + 3] = a.w;
+          N[4 * q] = b.x, N[4 * q + 1] = b.y, N[4 * q + 2] = b.z, N[4 * q + 3] = b.w;
+        }
 #pragma unroll
-          for (int e = 0; e < 8; ++e) dv[e] = __fsub_rn(sVr[m0 + e], sVr[-(m0 + e)]);
-        } else {
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) dv[d][e] = __fsub_rn(P[d + e + 1], N[d - e + 7]);
+      } else {
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int m = m0 + e;
-            dv[e] = 0.f;
+            dv[d][e] = 0.f;
             if (m <= h - 1) {
-              if (contig) dv[e] = __fsub_rn(sVr[m], sVr[-m]);
-              else if (valid)
-                dv[e] = __fsub_rn(potential_at(Vr, n_x, bc, (long long)cell + m),
-                                  potential_at(Vr, n_x, bc, (long long)cell - m));
+              if (contig) dv[d][e] = __fsub_rn(sV[4 * rg + d + h + m], sV[4 * rg + d + h - m]);
+              else if (valid_d[d])
+                dv[d][e] = __fsub_rn(potential_at(V_d[d], n_x, bc, (long long)cell_d[d] + m),
+                                     potential_at(V_d[d], n_x, bc, (long long)cell_d[d] - m));
             }
           }
-        }
-        *reinterpret_cast<uint4*>(blk + core_offset(r, k8 * 8)) =
-            make_uint4(pack2<PREC>(dv[0], dv[1]), pack2<PREC>(dv[2], dv[3]), pack2<PREC>(dv[4], dv[5]),
-                       pack2<PREC>(dv[6], dv[7]));
+      }
+      uint4 w[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        w[d] = make_uint4(pack2<PREC>(dv[d][0], dv[d][1]), pack2<PREC>(dv[d][2], dv[d][3]),
+                          pack2<PREC>(dv[d][4], dv[d][5]), pack2<PREC>(dv[d][6], dv[d][7]));
+      // store i writes row 4 rg + x, x = (i + rg / 2) % 4: eight consecutive
+      // lanes then cover the eight 16-byte bank groups
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int x = (i + (rg >> 1)) & 3;
+        const uint4 v = x == 0 ? w[0] : x == 1 ? w[1] : x == 2 ? w[2] : w[3];
+        *reinterpret_cast<uint4*>(blk + core_offset(4 * rg + x, k8 * 8)) = v;
       }
       fence_proxy_async_smem();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kb])) : "memory");
     }
-    // epilogue of each column tile: warp w reads lanes 32 (w % 4) .. + 31, columns of half w / 4
-    const int quad = warp & 3, chalf = warp >> 2;
-    const int row = row0 + quad * 32 + lane;
+    // epilogue of each column tile: warp w reads lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31
+    const int quad = warp & 3, cq = warp >> 2;
+    float* stg = sV + warp * kWsStageFloats;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     const bool vec_ok = (h & 3) == 0 && (reinterpret_cast<uintptr_t>(VWh) & 15) == 0;
     for (int j = 0; j < n_my; ++j) {
@@ -612,28 +674,39 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
         break;
       }
       tc_fence_after();
-      const uint32_t accA = tmem + (uint32_t)buf * acc_stride, accB = accA + (uint32_t)TN;
-      const int col0 = (nt_begin + j) * TN;
 #pragma unroll 1
-      for (int cc = chalf * (TN / 2); cc < (chalf + 1) * (TN / 2); cc += 16) {
-        float a[16], b[16];
-        tmem_ld16(accA + lane_base + (uint32_t)cc, a);
-        if (has_B) tmem_ld16(accB + lane_base + (uint32_t)cc, b);
-        if (row < n_rows) {
-          float* out = VWh + (size_t)row * h + col0 + cc;
-          const int lim = min(16, h - col0 - cc);
+      for (int hf = 0; hf < 2; ++hf) {
+        const int cc = cq * 32 + hf * 16;
+        const int col0 = (nt_begin + j) * TN + cc;
+        float a[16];
+        tmem_ld16(tmem + (uint32_t)(buf * TN) + lane_base + (uint32_t)cc, a);
+        // row `lane` of the piece; its four 16-byte groups are XOR-swizzled by
+        // (row / 2) % 4, which keeps both the row-wise writes and the
+        // group-wise reads below free of bank conflicts
 #pragma unroll
-          for (int q = 0; q < 16; ++q) a[q] = __fmul_rn(c, has_B ? __fadd_rn(a[q], b[q]) : a[q]);
-          if (vec_ok && lim == 16) {
+        for (int g = 0; g < 4; ++g)
+          *reinterpret_cast<float4*>(stg + lane * 16 + 4 * (g ^ ((lane >> 1) & 3))) =
+              make_float4(__fmul_rn(c, a[4 * g]), __fmul_rn(c, a[4 * g + 1]), __fmul_rn(c, a[4 * g + 2]),
+                          __fmul_rn(c, a[4 * g + 3]));
+        __syncwarp();
 #pragma unroll
-            for (int q = 0; q < 16; q += 4)
-              *reinterpret_cast<float4*>(out + q) = make_float4(a[q], a[q + 1], a[q + 2], a[q + 3]);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (q < lim) out[q] = a[q];
+        for (int i = 0; i < 4; ++i) {
+          const int rr = 8 * i + (lane >> 2), g = lane & 3;
+          const float4 v = *reinterpret_cast<const float4*>(stg + rr * 16 + 4 * (g ^ ((rr >> 1) & 3)));
+          const int grow = row0 + quad * 32 + rr, gcol = col0 + 4 * g;
+          if (grow < n_rows && gcol < h) {
+            float* out = VWh + (size_t)grow * h + gcol;
+            if (vec_ok) {
+              *reinterpret_cast<float4*>(out) = v;
+            } else {
+              out[0] = v.x;
+              if (gcol + 1 < h) out[1] = v.y;
+              if (gcol + 2 < h) out[2] = v.z;
+              if (gcol + 3 < h) out[3] = v.w;
+            }
           }
         }
+        __syncwarp();
       }
       tc_fence_before();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
@@ -686,14 +759,22 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
   dim3 grid((max_rows + TM - 1) / TM, g.NT);
   const int row_tiles = (max_rows + TM - 1) / TM;
   const size_t ws_sm = ws_smem_bytes(g.KB, g_h(p));
-  if ((prec == WMC_BF16 || prec == WMC_FP16) && g.KB <= kWsMaxKB && ws_sm <= 220 * 1024 &&
-      (long long)row_tiles * g.NT >= 2ll * num_sms()) {
-    // warp-specialised form; the column tiles are split over grid.y only as far
-    // as needed to give every SM a CTA
+  if ((prec == WMC_BF16 || prec == WMC_FP16) && g.KB <= kWsMaxKB && ws_sm <= 226 * 1024) {
+    // warp-specialised form.  The column tiles are split over grid.y by the
+    // factor that minimises waves x per-CTA work, with the fixed part of a CTA
+    // (set-up and building A) counted as three column tiles.
     const uint16_t* img = prec == WMC_BF16 ? base : base + n16;
+    const long long sms = num_sms();
     int n_split = 1;
-    while (n_split < g.NT && (long long)row_tiles * n_split < num_sms()) n_split *= 2;
-    n_split = std::min(n_split, g.NT);
+    long long best = -1;
+    for (int ns = 1; ns <= g.NT; ns *= 2) {
+      const long long waves = ((long long)row_tiles * ns + sms - 1) / sms;
+      const long long cost = waves * (3 + (g.NT + ns - 1) / ns);
+      if (best < 0 || cost < best) {
+        best = cost;
+        n_split = ns;
+      }
+    }
     const dim3 ws_grid(row_tiles, n_split);
     if (prec == WMC_BF16) {
       cudaFuncSetAttribute(k_kernel_eval_tc_ws<WMC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_sm);
