@@ -23,11 +23,12 @@ namespace wmc {
 
 namespace {
 
-// number of momentum indices M in [-n_M/2, n_M/2) with M = r (mod Q)
-__device__ __forceinline__ int grid_count(int r, int Q, int n_M) {
-  const int M0 = -(n_M / 2);
-  const int M1 = M0 + ((((r - M0) % Q) + Q) % Q);
-  return M1 < n_M / 2 ? (n_M / 2 - 1 - M1) / Q + 1 : 0;
+// number of momentum indices M in [-n_M/2, n_M/2) with M = r (mod Q), r in
+// [0, Q), for n_M = a Q + b and r0 = -n_M/2 mod Q
+__device__ __forceinline__ int grid_count(int r, int Q, int a, int b, int r0) {
+  int off = r - r0;
+  if (off < 0) off += Q;
+  return a + (off < b ? 1 : 0);
 }
 
 // 1 - |tanh u| = 2 / (e^{2|u|} + 1), accurate where tanh saturates.
@@ -71,35 +72,62 @@ __global__ void k_potential_tanh(const float* __restrict__ theta, int n_pot, int
   V[q] = v;
 }
 
-// one thread per (potential, parameter): compensated FP32 sum over the cells
-__global__ void k_potential_tanh_vjp(const float* __restrict__ theta, int n_pot, int nb, int ns, int n_x, float dx,
-                                     float eps, const float* __restrict__ Vbar, float* __restrict__ theta_bar) {
+// One block per (potential, parameter): each thread keeps a compensated FP32
+// sum over a stride of the cells; the block then combines the (sum, error)
+// pairs in a fixed tree order, so the result is deterministic.
+constexpr int kVjpThreads = 256;
+
+__device__ __forceinline__ void pair_add(float& s, float& e, float s2, float e2) {
+  two_sum_acc(s, e, s2);
+  e = __fadd_rn(e, e2);
+}
+
+__global__ __launch_bounds__(kVjpThreads) void k_potential_tanh_vjp(const float* __restrict__ theta, int n_pot, int nb,
+                                                                    int ns, int n_x, float dx, float eps,
+                                                                    const float* __restrict__ Vbar,
+                                                                    float* __restrict__ theta_bar) {
+  __shared__ float red_s[kVjpThreads / 32], red_e[kVjpThreads / 32];
   const int P = 3 * nb + ns;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.x;
   if (q >= n_pot * P) return;
   const int b = q / P, j = q % P;
   const float* th = theta + (size_t)b * P;
   const float* vb = Vbar + (size_t)b * n_x;
   const float inv = 1.f / eps, L = (float)n_x * dx;
   float s = 0.f, e = 0.f;
-  for (int l = 0; l < n_x; ++l) {
-    const float x = ((float)l + 0.5f) * dx;
-    float d;
-    if (j < 3 * nb) {
-      const int k = j % nb;
-      const float hk = th[k], wk = th[nb + k], ck = th[2 * nb + k];
+  if (j < 3 * nb) {
+    const int k = j % nb;
+    const float hk = th[k], wk = th[nb + k], ck = th[2 * nb + k];
+    for (int l = threadIdx.x; l < n_x; l += kVjpThreads) {
+      const float x = ((float)l + 0.5f) * dx;
       const float up = (x - ck + 0.5f * wk) * inv, um = (x - ck - 0.5f * wk) * inv;
-      const float sp = sech2(up), sm = sech2(um);
-      if (j < nb) d = 0.5f * tanh_diff(up, um);               // d/d h_k
-      else if (j < 2 * nb) d = hk * (sp + sm) * 0.25f * inv;  // d/d w_k
-      else d = hk * (sm - sp) * 0.5f * inv;                   // d/d c_k
-    } else {
-      const int sidx = j - 3 * nb;
-      d = window(x, L * sidx / ns, L * (sidx + 1) / ns, inv);  // d/d o_s
+      float d;
+      if (j < nb) d = 0.5f * tanh_diff(up, um);                           // d/d h_k
+      else if (j < 2 * nb) d = hk * (sech2(up) + sech2(um)) * 0.25f * inv;  // d/d w_k
+      else d = hk * (sech2(um) - sech2(up)) * 0.5f * inv;                  // d/d c_k
+      two_sum_acc(s, e, vb[l] * d);
     }
-    two_sum_acc(s, e, vb[l] * d);
+  } else {
+    const int sidx = j - 3 * nb;
+    const float a = L * sidx / ns, bb = L * (sidx + 1) / ns;
+    for (int l = threadIdx.x; l < n_x; l += kVjpThreads) {
+      const float x = ((float)l + 0.5f) * dx;
+      two_sum_acc(s, e, vb[l] * window(x, a, bb, inv));  // d/d o_s
+    }
   }
-  theta_bar[q] = s + e;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, s, off), e2 = __shfl_down_sync(0xffffffffu, e, off);
+    pair_add(s, e, s2, e2);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red_s[warp] = s, red_e[warp] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float ts = red_s[0], te = red_e[0];
+    for (int w = 1; w < kVjpThreads / 32; ++w) pair_add(ts, te, red_s[w], red_e[w]);
+    theta_bar[q] = ts + te;
+  }
 }
 
 // ---------------------------------------------------------------- Abar
@@ -108,7 +136,7 @@ __global__ void k_potential_tanh_vjp(const float* __restrict__ theta, int n_pot,
 // staged in shared memory (compensated FP32 in chunks of 32 terms).
 constexpr int kAdjWarps = 8;
 
-template <int C>
+template <int C, int R>  // R rows per warp share each sine load
 __global__ __launch_bounds__(kAdjWarps * 32) void k_adj_abar(int Q, int n_M, int rows, const float* __restrict__ VWh,
                                                              const float* __restrict__ gVW,
                                                              const float* __restrict__ g_gamma,
@@ -117,52 +145,75 @@ __global__ __launch_bounds__(kAdjWarps * 32) void k_adj_abar(int Q, int n_M, int
   extern __shared__ float s_mem[];
   const int h = Q / 2;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* s_Bt = s_mem;                                 // [h][32 C]: s_Bt[r][kk] = S[kk+1][r]
-  float* s_g = s_mem + h * 32 * C + wid * 32 * C;     // Gbar of this warp's row
-  if ((int)(blockIdx.x * kAdjWarps) >= rows) return;
+  const int ca = n_M / Q, cb = n_M - ca * Q, cr0 = ((-(n_M / 2)) % Q + Q) % Q;
+  float* s_Bt = s_mem;                                   // [h][32 C]: s_Bt[r][kk] = S[kk+1][r]
+  float* s_g = s_mem + h * 32 * C + wid * R * 32 * C;    // Gbar of this warp's rows
+  if ((int)(blockIdx.x * kAdjWarps * R) >= rows) return;
   for (int q = threadIdx.x; q < h * 32 * C; q += blockDim.x) {
     const int r = q / (32 * C), kk = q % (32 * C);
     s_Bt[q] = kk < h - 1 ? __ldg(B + (size_t)kk * Np + r) : 0.f;
   }
   __syncthreads();
-  for (int row = blockIdx.x * kAdjWarps + wid; row < rows; row += gridDim.x * kAdjWarps) {
-    const float gg = g_gamma ? __ldg(g_gamma + row) : 0.f;
+  for (int row0 = (blockIdx.x * kAdjWarps + wid) * R; row0 < rows; row0 += gridDim.x * kAdjWarps * R) {
 #pragma unroll
-    for (int cc = 0; cc < C; ++cc) {
-      const int r = lane + 32 * cc;
-      float g = 0.f;
-      if (r < h) {
-        if (gVW) g = __ldg(gVW + (size_t)row * h + r);
-        if (gg != 0.f && r > 0) {
-          const float v = __ldg(VWh + (size_t)row * h + r);
-          const int dg = v > 0.f ? grid_count(r, Q, n_M) : (v < 0.f ? -grid_count(Q - r, Q, n_M) : 0);
-          g = __fadd_rn(g, __fmul_rn(gg, (float)dg));
+    for (int gq = 0; gq < R; ++gq) {
+      const int row = row0 + gq;
+      const bool ok = row < rows;
+      const float gg = (ok && g_gamma) ? __ldg(g_gamma + row) : 0.f;
+#pragma unroll
+      for (int cc = 0; cc < C; ++cc) {
+        const int r = lane + 32 * cc;
+        float g = 0.f;
+        if (ok && r < h) {
+          if (gVW) g = __ldg(gVW + (size_t)row * h + r);
+          if (gg != 0.f && r > 0) {
+            const float v = __ldg(VWh + (size_t)row * h + r);
+            const int dg = v > 0.f ? grid_count(r, Q, ca, cb, cr0) : (v < 0.f ? -grid_count(Q - r, Q, ca, cb, cr0) : 0);
+            g = __fadd_rn(g, __fmul_rn(gg, (float)dg));
+          }
         }
+        s_g[gq * 32 * C + r] = g;
       }
-      s_g[r] = g;
     }
     __syncwarp();
-    float sacc[C], eacc[C];
+    float sacc[R][C], eacc[R][C];
 #pragma unroll
-    for (int q = 0; q < C; ++q) sacc[q] = eacc[q] = 0.f;
+    for (int gq = 0; gq < R; ++gq)
+#pragma unroll
+      for (int q = 0; q < C; ++q) sacc[gq][q] = eacc[gq][q] = 0.f;
     for (int r0 = 0; r0 < h; r0 += 32) {
-      float part[C];
+      float part[R][C];
 #pragma unroll
-      for (int q = 0; q < C; ++q) part[q] = 0.f;
+      for (int gq = 0; gq < R; ++gq)
+#pragma unroll
+        for (int q = 0; q < C; ++q) part[gq][q] = 0.f;
       const int r1 = min(r0 + 32, h);
       for (int r = r0; r < r1; ++r) {
-        const float g = s_g[r];
         const float* bt = s_Bt + r * 32 * C;
+        float bv[C];
 #pragma unroll
-        for (int q = 0; q < C; ++q) part[q] = fmaf(g, bt[lane + 32 * q], part[q]);
+        for (int q = 0; q < C; ++q) bv[q] = bt[lane + 32 * q];
+#pragma unroll
+        for (int gq = 0; gq < R; ++gq) {
+          const float g = s_g[gq * 32 * C + r];
+#pragma unroll
+          for (int q = 0; q < C; ++q) part[gq][q] = fmaf(g, bv[q], part[gq][q]);
+        }
       }
 #pragma unroll
-      for (int q = 0; q < C; ++q) two_sum_acc(sacc[q], eacc[q], part[q]);
+      for (int gq = 0; gq < R; ++gq)
+#pragma unroll
+        for (int q = 0; q < C; ++q) two_sum_acc(sacc[gq][q], eacc[gq][q], part[gq][q]);
     }
 #pragma unroll
-    for (int q = 0; q < C; ++q) {
-      const int kk = lane + 32 * q;
-      if (kk < h - 1) Abar[(size_t)row * h + kk] = __fmul_rn(c, __fadd_rn(sacc[q], eacc[q]));
+    for (int gq = 0; gq < R; ++gq) {
+      const int row = row0 + gq;
+      if (row >= rows) break;
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        const int kk = lane + 32 * q;
+        if (kk < h - 1) Abar[(size_t)row * h + kk] = __fmul_rn(c, __fadd_rn(sacc[gq][q], eacc[gq][q]));
+      }
     }
     __syncwarp();
   }
@@ -170,21 +221,38 @@ __global__ __launch_bounds__(kAdjWarps * 32) void k_adj_abar(int Q, int n_M, int
 
 // ---------------------------------------------------------------- Vbar
 // Vbar[b][l] = sum_{m=1}^{h-1} Abar[b][l-m][m-1] - Abar[b][l+m][m-1], rows of
-// potential b at b n_x .. b n_x + n_x - 1, V = 0 outside the domain.
-__global__ void k_adj_vbar(int Q, int n_x, int n_pot, const float* __restrict__ Abar, float* __restrict__ Vbar) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= (long long)n_pot * n_x) return;
+// potential b at b n_x .. b n_x + n_x - 1, V = 0 outside the domain.  A block
+// computes kVbarTile consecutive cells of one potential: the Abar rows they
+// draw on, [l0 - h + 1, l0 + kVbarTile + h - 1), pass through shared memory in
+// coalesced chunks of kVbarChunk rows, and thread l adds A[j][l - j - 1] and
+// subtracts A[j][j - l - 1] from each staged row j (compensated FP32, rows in
+// increasing order).
+constexpr int kVbarTile = 256, kVbarChunk = 32;
+
+__global__ __launch_bounds__(kVbarTile) void k_adj_vbar(int Q, int n_x, int n_pot, const float* __restrict__ Abar,
+                                                        float* __restrict__ Vbar) {
+  extern __shared__ float s_A[];  // kVbarChunk x h
   const int h = Q / 2;
-  const int b = (int)(q / n_x), l = (int)(q % n_x);
+  const int tiles = (n_x + kVbarTile - 1) / kVbarTile;
+  const int b = blockIdx.x / tiles, l0 = (blockIdx.x % tiles) * kVbarTile;
+  if (b >= n_pot) return;
+  const int l = l0 + threadIdx.x;
   const float* Ab = Abar + (size_t)b * n_x * h;
+  const int j_lo = max(0, l0 - (h - 1)), j_hi = min(n_x, l0 + kVbarTile + h - 1);
   float s = 0.f, e = 0.f;
-  for (int m = 1; m <= h - 1; ++m) {
-    float t = 0.f;
-    if (l - m >= 0) t = __ldg(Ab + (size_t)(l - m) * h + (m - 1));
-    if (l + m < n_x) t = __fsub_rn(t, __ldg(Ab + (size_t)(l + m) * h + (m - 1)));
-    two_sum_acc(s, e, t);
+  for (int j0 = j_lo; j0 < j_hi; j0 += kVbarChunk) {
+    const int nj = min(kVbarChunk, j_hi - j0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nj * h; q += kVbarTile) s_A[q] = __ldg(Ab + (size_t)j0 * h + q);
+    __syncthreads();
+    for (int jj = 0; jj < nj; ++jj) {
+      const int j = j0 + jj;
+      const int mp = l - j, mn = j - l;  // row j feeds Vbar[j + m] with +, Vbar[j - m] with -
+      if (mp >= 1 && mp <= h - 1) two_sum_acc(s, e, s_A[jj * h + mp - 1]);
+      else if (mn >= 1 && mn <= h - 1) two_sum_acc(s, e, -s_A[jj * h + mn - 1]);
+    }
   }
-  Vbar[q] = s + e;
+  if (l < n_x) Vbar[(size_t)b * n_x + l] = s + e;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -200,7 +268,7 @@ cudaError_t launch_potential_tanh_vjp(const float* theta, int n_pot, int nb, int
                                       const float* Vbar, float* theta_bar, cudaStream_t s) {
   const int n = n_pot * (3 * nb + ns);
   if (n <= 0) return cudaSuccess;
-  k_potential_tanh_vjp<<<(n + 127) / 128, 128, 0, s>>>(theta, n_pot, nb, ns, n_x, dx, eps, Vbar, theta_bar);
+  k_potential_tanh_vjp<<<n, kVjpThreads, 0, s>>>(theta, n_pot, nb, ns, n_x, dx, eps, Vbar, theta_bar);
   return cudaGetLastError();
 }
 
@@ -211,22 +279,32 @@ cudaError_t launch_kernel_vjp(const wmc_params& p, int n_pot, const float* VWh, 
   if (rows <= 0) return cudaSuccess;
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   const int C = h <= 32 ? 1 : (h <= 64 ? 2 : 4);
-  const size_t sm = sizeof(float) * ((size_t)h * 32 * C + (size_t)kAdjWarps * 32 * C);
-  int blocks = (rows + kAdjWarps - 1) / kAdjWarps;
+  const int R = (long long)rows >= 4ll * num_sms() * kAdjWarps * 4 ? 4 : 1;
+  const size_t sm = sizeof(float) * ((size_t)h * 32 * C + (size_t)kAdjWarps * R * 32 * C);
+  int blocks = (rows + kAdjWarps * R - 1) / (kAdjWarps * R);
   if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
-#define WMC_LAUNCH_ABAR(CC)                                                                                   \
-  do {                                                                                                        \
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_adj_abar<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-    k_adj_abar<CC><<<blocks, kAdjWarps * 32, sm, s>>>(p.Q, p.n_M, rows, VWh, gVW, g_gamma, B, L.Np, c, Abar);     \
+#define WMC_LAUNCH_ABAR(CC, RR)                                                                              \
+  do {                                                                                                       \
+    if (sm > 48 * 1024)                                                                                      \
+      cudaFuncSetAttribute(k_adj_abar<CC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);        \
+    k_adj_abar<CC, RR><<<blocks, kAdjWarps * 32, sm, s>>>(p.Q, p.n_M, rows, VWh, gVW, g_gamma, B, L.Np, c, Abar); \
   } while (0)
-  if (C == 1) WMC_LAUNCH_ABAR(1);
-  else if (C == 2) WMC_LAUNCH_ABAR(2);
-  else WMC_LAUNCH_ABAR(4);
+  if (R == 4) {
+    if (C == 1) WMC_LAUNCH_ABAR(1, 4);
+    else if (C == 2) WMC_LAUNCH_ABAR(2, 4);
+    else WMC_LAUNCH_ABAR(4, 4);
+  } else {
+    if (C == 1) WMC_LAUNCH_ABAR(1, 1);
+    else if (C == 2) WMC_LAUNCH_ABAR(2, 1);
+    else WMC_LAUNCH_ABAR(4, 1);
+  }
 #undef WMC_LAUNCH_ABAR
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const long long n = (long long)rows;
-  k_adj_vbar<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.Q, p.n_x, n_pot, Abar, Vbar);
+  const int tiles = (p.n_x + kVbarTile - 1) / kVbarTile;
+  const size_t vsm = sizeof(float) * (size_t)kVbarChunk * h;
+  if (vsm > 48 * 1024) cudaFuncSetAttribute(k_adj_vbar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+  k_adj_vbar<<<(unsigned)((long long)tiles * n_pot), kVbarTile, vsm, s>>>(p.Q, p.n_x, n_pot, Abar, Vbar);
   return cudaGetLastError();
 }
 

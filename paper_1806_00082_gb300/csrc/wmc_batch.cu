@@ -82,7 +82,7 @@ BatchLayout batch_layout(const wmc_params* ps, int n) {
     if (ps[s].n_M > L.NM) L.NM = ps[s].n_M;
   }
   L.n_blk = (int)((L.n_cells + kScanCells - 1) / kScanCells);
-  L.max_items = 2 * L.n_cells + (1ll << 21);
+  L.max_items = 2 * L.n_cells + (1ll << 23);
   const size_t nc = (size_t)L.n_cells;
   size_t o = 0;
   L.header = o; o = al256(o + sizeof(DevHeader));
@@ -472,11 +472,11 @@ __global__ __launch_bounds__(kBatchRowWarps * 32) void k_b_kernel_rows(
     }
     __syncwarp();
     const int r0 = ((-(n_M / 2)) % Q + Q) % Q;
-    auto xpos = [&](int k) { return positive_part_smem(s_row, Q, (r0 + k) % Q); };
+    auto xres = [&](int rr) { return positive_part_smem(s_row, Q, rr); };
     double g;
     int sc;
     long long tot;
-    warp_row_cdf(xpos, n_M, s.log2_nM, lane, cdf + (size_t)row * NM, g, sc, tot);
+    warp_row_cdf(xres, Q, r0, n_M, s.log2_nM, lane, cdf + (size_t)row * NM, g, sc, tot);
     if (lane == 0) {
       gamma[row] = g;
       const unsigned long long thr = g > 0.0 ? event_threshold(g, s.dt, flags) : 0ull;
@@ -505,28 +505,32 @@ struct BatchStepArgs {
   int NM, per_thread;
 };
 
-__global__ __launch_bounds__(256) void k_b_step(BatchStepArgs a) {
+// One warp per work item: an item is a run of 32 x per_thread ids of one row
+// (quad-aligned to the global ids), so a sparse row costs one warp, not a
+// block.  Each warp owns its slice of shared memory (row prefix, signed
+// counts, and the three output rows i-1, i, i+1 it accumulates into) and
+// takes items from the global ticket without block-wide barriers.
+constexpr int kBStepWarps = 8;
+
+__global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a) {
   extern __shared__ int smem[];
   const int NM = a.NM;
-  int* s_pre = smem;
+  const int tid = threadIdx.x, lane = tid & 31;
+  int* s_pre = smem + (size_t)(tid >> 5) * (5 * NM + 1);
   int* s_n = s_pre + (NM + 1);
   int* s_acc = s_n + NM;
-  uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_acc + 3 * NM);
-  uint32_t* s_hi = s_lo + NM;
-  __shared__ int s_item;
-  __shared__ unsigned long long s_red[5][8];
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ unsigned long long s_red[5][kBStepWarps];
   const uint32_t t = a.hdr->step;
   const int n_items = a.hdr->n_items;
   const int PER = a.per_thread;
-  const int chunk = 256 * PER;
+  const int chunk = 32 * PER;
   unsigned long long pairs = 0, absorbed = 0, dropped = 0;
   long long abs_signed = 0, drop_signed = 0;
 
   for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(&a.hdr->item_ticket, 1u);
-    __syncthreads();
-    const int item = s_item;
+    int item = 0;
+    if (lane == 0) item = (int)atomicAdd(&a.hdr->item_ticket, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_items) break;
     const int2 it = __ldg(a.items + item);
     const long long cg = it.x;
@@ -541,17 +545,15 @@ __global__ __launch_bounds__(256) void k_b_step(BatchStepArgs a) {
     const unsigned long long thr_p = i + 1 < n_x ? __ldg(a.thr_cell + cg + 1) : 0ull;
     const uint32_t sim = S.sim, k0 = S.k0, k1 = S.k1;
     const int32_t* hrow = a.hist_in + S.hist_off;
-    for (int q = tid; q < 3 * n_M; q += 256) s_acc[q] = 0;
-    for (int k = tid; k < n_M; k += 256) {
-      s_lo[k] = __ldg(a.xlo + S.tab_off + k);
-      s_hi[k] = __ldg(a.xhi + S.tab_off + k);
-    }
-    if ((tid >> 5) == 0) warp_row_prefix(hrow, i, n_M, s_n, s_pre, lane);
-    __syncthreads();
+    const uint32_t* xlo = a.xlo + S.tab_off;
+    const uint32_t* xhi = a.xhi + S.tab_off;
+    for (int q = lane; q < 3 * n_M; q += 32) s_acc[q] = 0;
+    warp_row_prefix(hrow, i, n_M, s_n, s_pre, lane);
+    __syncwarp();
 
     const uint32_t Ti = (uint32_t)s_pre[n_M];
     const unsigned long long A = base & ~3u;
-    const unsigned long long lo64 = A + (unsigned long long)ch * chunk + (unsigned long long)tid * PER;
+    const unsigned long long lo64 = A + (unsigned long long)ch * chunk + (unsigned long long)lane * PER;
     const unsigned long long row_end = (unsigned long long)base + Ti;
     const unsigned long long g0_64 = lo64 > base ? lo64 : base;
     const unsigned long long g1_64 = lo64 + PER < row_end ? lo64 + PER : row_end;
@@ -564,7 +566,7 @@ __global__ __launch_bounds__(256) void k_b_step(BatchStepArgs a) {
       k = bucket_of(s_pre, n_M, (int)(g0 - base));
       uint32_t end_g = base + (uint32_t)s_pre[k + 1];
       sgn = s_n[k] > 0 ? 1 : -1;
-      uint32_t lo = s_lo[k], hi = s_hi[k];
+      uint32_t lo = __ldg(xlo + k), hi = __ldg(xhi + k);
       dir = drift_dir(lo, hi);
       unsigned long long thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
       for (uint32_t q = g0 >> 2; q <= (g1 - 1u) >> 2; ++q) {
@@ -593,8 +595,8 @@ __global__ __launch_bounds__(256) void k_b_step(BatchStepArgs a) {
             do { ++k; } while (base + (uint32_t)s_pre[k + 1] <= id);
             end_g = base + (uint32_t)s_pre[k + 1];
             sgn = s_n[k] > 0 ? 1 : -1;
-            lo = s_lo[k];
-            hi = s_hi[k];
+            lo = __ldg(xlo + k);
+            hi = __ldg(xhi + k);
             dir = drift_dir(lo, hi);
             thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
           }
@@ -645,17 +647,17 @@ __global__ __launch_bounds__(256) void k_b_step(BatchStepArgs a) {
         }
       }
     }
-    __syncthreads();
+    __syncwarp();
     int32_t* orow_base = a.hist_out + S.hist_off;
-    for (int q = tid; q < 3 * n_M; q += 256) {
+    for (int q = lane; q < 3 * n_M; q += 32) {
       const int v = s_acc[q];
       if (v) {
         const int dd = q / n_M, kc = q - dd * n_M;
         atomicAdd(orow_base + (size_t)(i - 1 + dd) * n_M + kc, v);
       }
     }
+    __syncwarp();
   }
-
   const int wid = tid >> 5;
   unsigned long long vals[5] = {pairs, absorbed, (unsigned long long)abs_signed, dropped,
                                 (unsigned long long)drop_signed};
@@ -669,7 +671,7 @@ __global__ __launch_bounds__(256) void k_b_step(BatchStepArgs a) {
   __syncthreads();
   if (tid < 5) {
     unsigned long long v = 0;
-    for (int w = 0; w < 8; ++w) v += s_red[tid][w];
+    for (int w = 0; w < kBStepWarps; ++w) v += s_red[tid][w];
     if (v) {
       unsigned long long* dst[5] = {&a.hdr->pairs, &a.hdr->absorbed,
                                     reinterpret_cast<unsigned long long*>(&a.hdr->absorbed_signed), &a.hdr->dropped,
@@ -691,13 +693,13 @@ __global__ __launch_bounds__(256) void k_b_step(BatchStepArgs a) {
 __global__ void k_b_set_step(DevHeader* hdr, uint32_t step) { hdr->step = step; }
 
 // ---------------------------------------------------------------- host driver
-size_t b_step_smem(int NM) { return sizeof(int) * (size_t)(NM + 1 + NM + 3 * NM) + 2 * sizeof(uint32_t) * NM; }
+size_t b_step_smem(int NM) { return sizeof(int) * (size_t)kBStepWarps * (5 * NM + 1); }
 
 int b_step_grid(int NM) {
   int per_sm = 0;
   const size_t sm = b_step_smem(NM);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_b_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_step, 256, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_step, kBStepWarps * 32, sm);
   if (per_sm < 1) per_sm = 1;
   return per_sm * num_sms();
 }
@@ -705,7 +707,7 @@ int b_step_grid(int NM) {
 cudaError_t b_one_step(const BatchLayout& L, const BatchView& v, int n, const float* V, const int32_t* in,
                        int32_t* out, int per_thread, int grid, cudaStream_t s) {
   const long long nc = L.n_cells;
-  const int chunk = 256 * per_thread;
+  const int chunk = 32 * per_thread;  // ids per warp item
   k_b_rows<<<(unsigned)((nc * 32 + 255) / 256), 256, 0, s>>>(in, v.descs, v.cell_sim, v.D, nc, v.T, v.reach);
   k_b_scan1<<<L.n_blk, kScanThreads, 0, s>>>(v.T, v.reach, v.descs, v.cell_sim, nc, chunk, v.blk);
   k_b_scan2<<<1, kScanThreads, 0, s>>>(v.blk, L.n_blk, L.max_items, v.hdr, 1);
@@ -741,7 +743,7 @@ cudaError_t b_one_step(const BatchLayout& L, const BatchView& v, int n, const fl
   a.hdr = v.hdr;
   a.NM = L.NM;
   a.per_thread = per_thread;
-  k_b_step<<<grid, 256, b_step_smem(L.NM), s>>>(a);
+  k_b_step<<<grid, kBStepWarps * 32, b_step_smem(L.NM), s>>>(a);
   return cudaGetLastError();
 }
 

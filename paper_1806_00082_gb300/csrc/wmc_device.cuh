@@ -63,18 +63,32 @@ __device__ __forceinline__ float positive_part_smem(const float* v, int Q, int r
   return x > 0.f ? x : 0.f;
 }
 
+// total 2^-s as a double: the conversion of total rounds to nearest, the
+// power of two (built from its bits) scales exactly; two FP64 operations,
+// where the library ldexp costs many on the narrow FP64 pipe.
+__device__ __forceinline__ double scaled_total(long long total, int s) {
+  if (s > -1023 && s < 1023) return __dmul_rn((double)total, __longlong_as_double((long long)(1023 - s) << 52));
+  return ldexp((double)total, -s);
+}
+
 // The fixed-point CDF of one row held in a warp: lane l takes the contiguous
 // columns k in [l E, (l+1) E), E = ceil(n_M / 32), so a row needs one warp
 // reduction (maximum), one warp scan of the lane totals and E sequential
 // integer additions per lane; lanes write contiguous runs of the row-major CDF.
-// xpos(k) returns max(V_W(k), 0) for column k.
-template <class XPos>
-__device__ __forceinline__ void warp_row_cdf(XPos xpos, int n_M, int log2_nM, int lane, long long* __restrict__ out,
-                                             double& gamma_out, int& scale_out, long long& total_out) {
+// Column k has momentum residue (r0 + k) mod Q (r0 = -n_M/2 mod Q); xres(rr)
+// returns max(V_W, 0) at residue rr, stepped incrementally along a lane's run.
+template <class XRes>
+__device__ __forceinline__ void warp_row_cdf(XRes xres, int Q, int r0, int n_M, int log2_nM, int lane,
+                                             long long* __restrict__ out, double& gamma_out, int& scale_out,
+                                             long long& total_out) {
   const int E = (n_M + 31) >> 5;
-  const int k0 = lane * E, k1 = min(k0 + E, n_M);
+  const int k0 = min(lane * E, n_M), k1 = min(k0 + E, n_M);
+  const int rr0 = (r0 + k0) % Q;
   uint32_t mx = 0u;
-  for (int k = k0; k < k1; ++k) mx = max(mx, __float_as_uint(xpos(k)));
+  for (int k = k0, rr = rr0; k < k1; ++k) {
+    mx = max(mx, __float_as_uint(xres(rr)));
+    if (++rr == Q) rr = 0;
+  }
   mx = __reduce_max_sync(0xffffffffu, mx);
   if (mx == 0u) {
     if (out)
@@ -86,7 +100,10 @@ __device__ __forceinline__ void warp_row_cdf(XPos xpos, int n_M, int log2_nM, in
   }
   const int s = 61 - log2_nM - floor_log2_pos(__uint_as_float(mx));
   long long local = 0;
-  for (int k = k0; k < k1; ++k) local += quantise(xpos(k), s);
+  for (int k = k0, rr = rr0; k < k1; ++k) {
+    local += quantise(xres(rr), s);
+    if (++rr == Q) rr = 0;
+  }
   long long incl = local;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -96,12 +113,13 @@ __device__ __forceinline__ void warp_row_cdf(XPos xpos, int n_M, int log2_nM, in
   const long long total = __shfl_sync(0xffffffffu, incl, 31);
   if (out) {
     long long run = incl - local;
-    for (int k = k0; k < k1; ++k) {
-      run += quantise(xpos(k), s);
+    for (int k = k0, rr = rr0; k < k1; ++k) {
+      run += quantise(xres(rr), s);
       out[k] = run;
+      if (++rr == Q) rr = 0;
     }
   }
-  gamma_out = ldexp((double)total, -s);
+  gamma_out = scaled_total(total, s);
   scale_out = s;
   total_out = total;
 }

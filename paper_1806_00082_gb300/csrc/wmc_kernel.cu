@@ -154,11 +154,11 @@ __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2
   if (row >= n_rows) return;
   const float* v = VWh + (size_t)row * (Q / 2);
   const int r0 = ((-(n_M / 2)) % Q + Q) % Q;   // r of column k = 0
-  auto xpos = [&](int k) { return positive_part(v, Q, (r0 + k) % Q); };
+  auto xres = [&](int rr) { return positive_part(v, Q, rr); };
   double g;
   int sc;
   long long tot;
-  warp_row_cdf(xpos, n_M, log2_nM, lane, cdf ? cdf + (size_t)row * n_M : nullptr, g, sc, tot);
+  warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, cdf ? cdf + (size_t)row * n_M : nullptr, g, sc, tot);
   if (lane == 0) {
     gamma[row] = g;
     if (scale) scale[row] = sc;
@@ -166,6 +166,102 @@ __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2
       const unsigned long long thr = g > 0.0 ? event_threshold(g, dt, flags) : 0ull;
       gthr[row] = thr;
       if (thr_cell) thr_cell[__ldg(occ + row)] = thr;
+    }
+  }
+}
+
+// gamma (and the scale s) alone, from the folded row: column r of the half
+// period carries V_W at the cnt(r) grid momenta M = r (mod Q) and -V_W at the
+// cnt(Q - r) momenta M = -r (mod Q).  The maximum over the grid and the sum of
+// the quantised positive parts are the same integers the full CDF pass forms
+// (same s, exact int64 sums), so gamma is bit-identical; the row is read once,
+// coalesced, instead of once per grid column.
+// number of M in [-n_M/2, n_M/2) with M = rr (mod Q), rr in [0, Q), for
+// n_M = a Q + b and r0 = -n_M/2 mod Q: a, plus one where the grid's first b
+// columns reach the residue
+__device__ __forceinline__ int residue_count(int rr, int Q, int a, int b, int r0) {
+  int off = rr - r0;
+  if (off < 0) off += Q;
+  return a + (off < b ? 1 : 0);
+}
+
+// C > 0: h <= 32 C, lane l holds the columns r = l + 32 c of a row and their
+// two residue multiplicities in registers across the rows it visits; C = 0:
+// any h, multiplicities formed per element.
+template <int C>
+__global__ __launch_bounds__(kCdfWarps * 32) void k_gamma_folded(int Q, int log2_nM, int ca, int cb, int r0,
+                                                                 const float* __restrict__ VWh, int n_rows,
+                                                                 double* __restrict__ gamma, int* __restrict__ scale) {
+  const int lane = threadIdx.x & 31;
+  const int h = Q / 2;
+  constexpr int CR = C > 0 ? C : 1;
+  int cp[CR], cn[CR];  // multiplicities of +V_W (residue r) and -V_W (residue Q - r)
+#pragma unroll
+  for (int c = 0; c < CR; ++c) {
+    const int r = lane + 32 * c;
+    const bool in = C > 0 && r >= 1 && r < h;
+    cp[c] = in ? residue_count(r, Q, ca, cb, r0) : 0;
+    cn[c] = in ? residue_count(Q - r, Q, ca, cb, r0) : 0;
+  }
+  for (int row = blockIdx.x * kCdfWarps + (threadIdx.x >> 5); row < n_rows; row += gridDim.x * kCdfWarps) {
+    const float* v = VWh + (size_t)row * h;
+    uint32_t mx = 0u;
+    long long local = 0;
+    if (C > 0) {
+      float x[CR];
+#pragma unroll
+      for (int c = 0; c < CR; ++c) {
+        const int r = lane + 32 * c;
+        x[c] = r < h ? __ldg(v + r) : 0.f;
+        const float xp = x[c] > 0.f && cp[c] ? x[c] : 0.f, xn = x[c] < 0.f && cn[c] ? -x[c] : 0.f;
+        mx = max(mx, max(__float_as_uint(xp), __float_as_uint(xn)));
+      }
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (mx == 0u) {
+        if (lane == 0) {
+          gamma[row] = 0.0;
+          if (scale) scale[row] = 0;
+        }
+        continue;
+      }
+      const int s = 61 - log2_nM - floor_log2_pos(__uint_as_float(mx));
+#pragma unroll
+      for (int c = 0; c < CR; ++c) {
+        if (x[c] > 0.f) local += (long long)cp[c] * quantise(x[c], s);
+        else if (x[c] < 0.f) local += (long long)cn[c] * quantise(-x[c], s);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+      if (lane == 0) {
+        gamma[row] = scaled_total(local, s);
+        if (scale) scale[row] = s;
+      }
+    } else {
+      for (int r = 1 + lane; r < h; r += 32) {
+        const float x = __ldg(v + r);
+        if (x > 0.f && residue_count(r, Q, ca, cb, r0) > 0) mx = max(mx, __float_as_uint(x));
+        if (x < 0.f && residue_count(Q - r, Q, ca, cb, r0) > 0) mx = max(mx, __float_as_uint(-x));
+      }
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (mx == 0u) {
+        if (lane == 0) {
+          gamma[row] = 0.0;
+          if (scale) scale[row] = 0;
+        }
+        continue;
+      }
+      const int s = 61 - log2_nM - floor_log2_pos(__uint_as_float(mx));
+      for (int r = 1 + lane; r < h; r += 32) {
+        const float x = __ldg(v + r);
+        if (x > 0.f) local += (long long)residue_count(r, Q, ca, cb, r0) * quantise(x, s);
+        else if (x < 0.f) local += (long long)residue_count(Q - r, Q, ca, cb, r0) * quantise(-x, s);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+      if (lane == 0) {
+        gamma[row] = scaled_total(local, s);
+        if (scale) scale[row] = s;
+      }
     }
   }
 }
@@ -187,7 +283,9 @@ static int ceil_log2(int n) {
 constexpr int kRowWarps = 8;
 constexpr int kRowMaxH = 128;
 
-template <int C>  // output columns per lane: h <= 32 C
+// A warp accumulates R rows together, sharing each sine load among them (R = 4
+// when there are rows enough to fill the GPU that way, else 1).
+template <int C, int R>  // output columns per lane: h <= 32 C
 __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
     const float* __restrict__ V, int n_x, int bc, int Q, int n_M, int log2_nM, const int* __restrict__ occ,
     const int* __restrict__ n_occ_dev, int n_occ_host, const float* __restrict__ B, int Np, float c,
@@ -197,80 +295,103 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
   extern __shared__ float s_mem[];
   const int h = Q / 2;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* s_B = s_mem;                                   // (h - 1) x h, row m - 1
-  float* s_row = s_mem + (h - 1) * h + wid * 2 * 32 * C;  // kernel row (h floats)
-  float* s_dv = s_row + 32 * C;                         // dV(m) at s_dv[m - 1]
+  float* s_B = s_mem;                                             // (h - 1) x h, row m - 1
+  float* s_row = s_mem + (h - 1) * h + wid * (R + 1) * 32 * C;    // kernel row (h floats)
+  float* s_dv = s_row + 32 * C;                                   // row g: dV(m) at s_dv[g 32 C + m - 1]
   const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
-  if ((int)(blockIdx.x * kRowWarps) >= n_rows) return;
+  if ((int)(blockIdx.x * kRowWarps * R) >= n_rows) return;
   for (int q = threadIdx.x; q < (h - 1) * h; q += blockDim.x) {
     const int m1 = q / h, r = q - m1 * h;
     s_B[q] = __ldg(B + (size_t)m1 * Np + r);
   }
   __syncthreads();
   const int r0 = ((-(n_M / 2)) % Q + Q) % Q;
-  for (int row = blockIdx.x * kRowWarps + wid; row < n_rows; row += gridDim.x * kRowWarps) {
-    const int i = occ ? __ldg(occ + row) : row % n_x;
-    const float* Vr = occ ? V : V + (size_t)(row / n_x) * n_x;
+  for (int row0 = (blockIdx.x * kRowWarps + wid) * R; row0 < n_rows; row0 += gridDim.x * kRowWarps * R) {
 #pragma unroll
-    for (int q = 0; q < C; ++q) {
-      const int m = lane + 1 + 32 * q;
-      s_dv[m - 1] = m <= h - 1 ? __fsub_rn(pot(Vr, n_x, bc, (long long)i + m), pot(Vr, n_x, bc, (long long)i - m))
+    for (int g = 0; g < R; ++g) {
+      const int row = row0 + g;
+      const bool ok = row < n_rows;
+      const int i = ok ? (occ ? __ldg(occ + row) : row % n_x) : 0;
+      const float* Vr = (occ || !ok) ? V : V + (size_t)(row / n_x) * n_x;
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        const int m = lane + 1 + 32 * q;
+        s_dv[g * 32 * C + m - 1] =
+            (ok && m <= h - 1) ? __fsub_rn(pot(Vr, n_x, bc, (long long)i + m), pot(Vr, n_x, bc, (long long)i - m))
                                : 0.f;
+      }
     }
     __syncwarp();
-    float sacc[C], eacc[C];
+    float sacc[R][C], eacc[R][C];
 #pragma unroll
-    for (int cc = 0; cc < C; ++cc) sacc[cc] = eacc[cc] = 0.f;
+    for (int g = 0; g < R; ++g)
+#pragma unroll
+      for (int cc = 0; cc < C; ++cc) sacc[g][cc] = eacc[g][cc] = 0.f;
     for (int m0 = 1; m0 <= h - 1; m0 += 32) {   // chunks of 32 window terms
-      float part[C];
+      float part[R][C];
 #pragma unroll
-      for (int cc = 0; cc < C; ++cc) part[cc] = 0.f;
+      for (int g = 0; g < R; ++g)
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) part[g][cc] = 0.f;
       const int m1 = min(m0 + 32, h);
       for (int m = m0; m < m1; ++m) {
-        const float d = s_dv[m - 1];
         const float* brow = s_B + (m - 1) * h;
+        float b[C];
 #pragma unroll
         for (int cc = 0; cc < C; ++cc) {
           const int r = lane + 32 * cc;
-          if (r < h) part[cc] = fmaf(d, brow[r], part[cc]);
+          b[cc] = r < h ? brow[r] : 0.f;
+        }
+#pragma unroll
+        for (int g = 0; g < R; ++g) {
+          const float d = s_dv[g * 32 * C + m - 1];
+#pragma unroll
+          for (int cc = 0; cc < C; ++cc) part[g][cc] = fmaf(d, b[cc], part[g][cc]);
         }
       }
 #pragma unroll
-      for (int cc = 0; cc < C; ++cc) two_sum_acc(sacc[cc], eacc[cc], part[cc]);
-    }
-    float* out = VWh + (size_t)row * h;
+      for (int g = 0; g < R; ++g)
 #pragma unroll
-    for (int cc = 0; cc < C; ++cc) {
-      const int r = lane + 32 * cc;
-      if (r < h) {
-        const float v = __fmul_rn(c, __fadd_rn(sacc[cc], eacc[cc]));
-        out[r] = v;
-        s_row[r] = v;
-      }
+        for (int cc = 0; cc < C; ++cc) two_sum_acc(sacc[g][cc], eacc[g][cc], part[g][cc]);
     }
-    __syncwarp();
-    if (gamma) {
-      auto xpos = [&](int k) { return positive_part_smem(s_row, Q, (r0 + k) % Q); };
-      double g;
-      int sc;
-      long long tot;
-      warp_row_cdf(xpos, n_M, log2_nM, lane, cdf + (size_t)row * n_M, g, sc, tot);
-      if (lane == 0) {
-        gamma[row] = g;
-        const unsigned long long thr = g > 0.0 ? event_threshold(g, dt, flags) : 0ull;
-        gthr[row] = thr;
-        if (thr_cell) thr_cell[i] = thr;
+#pragma unroll
+    for (int g = 0; g < R; ++g) {
+      const int row = row0 + g;
+      if (row >= n_rows) break;
+      float* out = VWh + (size_t)row * h;
+#pragma unroll
+      for (int cc = 0; cc < C; ++cc) {
+        const int r = lane + 32 * cc;
+        if (r < h) {
+          const float v = __fmul_rn(c, __fadd_rn(sacc[g][cc], eacc[g][cc]));
+          out[r] = v;
+          s_row[r] = v;
+        }
       }
+      __syncwarp();
+      if (gamma) {
+        auto xres = [&](int rr) { return positive_part_smem(s_row, Q, rr); };
+        double gm;
+        int sc;
+        long long tot;
+        warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, cdf + (size_t)row * n_M, gm, sc, tot);
+        if (lane == 0) {
+          gamma[row] = gm;
+          const unsigned long long thr = gm > 0.0 ? event_threshold(gm, dt, flags) : 0ull;
+          gthr[row] = thr;
+          if (thr_cell) thr_cell[occ ? __ldg(occ + row) : row % n_x] = thr;
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
 bool small_window(const wmc_params& p) { return p.Q / 2 <= kRowMaxH; }
 
-static size_t rows_small_smem(int h) {
+static size_t rows_small_smem(int h, int R) {
   const int C = h <= 32 ? 1 : (h <= 64 ? 2 : 4);
-  return sizeof(float) * ((size_t)(h - 1) * h + (size_t)kRowWarps * 2 * 32 * C);
+  return sizeof(float) * ((size_t)(h - 1) * h + (size_t)kRowWarps * (R + 1) * 32 * C);
 }
 
 cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
@@ -281,21 +402,28 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
   const Layout L = layout(p);
   const int h = L.h;
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
-  const size_t sm = rows_small_smem(h);
-  int blocks = (max_rows + kRowWarps - 1) / kRowWarps;
+  const int R = (long long)max_rows >= 2ll * num_sms() * kRowWarps * 4 ? 4 : 1;
+  const size_t sm = rows_small_smem(h, R);
+  int blocks = (max_rows + kRowWarps * R - 1) / (kRowWarps * R);
   if (blocks > 2 * num_sms()) blocks = 2 * num_sms();
   const int lg = ceil_log2(p.n_M);
-#define WMC_LAUNCH_ROWS(CC)                                                                                         \
-  do {                                                                                                              \
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_kernel_rows_small<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)sm);                                                              \
-    k_kernel_rows_small<CC><<<blocks, kRowWarps * 32, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, p.n_M, lg, occ,       \
-                                                               n_occ_dev, n_occ_host, B, L.Np, c, VWh, cdf, gamma,  \
-                                                               gthr, thr_cell, flags, p.dt_s);                      \
+#define WMC_LAUNCH_ROWS(CC, RR)                                                                                   \
+  do {                                                                                                            \
+    if (sm > 48 * 1024)                                                                                           \
+      cudaFuncSetAttribute(k_kernel_rows_small<CC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);    \
+    k_kernel_rows_small<CC, RR><<<blocks, kRowWarps * 32, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, p.n_M, lg, occ, \
+                                                                   n_occ_dev, n_occ_host, B, L.Np, c, VWh, cdf,   \
+                                                                   gamma, gthr, thr_cell, flags, p.dt_s);         \
   } while (0)
-  if (h <= 32) WMC_LAUNCH_ROWS(1);
-  else if (h <= 64) WMC_LAUNCH_ROWS(2);
-  else WMC_LAUNCH_ROWS(4);
+  if (R == 4) {
+    if (h <= 32) WMC_LAUNCH_ROWS(1, 4);
+    else if (h <= 64) WMC_LAUNCH_ROWS(2, 4);
+    else WMC_LAUNCH_ROWS(4, 4);
+  } else {
+    if (h <= 32) WMC_LAUNCH_ROWS(1, 1);
+    else if (h <= 64) WMC_LAUNCH_ROWS(2, 1);
+    else WMC_LAUNCH_ROWS(4, 1);
+  }
 #undef WMC_LAUNCH_ROWS
   return cudaGetLastError();
 }
@@ -305,6 +433,21 @@ cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_
                        long long* cdf, double* gamma, int* scale, unsigned long long* gthr, const int* occ,
                        unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s) {
   if (max_rows <= 0) return cudaSuccess;
+  if (!cdf && !gthr && !n_rows_dev) {  // gamma (and scale) only
+    const int h = p.Q / 2, ca = p.n_M / p.Q, cb = p.n_M - ca * p.Q, r0 = ((-(p.n_M / 2)) % p.Q + p.Q) % p.Q;
+    int blocks = (max_rows + kCdfWarps - 1) / kCdfWarps;
+    if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+    const int lg = ceil_log2(p.n_M);
+    if (h <= 32)
+      k_gamma_folded<1><<<blocks, kCdfWarps * 32, 0, s>>>(p.Q, lg, ca, cb, r0, VWh, n_rows_host, gamma, scale);
+    else if (h <= 64)
+      k_gamma_folded<2><<<blocks, kCdfWarps * 32, 0, s>>>(p.Q, lg, ca, cb, r0, VWh, n_rows_host, gamma, scale);
+    else if (h <= 128)
+      k_gamma_folded<4><<<blocks, kCdfWarps * 32, 0, s>>>(p.Q, lg, ca, cb, r0, VWh, n_rows_host, gamma, scale);
+    else
+      k_gamma_folded<0><<<blocks, kCdfWarps * 32, 0, s>>>(p.Q, lg, ca, cb, r0, VWh, n_rows_host, gamma, scale);
+    return cudaGetLastError();
+  }
   k_cdf<<<(max_rows + kCdfWarps - 1) / kCdfWarps, kCdfWarps * 32, 0, s>>>(
       p.n_M, p.Q, ceil_log2(p.n_M), VWh, n_rows_dev, n_rows_host, cdf, gamma, scale, gthr, occ, thr_cell, flags,
       p.dt_s);

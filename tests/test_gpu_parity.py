@@ -134,6 +134,30 @@ def test_cdf_bit_exact_on_same_kernel_values(wmc, wl):
     assert npos > 0
 
 
+@pytest.mark.parametrize("wl", [wi.BARRIER_100, wi.BARRIER_2000, wi.BARRIER_2000.replace(n_M=48),
+                                wi.DOUBLE_BARRIER_16384,
+                                wi.DOUBLE_BARRIER_16384.replace(n_M=1536, dt_s=0.5 * wi.DOUBLE_BARRIER_16384.dt_s)])
+def test_gamma_only_bit_exact(wmc, wl):
+    """gamma and the scale without the CDF (read from the folded row with
+    residue multiplicities) equal the oracle's for momentum grids shorter than,
+    equal to and longer than the period, including rows that are all zero."""
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    rows = np.arange(0, wl.n_x, max(1, wl.n_x // 300))
+    po = oracle.params(wl)
+    full = oracle.kernel_rows(po, V, rows).astype(np.float32)
+    half = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, rows)[:, wl.Q // 2:].astype(np.float32)
+    half[3] = 0.0
+    full[3] = 0.0
+    _, gamma, scale = wmc.kernel_cdf(p, torch.from_numpy(np.ascontiguousarray(half)).cuda(), with_cdf=False)
+    gamma, scale = gamma.cpu().numpy(), scale.cpu().numpy()
+    for r in range(rows.size):
+        _, g_ref, s_ref = oracle.cdf_row(full[r].astype(np.float64), with_scale=True)
+        assert gamma[r] == g_ref, r
+        assert scale[r] == s_ref, r
+    assert gamma[3] == 0.0
+
+
 # --------------------------------------------------------------------------- steps, bit-exact
 def _compare_steps(wmc, wl, hist0, t_first, n_steps, V=None):
     p = wmc.Params.of(wl)
