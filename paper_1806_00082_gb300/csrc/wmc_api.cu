@@ -138,11 +138,10 @@ static cudaError_t kernel_and_cdf_occupied(const wmc_params& p, const View& v, c
 static wmc_status one_step(const wmc_params& p, const View& v, const float* V, const int32_t* in, int32_t* out,
                            wmc_precision prec, int device_step, uint32_t t, cudaStream_t s) {
   const Layout L = layout(p);
-  cudaError_t e = launch_plan(p, v, in, nullptr, device_step, s);
+  // the per-cell scan also zeroes the output histogram and plans the step
+  cudaError_t e = launch_plan(p, v, in, nullptr, device_step, s, out);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
   e = kernel_and_cdf_occupied(p, v, V, prec, s);
-  if (e != cudaSuccess) return WMC_ERR_CUDA;
-  e = cudaMemsetAsync(out, 0, sizeof(int32_t) * (size_t)p.n_x * (size_t)p.n_M, s);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
   e = launch_step(p, v, in, t, device_step, out, s);
   return cuda_status(e);

@@ -29,8 +29,9 @@ constexpr uint32_t kPurposePick = 3u;
 // ceil((T[i] + 3) / kChunk) items (the last may be empty).  A block takes one
 // item at a time, each of its threads kPerThread consecutive ids.
 constexpr int kStepThreads = 256;
+constexpr int kStepWorkers = kStepThreads - 32;  // warp 0 of a step block prepares the next work item
 constexpr int kPerThread = 32;
-constexpr int kChunk = kStepThreads * kPerThread;
+constexpr int kChunk = kStepWorkers * kPerThread;
 constexpr int kMaxStepBlocks = 8192;
 constexpr long long kMaxItemsBase = 1ll << 20;   // item descriptors: 2^32 / kChunk + n_x
 
@@ -117,7 +118,7 @@ __host__ __device__ __forceinline__ int items_of_cell(unsigned long long t) {
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t s);
 cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, int advance_step,
-                        cudaStream_t s);
+                        cudaStream_t s, int32_t* zero_out = nullptr);
 int step_grid(int n_M);
 cudaError_t launch_kernel_eval(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
                                int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s);

@@ -300,9 +300,23 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
   float* s_dv = s_row + 32 * C;                                   // row g: dV(m) at s_dv[g 32 C + m - 1]
   const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
   if ((int)(blockIdx.x * kRowWarps * R) >= n_rows) return;
-  for (int q = threadIdx.x; q < (h - 1) * h; q += blockDim.x) {
-    const int m1 = q / h, r = q - m1 * h;
-    s_B[q] = __ldg(B + (size_t)m1 * Np + r);
+  {
+    // stage the sine rows with eight loads in flight per thread
+    const int nB = (h - 1) * h;
+    for (int q0 = threadIdx.x; q0 < nB; q0 += 8 * kRowWarps * 32) {
+      float tmp[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * kRowWarps * 32;
+        const int m1 = q / h, r = q - m1 * h;
+        tmp[u] = q < nB ? __ldg(B + (size_t)m1 * Np + r) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * kRowWarps * 32;
+        if (q < nB) s_B[q] = tmp[u];
+      }
+    }
   }
   __syncthreads();
   const int r0 = ((-(n_M / 2)) % Q + Q) % Q;

@@ -51,82 +51,41 @@ cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t 
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- per-cell scan
-// One warp per cell: survivors T[i] = sum_k |n(i,k)|, reach bits (bit0 cell
-// occupied, bit1 a momentum that drifts right is present, bit2 one that drifts
-// left), and optionally the density rho[i] = sum_k n(i,k).
-__global__ void k_rows(const int32_t* __restrict__ hist, int n_x, int n_M, const float* __restrict__ D,
-                       unsigned long long* __restrict__ T, unsigned char* __restrict__ reach,
-                       long long* __restrict__ rho) {
-  const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (warp >= n_x) return;
-  const int32_t* row = hist + (size_t)warp * n_M;
-  unsigned long long a = 0;
-  long long sn = 0;
-  unsigned bits = 0;
-  if ((n_M & 3) == 0) {
-    const int4* row4 = reinterpret_cast<const int4*>(row);
-    const float4* D4 = reinterpret_cast<const float4*>(D);
-    for (int q = lane; q < n_M / 4; q += 32) {
-      const int4 n = row4[q];
-      const float4 d = D4[q];
-      const int nv[4] = {n.x, n.y, n.z, n.w};
-      const float dv[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (nv[e]) {
-          a += (unsigned long long)(nv[e] < 0 ? -(long long)nv[e] : (long long)nv[e]);
-          sn += nv[e];
-          bits |= 1u | (dv[e] > 0.f ? 2u : 0u) | (dv[e] < 0.f ? 4u : 0u);
-        }
-      }
-    }
-  } else {
-    for (int k = lane; k < n_M; k += 32) {
-      const int n = row[k];
-      if (n) {
-        a += (unsigned long long)(n < 0 ? -(long long)n : (long long)n);
-        sn += n;
-        bits |= 1u | (D[k] > 0.f ? 2u : 0u) | (D[k] < 0.f ? 4u : 0u);
-      }
-    }
-  }
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, off);
-    sn += __shfl_down_sync(0xffffffffu, sn, off);
-    bits |= __shfl_down_sync(0xffffffffu, bits, off);
-  }
-  if (lane == 0) {
-    T[warp] = a;
-    reach[warp] = (unsigned char)bits;
-    if (rho) rho[warp] = sn;
-  }
-}
-
+// ---------------------------------------------------------------- per-cell scan and plan
 __device__ __forceinline__ int needs_kernel(const unsigned char* reach, int i, int n_x) {
   return (reach[i] & 1) || (i > 0 && (reach[i - 1] & 2)) || (i + 1 < n_x && (reach[i + 1] & 4));
 }
 
-// One block: exclusive prefix sums of survivors (ids), work items and needed
-// cells, then the occupied list, row map and work-item descriptors; the
-// per-cell event thresholds are cleared (the kernel stage fills the occupied
-// cells).  Single block because n_x is at
-// most a few 10^4 in the workloads and this runs once per step.
-constexpr int kPlanThreads = 1024;
+// T and reach of every cell staged in shared memory by coalesced loads when
+// they fit, so the scan's per-thread runs read on-chip memory
+constexpr int kPlanStage = 4096;
 
-__global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned long long* __restrict__ T,
-                                                       const unsigned char* __restrict__ reach,
-                                                       unsigned long long* __restrict__ R, int* __restrict__ IP,
-                                                       int* __restrict__ occ, int* __restrict__ row_map,
-                                                       int2* __restrict__ items, long long max_items,
-                                                       unsigned long long* __restrict__ thr_cell, DevHeader* hdr,
-                                                       int advance_step) {
+// The plan, by one block (blockDim.x threads, a multiple of 32 up to 1024):
+// exclusive prefix sums of survivors (ids), work items and needed cells, then
+// the occupied list, row map and work-item descriptors; the per-cell event
+// thresholds are cleared (the kernel stage fills the occupied cells).
+__device__ __forceinline__ void plan_block(int n_x, const unsigned long long* T_g, const unsigned char* reach_g,
+                           unsigned long long* __restrict__ R, int* __restrict__ IP, int* __restrict__ occ,
+                           int* __restrict__ row_map, int2* __restrict__ items, long long max_items,
+                           unsigned long long* __restrict__ thr_cell, DevHeader* hdr, int advance_step) {
   __shared__ unsigned long long wT[32];
   __shared__ int wI[32], wN[32], wBig[32];
+  __shared__ unsigned long long s_T[kPlanStage];
+  __shared__ unsigned char s_reach[kPlanStage];
+  const int nt = blockDim.x, nw = nt >> 5;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int per = (n_x + kPlanThreads - 1) / kPlanThreads;
+  const unsigned long long* T = T_g;
+  const unsigned char* reach = reach_g;
+  if (n_x <= kPlanStage) {
+    for (int i = tid; i < n_x; i += nt) {
+      s_T[i] = __ldg(T_g + i);
+      s_reach[i] = __ldg(reach_g + i);
+    }
+    __syncthreads();
+    T = s_T;
+    reach = s_reach;
+  }
+  const int per = (n_x + nt - 1) / nt;
   const int lo = min(tid * per, n_x), hi = min(lo + per, n_x);
   unsigned long long aT = 0;
   int aI = 0, aN = 0, big = 0;
@@ -160,8 +119,8 @@ __global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned l
   }
   __syncthreads();
   if (wid == 0) {
-    unsigned long long sT = wT[lane];
-    int sI = wI[lane], sN = wN[lane], sB = wBig[lane];
+    unsigned long long sT = lane < nw ? wT[lane] : 0ull;
+    int sI = lane < nw ? wI[lane] : 0, sN = lane < nw ? wN[lane] : 0, sB = lane < nw ? wBig[lane] : 0;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const unsigned long long uT = __shfl_up_sync(0xffffffffu, sT, off);
@@ -204,7 +163,7 @@ __global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned l
     r += t;
     baseI += items_of_cell(t);
   }
-  if (tid == kPlanThreads - 1) {
+  if (tid == nt - 1) {
     const unsigned long long P = wT[31];
     const int too_big = !ok;
     R[n_x] = P;
@@ -217,12 +176,87 @@ __global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned l
   }
 }
 
+// One warp per cell: survivors T[i] = sum_k |n(i,k)|, reach bits (bit0 cell
+// occupied, bit1 a momentum that drifts right is present, bit2 one that drifts
+// left), optionally the density rho[i] = sum_k n(i,k), and optionally a zeroed
+// row of the next histogram.
+constexpr int kRowsWarps = 8;
+
+__global__ __launch_bounds__(kRowsWarps * 32) void k_rows(const int32_t* __restrict__ hist, int n_x, int n_M,
+                                                          const float* __restrict__ D,
+                                                          unsigned long long* __restrict__ T,
+                                                          unsigned char* __restrict__ reach,
+                                                          long long* __restrict__ rho, int32_t* __restrict__ zero_out) {
+  const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp < n_x) {
+    const int32_t* row = hist + (size_t)warp * n_M;
+    unsigned long long a = 0;
+    long long sn = 0;
+    unsigned bits = 0;
+    if ((n_M & 3) == 0) {
+      const int4* row4 = reinterpret_cast<const int4*>(row);
+      const float4* D4 = reinterpret_cast<const float4*>(D);
+      int4* z4 = zero_out ? reinterpret_cast<int4*>(zero_out + (size_t)warp * n_M) : nullptr;
+      for (int q = lane; q < n_M / 4; q += 32) {
+        const int4 n = row4[q];
+        const float4 d = D4[q];
+        if (z4) z4[q] = make_int4(0, 0, 0, 0);
+        const int nv[4] = {n.x, n.y, n.z, n.w};
+        const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (nv[e]) {
+            a += (unsigned long long)(nv[e] < 0 ? -(long long)nv[e] : (long long)nv[e]);
+            sn += nv[e];
+            bits |= 1u | (dv[e] > 0.f ? 2u : 0u) | (dv[e] < 0.f ? 4u : 0u);
+          }
+        }
+      }
+    } else {
+      for (int k = lane; k < n_M; k += 32) {
+        const int n = row[k];
+        if (zero_out) zero_out[(size_t)warp * n_M + k] = 0;
+        if (n) {
+          a += (unsigned long long)(n < 0 ? -(long long)n : (long long)n);
+          sn += n;
+          bits |= 1u | (D[k] > 0.f ? 2u : 0u) | (D[k] < 0.f ? 4u : 0u);
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, off);
+      sn += __shfl_down_sync(0xffffffffu, sn, off);
+      bits |= __shfl_down_sync(0xffffffffu, bits, off);
+    }
+    if (lane == 0) {
+      T[warp] = a;
+      reach[warp] = (unsigned char)bits;
+      if (rho) rho[warp] = sn;
+    }
+  }
+}
+
+// The plan as its own single-block launch (n_x is at most a few 10^4 in the
+// workloads and this runs once per step).
+constexpr int kPlanThreads = 1024;
+
+__global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned long long* __restrict__ T,
+                                                       const unsigned char* __restrict__ reach,
+                                                       unsigned long long* __restrict__ R, int* __restrict__ IP,
+                                                       int* __restrict__ occ, int* __restrict__ row_map,
+                                                       int2* __restrict__ items, long long max_items,
+                                                       unsigned long long* __restrict__ thr_cell, DevHeader* hdr,
+                                                       int advance_step) {
+  plan_block(n_x, T, reach, R, IP, occ, row_map, items, max_items, thr_cell, hdr, advance_step);
+}
+
 cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, int advance_step,
-                        cudaStream_t s) {
-  const int warps_per_block = 8;
-  const int blocks = (p.n_x + warps_per_block - 1) / warps_per_block;
-  k_rows<<<blocks, warps_per_block * 32, 0, s>>>(hist, p.n_x, p.n_M, v.D, v.T, v.reach,
-                                                 reinterpret_cast<long long*>(rho));
+                        cudaStream_t s, int32_t* zero_out) {
+  const int blocks = (p.n_x + kRowsWarps - 1) / kRowsWarps;
+  k_rows<<<blocks, kRowsWarps * 32, 0, s>>>(hist, p.n_x, p.n_M, v.D, v.T, v.reach,
+                                            reinterpret_cast<long long*>(rho), zero_out);
   k_plan<<<1, kPlanThreads, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.items,
                                     layout(p).max_items, v.thr_cell, v.hdr, advance_step);
   return cudaGetLastError();

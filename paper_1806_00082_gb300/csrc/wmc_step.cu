@@ -6,10 +6,13 @@
 // The survivors are never stored: after annihilation every particle of bucket
 // (i, M) carries the same cell, momentum and sign, and its offset is a Philox
 // draw of its id, so the histogram and the id prefix describe the ensemble
-// exactly.  A block takes a work item (up to kChunk ids of one cell, aligned
-// so that each Philox call serves four consecutive ids of one thread),
-// privatises the three histogram rows its particles can land in (i-1, i, i+1)
-// in shared memory, and flushes them with one global atomic per non-zero
+// exactly.  A block takes work items (up to kChunk ids of one cell, aligned
+// so that each Philox call serves four consecutive ids of one thread) in a
+// fixed round-robin order; while its seven worker warps step the particles of
+// one item, warp 0 loads the next item's descriptor and row prefix into the
+// other of two shared buffers, so that latency is off the critical path.  The
+// block privatises the three histogram rows its particles can land in (i-1, i,
+// i+1) in shared memory and flushes them with one global atomic per non-zero
 // bucket.  A particle moves iff its offset word passes the integer threshold
 // of its momentum column, so a quad of ids inside one bucket costs one Philox
 // call and a handful of compares.
@@ -107,148 +110,176 @@ __device__ __forceinline__ void create_pair(const StepArgs& a, uint32_t id, uint
   }
 }
 
+// Descriptor of a work item, prepared by warp 0 one item ahead.
+struct ItemMeta {
+  unsigned long long thr_m, thr_0, thr_p;  // event thresholds of cells i-1, i, i+1
+  uint32_t base;                           // first id of cell i
+  int item, i, ch;
+};
+
 __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
   extern __shared__ int smem[];
   const int n_M = a.n_M;
-  int* s_pre = smem;                 // n_M + 1
-  int* s_n = s_pre + (n_M + 1);      // n_M
-  int* s_acc = s_n + n_M;            // 3 n_M: rows i-1, i, i+1
+  int* s_pre2 = smem;                    // 2 x (n_M + 1): prefix buffers
+  int* s_n2 = s_pre2 + 2 * (n_M + 1);    // 2 x n_M: signed count buffers
+  int* s_acc = s_n2 + 2 * n_M;           // 3 n_M: rows i-1, i, i+1
   uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_acc + 3 * n_M);  // n_M
   uint32_t* s_hi = s_lo + n_M;                                     // n_M
-  __shared__ int s_item;
+  __shared__ ItemMeta s_meta[2];
   __shared__ unsigned long long s_red[5][kStepThreads / 32];
-
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t t = a.t_from_device ? a.hdr->step : a.t;
   const int n_items = a.hdr->n_items;
   for (int k = tid; k < n_M; k += kStepThreads) {
     s_lo[k] = a.xlo[k];
     s_hi[k] = a.xhi[k];
   }
+  for (int q = tid; q < 3 * n_M; q += kStepThreads) s_acc[q] = 0;
+
+  // by warp 0: descriptor and row prefix of `item` into buffer `buf`
+  auto prepare = [&](int item, int buf) {
+    ItemMeta m;
+    m.item = item;
+    m.i = m.ch = 0;
+    m.base = 0u;
+    m.thr_m = m.thr_0 = m.thr_p = 0ull;
+    if (item < n_items) {
+      const int2 it = __ldg(a.items + item);
+      m.i = it.x;
+      m.ch = it.y;
+      m.base = (uint32_t)__ldg(a.R + m.i);
+      m.thr_m = m.i > 0 ? __ldg(a.thr_cell + m.i - 1) : 0ull;
+      m.thr_0 = __ldg(a.thr_cell + m.i);
+      m.thr_p = m.i + 1 < a.n_x ? __ldg(a.thr_cell + m.i + 1) : 0ull;
+      warp_row_prefix(a.hist_in, m.i, n_M, s_n2 + buf * n_M, s_pre2 + buf * (n_M + 1), lane);
+    }
+    if (lane == 0) s_meta[buf] = m;
+  };
+  if (wid == 0) prepare(blockIdx.x, 0);
 
   unsigned long long pairs = 0, absorbed = 0, dropped = 0;
   long long abs_signed = 0, drop_signed = 0;
 
-  for (;;) {
-    // items are handed out in order to whichever block is free
-    if (tid == 0) s_item = (int)atomicAdd(&a.hdr->item_ticket, 1u);
-    __syncthreads();  // also: the previous item is flushed
-    const int item = s_item;
-    if (item >= n_items) break;
-    const int2 it = __ldg(a.items + item);
-    const int i = it.x, ch = it.y;
-    const uint32_t base = (uint32_t)__ldg(a.R + i);
-    const unsigned long long thr_m = i > 0 ? __ldg(a.thr_cell + i - 1) : 0ull;
-    const unsigned long long thr_0 = __ldg(a.thr_cell + i);
-    const unsigned long long thr_p = i + 1 < a.n_x ? __ldg(a.thr_cell + i + 1) : 0ull;
-    for (int q = tid; q < 3 * n_M; q += kStepThreads) s_acc[q] = 0;
-    if ((tid >> 5) == 0) warp_row_prefix(a.hist_in, i, n_M, s_n, s_pre, lane);
-    __syncthreads();
+  for (int round = 0;; ++round) {
+    __syncthreads();  // this item's buffer is ready; the previous item is flushed
+    const int buf = round & 1;
+    const ItemMeta m = s_meta[buf];
+    if (m.item >= n_items) break;
+    if (wid == 0) {
+      prepare(m.item + (int)gridDim.x, buf ^ 1);
+    } else {
+      const int* s_pre = s_pre2 + buf * (n_M + 1);
+      const int* s_n = s_n2 + buf * n_M;
+      const int i = m.i, ch = m.ch;
+      const uint32_t base = m.base;
+      const unsigned long long thr_m = m.thr_m, thr_0 = m.thr_0, thr_p = m.thr_p;
+      const int w = tid - 32;  // worker index
+      const uint32_t Ti = (uint32_t)s_pre[n_M];
+      const unsigned long long A = base & ~3u;
+      const unsigned long long lo64 = A + (unsigned long long)ch * kChunk + (unsigned long long)w * kPerThread;
+      const unsigned long long row_end = (unsigned long long)base + Ti;
+      const unsigned long long g0_64 = lo64 > base ? lo64 : base;
+      const unsigned long long g1_64 = lo64 + kPerThread < row_end ? lo64 + kPerThread : row_end;
+      // ids stay below 2^32 (the plan guarantees it); compare in 64 bits first
+      const uint32_t g0 = g0_64 < g1_64 ? (uint32_t)g0_64 : 0u;
+      const uint32_t g1 = g0_64 < g1_64 ? (uint32_t)g1_64 : 0u;
+      const bool need_gen = (thr_m | thr_0 | thr_p) != 0ull;
 
-    const uint32_t Ti = (uint32_t)s_pre[n_M];
-    const unsigned long long A = base & ~3u;
-    const unsigned long long lo64 = A + (unsigned long long)ch * kChunk + (unsigned long long)tid * kPerThread;
-    const unsigned long long row_end = (unsigned long long)base + Ti;
-    const unsigned long long g0_64 = lo64 > base ? lo64 : base;
-    const unsigned long long g1_64 = lo64 + kPerThread < row_end ? lo64 + kPerThread : row_end;
-    // ids stay below 2^32 (the plan guarantees it); compare in 64 bits first
-    const uint32_t g0 = g0_64 < g1_64 ? (uint32_t)g0_64 : 0u;
-    const uint32_t g1 = g0_64 < g1_64 ? (uint32_t)g1_64 : 0u;
-    const bool need_gen = (thr_m | thr_0 | thr_p) != 0ull;
-
-    int k = 0, n_tot = 0, n_mov = 0, sgn = 1, dir = 0;
-    if (g0 < g1) {
-      k = bucket_of(s_pre, n_M, (int)(g0 - base));
-      uint32_t end_g = base + (uint32_t)s_pre[k + 1];
-      sgn = s_n[k] > 0 ? 1 : -1;
-      uint32_t lo = s_lo[k], hi = s_hi[k];
-      dir = drift_dir(lo, hi);
-      unsigned long long thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
-      for (uint32_t q = g0 >> 2; q <= (g1 - 1u) >> 2; ++q) {
-        const uint32_t qa = q << 2;
-        const uint4 wr = philox4x32_10(make_uint4(q, t - 1u, kPurposeRepos, a.sim), a.k0, a.k1);
-        uint4 wg = make_uint4(0u, 0u, 0u, 0u);
-        if (need_gen) wg = philox4x32_10(make_uint4(q, t, kPurposeGen, a.sim), a.k0, a.k1);
-        if (qa >= g0 && qa + 3u < g1 && qa + 3u < end_g) {
-          // four consecutive ids of bucket k
-          const int m0 = (wr.x > hi) | (wr.x < lo), m1 = (wr.y > hi) | (wr.y < lo);
-          const int m2 = (wr.z > hi) | (wr.z < lo), m3 = (wr.w > hi) | (wr.w < lo);
-          n_mov += m0 + m1 + m2 + m3;
-          n_tot += 4;
-          if (need_gen) {
-            const int mv[4] = {m0, m1, m2, m3};
-            const uint32_t u[4] = {wg.x, wg.y, wg.z, wg.w};
+      int k = 0, n_tot = 0, n_mov = 0, sgn = 1, dir = 0;
+      if (g0 < g1) {
+        k = bucket_of(s_pre, n_M, (int)(g0 - base));
+        uint32_t end_g = base + (uint32_t)s_pre[k + 1];
+        sgn = s_n[k] > 0 ? 1 : -1;
+        uint32_t lo = s_lo[k], hi = s_hi[k];
+        dir = drift_dir(lo, hi);
+        unsigned long long thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
+        for (uint32_t q = g0 >> 2; q <= (g1 - 1u) >> 2; ++q) {
+          const uint32_t qa = q << 2;
+          const uint4 wr = philox4x32_10(make_uint4(q, t - 1u, kPurposeRepos, a.sim), a.k0, a.k1);
+          uint4 wg = make_uint4(0u, 0u, 0u, 0u);
+          if (need_gen) wg = philox4x32_10(make_uint4(q, t, kPurposeGen, a.sim), a.k0, a.k1);
+          if (qa >= g0 && qa + 3u < g1 && qa + 3u < end_g) {
+            // four consecutive ids of bucket k
+            const int m0 = (wr.x > hi) | (wr.x < lo), m1 = (wr.y > hi) | (wr.y < lo);
+            const int m2 = (wr.z > hi) | (wr.z < lo), m3 = (wr.w > hi) | (wr.w < lo);
+            n_mov += m0 + m1 + m2 + m3;
+            n_tot += 4;
+            if (need_gen) {
+              const int mv[4] = {m0, m1, m2, m3};
+              const uint32_t u[4] = {wg.x, wg.y, wg.z, wg.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if ((unsigned long long)u[j] < (mv[j] ? thr_move : thr_0))
-                create_pair(a, qa + (uint32_t)j, t, i, mv[j] ? dir + 1 : 1, k, sgn, s_acc, pairs, dropped,
-                            drop_signed);
-            }
-          }
-          continue;
-        }
-        const uint32_t w4[4] = {wr.x, wr.y, wr.z, wr.w};
-        const uint32_t u4[4] = {wg.x, wg.y, wg.z, wg.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t id = qa + (uint32_t)j;
-          if (id < g0 || id >= g1) continue;
-          if (id >= end_g) {  // next non-empty bucket
-            const int stay = n_tot - n_mov;
-            if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
-            if (n_mov) {
-              if ((unsigned)(i + dir) < (unsigned)a.n_x) {
-                atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * n_mov);
-              } else {
-                absorbed += n_mov;
-                abs_signed += sgn * n_mov;
+              for (int j = 0; j < 4; ++j) {
+                if ((unsigned long long)u[j] < (mv[j] ? thr_move : thr_0))
+                  create_pair(a, qa + (uint32_t)j, t, i, mv[j] ? dir + 1 : 1, k, sgn, s_acc, pairs, dropped,
+                              drop_signed);
               }
             }
-            n_tot = n_mov = 0;
-            do { ++k; } while (base + (uint32_t)s_pre[k + 1] <= id);
-            end_g = base + (uint32_t)s_pre[k + 1];
-            sgn = s_n[k] > 0 ? 1 : -1;
-            lo = s_lo[k];
-            hi = s_hi[k];
-            dir = drift_dir(lo, hi);
-            thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
+            continue;
           }
-          const int mv = (w4[j] > hi) | (w4[j] < lo);
-          n_mov += mv;
-          ++n_tot;
-          if (need_gen && (unsigned long long)u4[j] < (mv ? thr_move : thr_0))
-            create_pair(a, id, t, i, mv ? dir + 1 : 1, k, sgn, s_acc, pairs, dropped, drop_signed);
+          const uint32_t w4[4] = {wr.x, wr.y, wr.z, wr.w};
+          const uint32_t u4[4] = {wg.x, wg.y, wg.z, wg.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t id = qa + (uint32_t)j;
+            if (id < g0 || id >= g1) continue;
+            if (id >= end_g) {  // next non-empty bucket
+              const int stay = n_tot - n_mov;
+              if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
+              if (n_mov) {
+                if ((unsigned)(i + dir) < (unsigned)a.n_x) {
+                  atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * n_mov);
+                } else {
+                  absorbed += n_mov;
+                  abs_signed += sgn * n_mov;
+                }
+              }
+              n_tot = n_mov = 0;
+              do { ++k; } while (base + (uint32_t)s_pre[k + 1] <= id);
+              end_g = base + (uint32_t)s_pre[k + 1];
+              sgn = s_n[k] > 0 ? 1 : -1;
+              lo = s_lo[k];
+              hi = s_hi[k];
+              dir = drift_dir(lo, hi);
+              thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
+            }
+            const int mv = (w4[j] > hi) | (w4[j] < lo);
+            n_mov += mv;
+            ++n_tot;
+            if (need_gen && (unsigned long long)u4[j] < (mv ? thr_move : thr_0))
+              create_pair(a, id, t, i, mv ? dir + 1 : 1, k, sgn, s_acc, pairs, dropped, drop_signed);
+          }
         }
       }
-    }
-    // last bucket of each thread: lanes holding the same bucket combine first
-    const int key = n_tot ? k : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int stay = __reduce_add_sync(peers, n_tot - n_mov);
-    const int mov = __reduce_add_sync(peers, n_mov);
-    if (key >= 0 && lane == __ffs(peers) - 1) {
-      if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
-      if (mov) {
-        if ((unsigned)(i + dir) < (unsigned)a.n_x) {
-          atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * mov);
-        } else {
-          absorbed += mov;
-          abs_signed += sgn * mov;
+      // last bucket of each thread: lanes holding the same bucket combine first
+      const int key = n_tot ? k : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int stay = __reduce_add_sync(peers, n_tot - n_mov);
+      const int mov = __reduce_add_sync(peers, n_mov);
+      if (key >= 0 && lane == __ffs(peers) - 1) {
+        if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
+        if (mov) {
+          if ((unsigned)(i + dir) < (unsigned)a.n_x) {
+            atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * mov);
+          } else {
+            absorbed += mov;
+            abs_signed += sgn * mov;
+          }
         }
       }
     }
     __syncthreads();
+    // flush the private rows (and clear them for the next item)
     for (int q = tid; q < 3 * n_M; q += kStepThreads) {
       const int v = s_acc[q];
       if (v) {
+        s_acc[q] = 0;
         const int d = q / n_M, kc = q - d * n_M;
-        atomicAdd(a.hist_out + (size_t)(i - 1 + d) * n_M + kc, v);
+        atomicAdd(a.hist_out + (size_t)(m.i - 1 + d) * n_M + kc, v);
       }
     }
   }
 
   // block totals of the counters, one atomic each
-  const int wid = tid >> 5;
   unsigned long long vals[5] = {pairs, absorbed, (unsigned long long)abs_signed, dropped,
                                 (unsigned long long)drop_signed};
 #pragma unroll
@@ -270,18 +301,11 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
     }
   }
   if (blockIdx.x == 0 && tid == 0 && n_items > 0) atomicAdd(&a.hdr->particle_steps, a.hdr->population);
-  if (tid == 0) {
-    // the last block to finish re-arms the item tickets for the next launch
-    __threadfence();
-    if (atomicAdd(&a.hdr->blocks_done, 1u) == gridDim.x - 1) {
-      a.hdr->item_ticket = 0u;
-      a.hdr->blocks_done = 0u;
-      __threadfence();
-    }
-  }
 }
 
-static size_t step_smem(int n_M) { return sizeof(int) * (size_t)(n_M + 1 + n_M + 3 * n_M) + 2 * sizeof(uint32_t) * n_M; }
+static size_t step_smem(int n_M) {
+  return sizeof(int) * (size_t)(2 * (n_M + 1) + 2 * n_M + 3 * n_M) + 2 * sizeof(uint32_t) * n_M;
+}
 
 int step_grid(int n_M) {
   static int cached_nM[8] = {0};
@@ -366,8 +390,8 @@ __global__ __launch_bounds__(kStepThreads) void k_materialize(const int32_t* __r
     __syncthreads();
     const int Ti = s_pre[n_M];
     const uint32_t base = (uint32_t)__ldg(R + i);
-    const int lo = chunk * kChunk + tid * kPerThread;
-    const int hi = min(lo + kPerThread, Ti);
+    const int lo = chunk * kChunk + tid * kPerThread;  // ids [chunk kChunk, (chunk + 1) kChunk) of the row
+    const int hi = tid < kStepWorkers ? min(lo + kPerThread, Ti) : lo;
     if (lo < hi) {
       int k = bucket_of(s_pre, n_M, lo);
       for (int lid = lo; lid < hi; ++lid) {

@@ -217,12 +217,28 @@ def test_steps_empty_and_single(wmc):
 
 
 def test_steps_bit_exact_large_buckets(wmc):
-    """Cells with more particles than one work item (4096): items split a cell."""
+    """Cells with more particles than one work item: items split a cell."""
     wl = wi.BARRIER_100
     h = np.zeros((wl.n_x, wl.n_M), np.int32)
     h[44, 30:36] = 3000
     h[45, 33] = -20000
     h[46, 60] = 9000
+    _compare_steps(wmc, wl, h, 2, 3)
+
+
+@pytest.mark.parametrize("sizes", [(7167, 7168, 7169, 7171), (8191, 8192, 8193, 3 * 7168 + 3),
+                                   (1, 2, 3, 4 * 7168 - 1)])
+def test_steps_bit_exact_work_item_boundaries(wmc, sizes):
+    """Cell populations around multiples of the work-item size, in cells whose
+    first id is not quad-aligned (a leading odd cell), with buckets split
+    across momenta and signs."""
+    wl = wi.BARRIER_100
+    h = np.zeros((wl.n_x, wl.n_M), np.int32)
+    h[40, 5] = 3  # shifts the first id of every later cell off a multiple of four
+    for j, n in enumerate(sizes):
+        c = 44 + 2 * j
+        h[c, 20] = n // 2
+        h[c, 41] = -(n - n // 2)
     _compare_steps(wmc, wl, h, 2, 3)
 
 
