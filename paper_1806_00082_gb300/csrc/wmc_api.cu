@@ -123,26 +123,64 @@ static cudaError_t kernel_and_cdf_occupied(const wmc_params& p, const View& v, c
                                           &v.hdr->flags, s);
     if (e != cudaSuccess) return e;
     return launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
-                      &v.hdr->flags, s);
+                      &v.hdr->flags, s, v.hdr);
   }
-  if (small_window(p))
-    return launch_kernel_rows_small(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, v.cdf, v.gamma, v.gthr,
-                                    v.thr_cell, &v.hdr->flags, s);
+  if (small_window(p))  // every cell a row, evaluated where the reach bits need it
+    return launch_kernel_rows_small(p, V, nullptr, nullptr, p.n_x, p.n_x, v.B, v.VWh, v.cdf, v.gamma, v.gthr,
+                                    v.thr_cell, &v.hdr->flags, s, v.reach, v.hdr);
   cudaError_t e = launch_kernel_eval(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, s);
   if (e != cudaSuccess) return e;
   return launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
-                    &v.hdr->flags, s);
+                    &v.hdr->flags, s, v.hdr);
+}
+
+// A second stream per device and a fork/join event pair, for running the
+// single-block plan beside the kernel stage.
+struct AuxStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static bool aux_stream(AuxStream& out) {
+  static std::mutex mu;
+  static AuxStream per_dev[16];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  AuxStream& a = per_dev[dev];
+  if (!a.s) {
+    if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess)
+      return false;
+  }
+  out = a;
+  return true;
 }
 
 // drift + kernel + step for one step, state in -> out, step number on the device
 static wmc_status one_step(const wmc_params& p, const View& v, const float* V, const int32_t* in, int32_t* out,
                            wmc_precision prec, int device_step, uint32_t t, cudaStream_t s) {
-  const Layout L = layout(p);
-  // the per-cell scan also zeroes the output histogram and plans the step
-  cudaError_t e = launch_plan(p, v, in, nullptr, device_step, s, out);
+  // the per-cell scan also zeroes the output histogram
+  cudaError_t e = launch_rows(p, v, in, nullptr, s, out);
   if (e != cudaSuccess) return WMC_ERR_CUDA;
-  e = kernel_and_cdf_occupied(p, v, V, prec, s);
-  if (e != cudaSuccess) return WMC_ERR_CUDA;
+  AuxStream aux;
+  if (prec == WMC_FP32 && small_window(p) && aux_stream(aux)) {
+    // the kernel stage needs only the reach bits, so the plan (ids, work items)
+    // runs beside it on the second stream; the step waits for both
+    if (cudaEventRecord(aux.fork, s) != cudaSuccess || cudaStreamWaitEvent(aux.s, aux.fork, 0) != cudaSuccess)
+      return WMC_ERR_CUDA;
+    e = launch_plan_scan(p, v, device_step, 0, aux.s);
+    if (e != cudaSuccess) return WMC_ERR_CUDA;
+    if (cudaEventRecord(aux.join, aux.s) != cudaSuccess) return WMC_ERR_CUDA;
+    e = kernel_and_cdf_occupied(p, v, V, prec, s);
+    if (cudaStreamWaitEvent(s, aux.join, 0) != cudaSuccess || e != cudaSuccess) return WMC_ERR_CUDA;
+  } else {
+    e = launch_plan_scan(p, v, device_step, 1, s);
+    if (e != cudaSuccess) return WMC_ERR_CUDA;
+    e = kernel_and_cdf_occupied(p, v, V, prec, s);
+    if (e != cudaSuccess) return WMC_ERR_CUDA;
+  }
   e = launch_step(p, v, in, t, device_step, out, s);
   return cuda_status(e);
 }
@@ -273,7 +311,7 @@ wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, vo
   cudaError_t e = launch_gather_table(*p, table, v.occ, &v.hdr->n_occ, p->n_x, v.VWh, s);
   if (e == cudaSuccess)
     e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
-                   &v.hdr->flags, s);
+                   &v.hdr->flags, s, v.hdr);
   return cuda_status(e);
 }
 

@@ -163,6 +163,12 @@ __device__ __forceinline__ void warp_row_prefix(const int32_t* __restrict__ hist
   if (lane == 31) s_pre[n_M] = incl;
 }
 
+// Cell i needs its kernel row this step: occupied, or a neighbour drifts into
+// it (reach bits: 1 occupied, 2 has a rightward momentum, 4 a leftward one).
+__device__ __forceinline__ int cell_needs_kernel(const unsigned char* reach, int i, int n_x) {
+  return (reach[i] & 1) || (i > 0 && (reach[i - 1] & 2)) || (i + 1 < n_x && (reach[i + 1] & 4));
+}
+
 // Largest k with s_pre[k] <= lid (so s_pre[k] <= lid < s_pre[k+1]).
 __device__ __forceinline__ int bucket_of(const int* s_pre, int n_M, int lid) {
   int lo = 0, hi = n_M;

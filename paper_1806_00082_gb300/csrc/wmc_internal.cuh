@@ -53,7 +53,8 @@ struct DevHeader {
   unsigned int magic;
   unsigned int item_ticket;  // next work item of the running step launch
   unsigned int blocks_done;  // step blocks finished (the last one resets both)
-  unsigned int pad[3];
+  unsigned int rows_by_cell; // 1: the kernel stage wrote its rows at the cell index, 0: at the occupied-list index
+  unsigned int pad[2];
 };
 
 // Byte offsets of the workspace regions (all 256-aligned).
@@ -119,6 +120,11 @@ __host__ __device__ __forceinline__ int items_of_cell(unsigned long long t) {
 cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t s);
 cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, int advance_step,
                         cudaStream_t s, int32_t* zero_out = nullptr);
+// the two halves of launch_plan: the per-cell scan, and the single-block plan
+// (clear_thr: also zero the event thresholds of every cell)
+cudaError_t launch_rows(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, cudaStream_t s,
+                        int32_t* zero_out);
+cudaError_t launch_plan_scan(const wmc_params& p, const View& v, int advance_step, int clear_thr, cudaStream_t s);
 int step_grid(int n_M);
 cudaError_t launch_kernel_eval(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
                                int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s);
@@ -128,7 +134,8 @@ bool small_window(const wmc_params& p);
 cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
                                      int n_occ_host, int max_rows, const float* B, float* VWh, long long* cdf,
                                      double* gamma, unsigned long long* gthr, unsigned long long* thr_cell,
-                                     unsigned int* flags, cudaStream_t s);
+                                     unsigned int* flags, cudaStream_t s, const unsigned char* reach = nullptr,
+                                     DevHeader* hdr = nullptr);
 cudaError_t launch_gather_table(const wmc_params& p, const float* table, const int* occ, const int* n_occ_dev,
                                 int max_rows, float* VWh, cudaStream_t s);
 // Tensor-core contraction (BF16, FP16, FP16 hi/lo split).
@@ -140,7 +147,8 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
 // CDF of rows, row-major cdf[row][n_M]; cdf/scale/gthr/thr_cell/flags may be null.
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host,
                        int max_rows, long long* cdf, double* gamma, int* scale, unsigned long long* gthr,
-                       const int* occ, unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s);
+                       const int* occ, unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s,
+                       DevHeader* hdr = nullptr);
 cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_in, uint32_t t, int t_from_device,
                         int32_t* hist_out, cudaStream_t s);
 cudaError_t launch_materialize(const wmc_params& p, const View& v, const int32_t* hist, uint32_t t, int32_t* cell,

@@ -147,8 +147,10 @@ __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2
                                                        int* __restrict__ scale, unsigned long long* __restrict__ gthr,
                                                        const int* __restrict__ occ,
                                                        unsigned long long* __restrict__ thr_cell,
-                                                       unsigned int* __restrict__ flags, double dt) {
+                                                       unsigned int* __restrict__ flags, double dt,
+                                                       DevHeader* __restrict__ hdr) {
   const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_host;
+  if (hdr && blockIdx.x == 0 && threadIdx.x == 0) hdr->rows_by_cell = 0u;  // rows follow the occupied list
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * kCdfWarps + (threadIdx.x >> 5);
   if (row >= n_rows) return;
@@ -291,9 +293,13 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
     const int* __restrict__ n_occ_dev, int n_occ_host, const float* __restrict__ B, int Np, float c,
     float* __restrict__ VWh, long long* __restrict__ cdf, double* __restrict__ gamma,
     unsigned long long* __restrict__ gthr, unsigned long long* __restrict__ thr_cell, unsigned int* __restrict__ flags,
-    double dt) {
+    double dt, const unsigned char* __restrict__ reach, DevHeader* __restrict__ hdr) {
+  // reach != nullptr (one potential, occ == nullptr): row r is cell r, evaluated
+  // only where the cell needs its kernel this step; the others get gamma = 0
+  // and a zero event threshold
   extern __shared__ float s_mem[];
   const int h = Q / 2;
+  if (hdr && blockIdx.x == 0 && threadIdx.x == 0) hdr->rows_by_cell = reach ? 1u : 0u;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* s_B = s_mem;                                             // (h - 1) x h, row m - 1
   float* s_row = s_mem + (h - 1) * h + wid * (R + 1) * 32 * C;    // kernel row (h floats)
@@ -324,7 +330,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
 #pragma unroll
     for (int g = 0; g < R; ++g) {
       const int row = row0 + g;
-      const bool ok = row < n_rows;
+      const bool ok = row < n_rows && (!reach || cell_needs_kernel(reach, row, n_x));
       const int i = ok ? (occ ? __ldg(occ + row) : row % n_x) : 0;
       const float* Vr = (occ || !ok) ? V : V + (size_t)(row / n_x) * n_x;
 #pragma unroll
@@ -372,6 +378,14 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
     for (int g = 0; g < R; ++g) {
       const int row = row0 + g;
       if (row >= n_rows) break;
+      if (reach && !cell_needs_kernel(reach, row, n_x)) {
+        if (gamma && lane == 0) {
+          gamma[row] = 0.0;
+          gthr[row] = 0ull;
+          if (thr_cell) thr_cell[row] = 0ull;
+        }
+        continue;
+      }
       float* out = VWh + (size_t)row * h;
 #pragma unroll
       for (int cc = 0; cc < C; ++cc) {
@@ -411,7 +425,8 @@ static size_t rows_small_smem(int h, int R) {
 cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
                                      int n_occ_host, int max_rows, const float* B, float* VWh, long long* cdf,
                                      double* gamma, unsigned long long* gthr, unsigned long long* thr_cell,
-                                     unsigned int* flags, cudaStream_t s) {
+                                     unsigned int* flags, cudaStream_t s, const unsigned char* reach,
+                                     DevHeader* hdr) {
   if (max_rows <= 0) return cudaSuccess;
   const Layout L = layout(p);
   const int h = L.h;
@@ -427,7 +442,8 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
       cudaFuncSetAttribute(k_kernel_rows_small<CC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);    \
     k_kernel_rows_small<CC, RR><<<blocks, kRowWarps * 32, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, p.n_M, lg, occ, \
                                                                    n_occ_dev, n_occ_host, B, L.Np, c, VWh, cdf,   \
-                                                                   gamma, gthr, thr_cell, flags, p.dt_s);         \
+                                                                   gamma, gthr, thr_cell, flags, p.dt_s, reach,   \
+                                                                   hdr);                                          \
   } while (0)
   if (R == 4) {
     if (h <= 32) WMC_LAUNCH_ROWS(1, 4);
@@ -445,7 +461,7 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
 
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host, int max_rows,
                        long long* cdf, double* gamma, int* scale, unsigned long long* gthr, const int* occ,
-                       unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s) {
+                       unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s, DevHeader* hdr) {
   if (max_rows <= 0) return cudaSuccess;
   if (!cdf && !gthr && !n_rows_dev) {  // gamma (and scale) only
     const int h = p.Q / 2, ca = p.n_M / p.Q, cb = p.n_M - ca * p.Q, r0 = ((-(p.n_M / 2)) % p.Q + p.Q) % p.Q;
@@ -464,7 +480,7 @@ cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_
   }
   k_cdf<<<(max_rows + kCdfWarps - 1) / kCdfWarps, kCdfWarps * 32, 0, s>>>(
       p.n_M, p.Q, ceil_log2(p.n_M), VWh, n_rows_dev, n_rows_host, cdf, gamma, scale, gthr, occ, thr_cell, flags,
-      p.dt_s);
+      p.dt_s, hdr);
   return cudaGetLastError();
 }
 

@@ -52,9 +52,6 @@ cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t 
 }
 
 // ---------------------------------------------------------------- per-cell scan and plan
-__device__ __forceinline__ int needs_kernel(const unsigned char* reach, int i, int n_x) {
-  return (reach[i] & 1) || (i > 0 && (reach[i - 1] & 2)) || (i + 1 < n_x && (reach[i + 1] & 4));
-}
 
 // T and reach of every cell staged in shared memory by coalesced loads when
 // they fit, so the scan's per-thread runs read on-chip memory
@@ -62,12 +59,14 @@ constexpr int kPlanStage = 4096;
 
 // The plan, by one block (blockDim.x threads, a multiple of 32 up to 1024):
 // exclusive prefix sums of survivors (ids), work items and needed cells, then
-// the occupied list, row map and work-item descriptors; the per-cell event
-// thresholds are cleared (the kernel stage fills the occupied cells).
+// the occupied list, row map and work-item descriptors; with clear_thr the
+// per-cell event thresholds are cleared (a kernel stage over the occupied list
+// then fills the occupied cells; one over every cell writes them all itself).
 __device__ __forceinline__ void plan_block(int n_x, const unsigned long long* T_g, const unsigned char* reach_g,
                            unsigned long long* __restrict__ R, int* __restrict__ IP, int* __restrict__ occ,
                            int* __restrict__ row_map, int2* __restrict__ items, long long max_items,
-                           unsigned long long* __restrict__ thr_cell, DevHeader* hdr, int advance_step) {
+                           unsigned long long* __restrict__ thr_cell, DevHeader* hdr, int advance_step,
+                           int clear_thr) {
   __shared__ unsigned long long wT[32];
   __shared__ int wI[32], wN[32], wBig[32];
   __shared__ unsigned long long s_T[kPlanStage];
@@ -93,7 +92,7 @@ __device__ __forceinline__ void plan_block(int n_x, const unsigned long long* T_
     const unsigned long long t = T[i];
     aT += t;
     aI += items_of_cell(t);
-    aN += needs_kernel(reach, i, n_x);
+    aN += cell_needs_kernel(reach, i, n_x);
     big |= t > 0x7fffffffull;
   }
   // block-wide exclusive scan of (aT, aI, aN)
@@ -150,10 +149,10 @@ __device__ __forceinline__ void plan_block(int n_x, const unsigned long long* T_
       const int ni = items_of_cell(t);
       for (int c = 0; c < ni; ++c) items[baseI + c] = make_int2(i, c);
     }
-    thr_cell[i] = 0ull;
+    if (clear_thr) thr_cell[i] = 0ull;
     R[i] = r;
     IP[i] = baseI;
-    if (needs_kernel(reach, i, n_x)) {
+    if (cell_needs_kernel(reach, i, n_x)) {
       occ[baseN] = i;
       row_map[i] = baseN;
       ++baseN;
@@ -248,18 +247,29 @@ __global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned l
                                                        int* __restrict__ occ, int* __restrict__ row_map,
                                                        int2* __restrict__ items, long long max_items,
                                                        unsigned long long* __restrict__ thr_cell, DevHeader* hdr,
-                                                       int advance_step) {
-  plan_block(n_x, T, reach, R, IP, occ, row_map, items, max_items, thr_cell, hdr, advance_step);
+                                                       int advance_step, int clear_thr) {
+  plan_block(n_x, T, reach, R, IP, occ, row_map, items, max_items, thr_cell, hdr, advance_step, clear_thr);
+}
+
+cudaError_t launch_rows(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, cudaStream_t s,
+                        int32_t* zero_out) {
+  const int blocks = (p.n_x + kRowsWarps - 1) / kRowsWarps;
+  k_rows<<<blocks, kRowsWarps * 32, 0, s>>>(hist, p.n_x, p.n_M, v.D, v.T, v.reach,
+                                            reinterpret_cast<long long*>(rho), zero_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan_scan(const wmc_params& p, const View& v, int advance_step, int clear_thr, cudaStream_t s) {
+  k_plan<<<1, kPlanThreads, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.items,
+                                    layout(p).max_items, v.thr_cell, v.hdr, advance_step, clear_thr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_plan(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, int advance_step,
                         cudaStream_t s, int32_t* zero_out) {
-  const int blocks = (p.n_x + kRowsWarps - 1) / kRowsWarps;
-  k_rows<<<blocks, kRowsWarps * 32, 0, s>>>(hist, p.n_x, p.n_M, v.D, v.T, v.reach,
-                                            reinterpret_cast<long long*>(rho), zero_out);
-  k_plan<<<1, kPlanThreads, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.items,
-                                    layout(p).max_items, v.thr_cell, v.hdr, advance_step);
-  return cudaGetLastError();
+  cudaError_t e = launch_rows(p, v, hist, rho, s, zero_out);
+  if (e != cudaSuccess) return e;
+  return launch_plan_scan(p, v, advance_step, 1, s);
 }
 
 // ---------------------------------------------------------------- density

@@ -34,6 +34,7 @@ struct StepArgs {
   int n_x, n_M, Q, child_wrap;
   uint32_t sim, k0, k1, t;
   int t_from_device;
+  int rows_by_cell;  // read from the header at kernel start
 };
 
 // Loads the signed counts of cell i into s_n and their exclusive prefix of
@@ -87,7 +88,7 @@ __device__ __forceinline__ void create_pair(const StepArgs& a, uint32_t id, uint
                                             int sgn, int* s_acc, unsigned long long& pairs,
                                             unsigned long long& dropped, long long& drop_signed) {
   const int n_M = a.n_M;
-  const int orow = __ldg(a.row_map + i - 1 + d);
+  const int orow = a.rows_by_cell ? i - 1 + d : __ldg(a.row_map + i - 1 + d);
   const uint4 wp = philox4x32_10(make_uint4(id, t, kPurposePick, a.sim), a.k0, a.k1);
   const unsigned long long U2 = ((unsigned long long)(wp.x >> 5) << 26) | (unsigned long long)(wp.y >> 6);
   const int kp = sample_momentum(a, orow, U2);
@@ -119,6 +120,7 @@ struct ItemMeta {
 
 __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
   extern __shared__ int smem[];
+  a.rows_by_cell = (int)a.hdr->rows_by_cell;  // how the kernel stage laid out its CDF rows
   const int n_M = a.n_M;
   int* s_pre2 = smem;                    // 2 x (n_M + 1): prefix buffers
   int* s_n2 = s_pre2 + 2 * (n_M + 1);    // 2 x n_M: signed count buffers
@@ -350,6 +352,7 @@ cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_
   a.k1 = (uint32_t)(p.seed >> 32);
   a.t = t;
   a.t_from_device = t_from_device;
+  a.rows_by_cell = 0;
   k_step<<<step_grid(p.n_M), kStepThreads, step_smem(p.n_M), s>>>(a);
   return cudaGetLastError();
 }

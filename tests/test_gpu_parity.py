@@ -286,6 +286,29 @@ def test_production_loop_density_barrier_100(wmc):
     np.testing.assert_array_equal(got, got2)
 
 
+def test_production_loop_equals_table_path_on_its_own_kernel(wmc):
+    """wmc_run (kernel rows at the cell index where the reach bits need them,
+    the plan on a second stream) and the call-by-call table path (rows at the
+    occupied-list index) fed the same FP32 kernel values give the same
+    histogram and counters; the packet sits on the barrier so pairs are
+    created every step."""
+    from tests._util import gpu_run_table
+    wl = wi.BARRIER_100.replace(packet=wi.Packet(50e-9, 6e-9, 0.1, 200_000))
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    h0 = wi.initial_histogram(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    occ = torch.arange(wl.n_x, dtype=torch.int32, device="cuda")
+    tab = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), occ, ws).cpu().numpy()
+    got_t, ct = gpu_run_table(wmc, torch, p, tab, h0, 1, 12)
+    got_r, cr = gpu_run(wmc, torch, p, V, h0, 1, 12)
+    np.testing.assert_array_equal(got_r, got_t)
+    for key in ("pairs", "absorbed", "absorbed_signed", "dropped", "dropped_signed", "particle_steps"):
+        assert cr[key] == ct[key], key
+    assert cr["pairs"] > 1000
+
+
 def test_production_loop_barrier_2000_matches_oracle(wmc):
     """At the 2000-cell workload the packet is farther than L_C / 2 from the
     barrier, so the occupied cells have a zero kernel in both precisions and the
