@@ -306,6 +306,20 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
   float* s_dv = s_row + 32 * C;                                   // row g: dV(m) at s_dv[g 32 C + m - 1]
   const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
   if ((int)(blockIdx.x * kRowWarps * R) >= n_rows) return;
+  if (reach && (int)(gridDim.x * kRowWarps * R) >= n_rows) {
+    // one pass over the rows: a block none of whose cells needs a kernel only
+    // writes their zero outputs and skips staging the sine matrix
+    const int row = (int)(blockIdx.x * kRowWarps * R) + (int)threadIdx.x;
+    const bool need = threadIdx.x < kRowWarps * R && row < n_rows && cell_needs_kernel(reach, row, n_x);
+    if (!__syncthreads_or(need)) {
+      if (gamma && threadIdx.x < kRowWarps * R && row < n_rows) {
+        gamma[row] = 0.0;
+        gthr[row] = 0ull;
+        if (thr_cell) thr_cell[row] = 0ull;
+      }
+      return;
+    }
+  }
   {
     // stage the sine rows with eight loads in flight per thread
     const int nB = (h - 1) * h;
