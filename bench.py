@@ -281,6 +281,9 @@ def step_roofline(wmc, torch, p, wl, V, a, b, ws, stream, t, flush, n=20):
             wmc.kernel_eval_occupied(p, V, ws)
             T = a.abs().sum(dim=1).cpu().numpy().astype(np.float64)
             flush.zero_()
+            # keep the stream busy while the host enqueues, so that the events
+            # bracket device time only (not the host's launch latency)
+            torch.cuda._sleep(100_000)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             wmc.step(p, a, t + q, b, ws)

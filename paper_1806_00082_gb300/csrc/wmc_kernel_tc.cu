@@ -720,6 +720,302 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
   }
 }
 
+// ---------------------------------------------------------------- warp-specialised split form
+// FP16 hi/lo split: A = A_hi + 2^-11 A_lo, B = B_hi + 2^-11 B_lo, and
+//   A B ~ A_hi B_hi + 2^-11 (A_hi B_lo + A_lo B_hi)
+// (the A_lo B_lo term is below FP32 rounding).  One CTA per 128 rows and one
+// column tile.  K runs in two passes, [0, half) and [half, KB) blocks, each
+// into its own FP32 accumulator of A_hi B_hi (as the K halves of the other
+// forms), with the cross terms in a third; the half-K A_hi / A_lo blocks of a
+// pass stay in shared memory while B_hi / B_lo stream through a 2-stage ring.
+// Roles as in k_kernel_eval_tc_ws; the builders start the second pass once
+// the MMAs of the first have released A (a_free).
+constexpr int kSpStages = 2;
+constexpr int kSpMaxHalf = 4;  // half-K blocks resident: KB <= 8 (Q <= 1026)
+
+__host__ __device__ constexpr size_t ws_split_smem_bytes(int KB, int h) {
+  return (size_t)2 * ((KB + 1) / 2) * kTileBytes + (size_t)kSpStages * 2 * kTileBytes +
+         sizeof(float) * (size_t)((TM + 2 * h) > (kWsBuilders / 32) * kWsStageFloats
+                                      ? (TM + 2 * h)
+                                      : (kWsBuilders / 32) * kWsStageFloats);
+}
+
+__global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
+    const float* __restrict__ V, int n_x, int bc, int Q, const int* __restrict__ occ,
+    const int* __restrict__ n_occ_dev, int n_occ_host, const uint16_t* __restrict__ img_hi,
+    const uint16_t* __restrict__ img_lo, int KB, float c, float* __restrict__ VWh, unsigned int* __restrict__ flags) {
+  constexpr uint32_t idesc = idesc_f16(0u);  // FP16 x FP16 -> FP32
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int half = (KB + 1) / 2;
+  uint8_t* sAh = smem;                                        // half blocks of A_hi
+  uint8_t* sAl = smem + (size_t)half * kTileBytes;             // half blocks of A_lo
+  uint8_t* sB = smem + (size_t)2 * half * kTileBytes;          // stages of (B_hi, B_lo)
+  float* sV = reinterpret_cast<float*>(sB + (size_t)kSpStages * 2 * kTileBytes);  // shared with the staging
+  __shared__ __align__(8) uint64_t a_ready[kSpMaxHalf];
+  __shared__ __align__(8) uint64_t b_full[kSpStages], b_empty[kSpStages];
+  __shared__ __align__(8) uint64_t a_free, acc_full, drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+
+  const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
+  const int row0 = blockIdx.x * TM;
+  const int h = Q / 2;
+  if (row0 >= n_rows) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = blockIdx.y;
+  const int n_pass = KB > half ? 2 : 1;
+  const int n_tiles = KB;  // B tiles streamed: one per K block
+
+  if (warp == 0) tmem_alloc(&tmem_slot, 512u);
+  if (tid == 0) {
+    for (int q = 0; q < kSpMaxHalf; ++q) mbar_init(&a_ready[q], kWsBuilders);
+    for (int q = 0; q < kSpStages; ++q) {
+      mbar_init(&b_full[q], 1);
+      mbar_init(&b_empty[q], 1);
+    }
+    mbar_init(&a_free, 1);
+    mbar_init(&acc_full, 1);
+    mbar_init(&drain, 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t acc_m0 = tmem, acc_m1 = tmem + (uint32_t)TN, acc_x = tmem + 2u * TN;
+
+  if (warp == kWsBuilders / 32 + 1) {
+    // ---- B producer: tile kb of column tile nt, hi and lo, in K order
+    if (lane == 0) {
+      int issued = 0;
+      for (int t = 0; t < n_tiles && !s_abort; ++t) {
+        const int st = t % kSpStages;
+        if (t >= kSpStages && !mbar_wait(&b_empty[st], (uint32_t)(((t / kSpStages) - 1) & 1))) {
+          atomicOr(flags, WMC_FLAG_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        uint8_t* dst = sB + (size_t)st * 2 * kTileBytes;
+        const size_t off = ((size_t)nt * KB + t) * (kTileBytes / 2);
+        mbar_expect_tx(&b_full[st], 2 * kTileBytes);
+        bulk_g2s(dst, img_hi + off, kTileBytes, &b_full[st]);
+        bulk_g2s(dst + kTileBytes, img_lo + off, kTileBytes, &b_full[st]);
+        issued = t + 1;
+      }
+      if (s_abort)
+        for (int t = max(0, issued - kSpStages); t < issued; ++t)
+          (void)mbar_wait(&b_full[t % kSpStages], (uint32_t)((t / kSpStages) & 1));
+    }
+  } else if (warp == kWsBuilders / 32) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      for (int pass = 0; pass < n_pass && !s_abort; ++pass) {
+        const int kb0 = pass * half, kb1 = pass ? KB : half;
+        const uint32_t acc_m = pass ? acc_m1 : acc_m0;
+        for (int kb = kb0; kb < kb1; ++kb) {
+          const int kbl = kb - kb0, st = kb % kSpStages;
+          if (!mbar_wait(&a_ready[kbl], (uint32_t)(pass & 1)) ||
+              !mbar_wait(&b_full[st], (uint32_t)((kb / kSpStages) & 1))) {
+            atomicOr(flags, WMC_FLAG_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(sAh + (size_t)kbl * kTileBytes), al = smem_u32(sAl + (size_t)kbl * kTileBytes);
+          const uint32_t bh = smem_u32(sB + (size_t)st * 2 * kTileBytes), bl = bh + kTileBytes;
+#pragma unroll
+          for (int s4 = 0; s4 < TK / 16; ++s4) {
+            const uint32_t o = s4 * 2 * kLBO;
+            const uint64_t dah = smem_desc(ah + o), dbh = smem_desc(bh + o);
+            mma_f16(acc_m, dah, dbh, idesc, (kb == kb0 && s4 == 0) ? 0u : 1u);
+            mma_f16(acc_x, dah, smem_desc(bl + o), idesc, (kb == 0 && s4 == 0) ? 0u : 1u);
+            mma_f16(acc_x, smem_desc(al + o), dbh, idesc, 1u);
+          }
+          mma_commit(&b_empty[st]);
+        }
+        if (s_abort) break;
+        mma_commit(pass + 1 < n_pass ? &a_free : &acc_full);
+      }
+      if (s_abort) {
+        mma_commit(&drain);
+        (void)mbar_wait(&drain, 0u);
+      }
+    }
+  } else {
+    // ---- A builders (warps 0-15): both passes, then the epilogue
+    const int rc = tid & (TM - 1);
+    const int rowc = row0 + rc;
+    const bool validc = rowc < n_rows;
+    const int cellc = validc ? (occ ? __ldg(occ + rowc) : rowc % n_x) : 0;
+    const int potc = (occ || !validc) ? 0 : rowc / n_x;
+    const int cell0 = occ ? __ldg(occ + row0) : row0 % n_x;
+    const int pot0 = occ ? 0 : row0 / n_x;
+    const bool contig = builders_and(validc && cellc == cell0 + rc && potc == pot0);
+    if (contig) {
+      const float* V0 = V + (size_t)pot0 * n_x;
+      constexpr int kU = 4;
+      for (int q0 = tid; q0 < TM + 2 * h; q0 += kU * kWsBuilders) {
+        float v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int q = q0 + u * kWsBuilders;
+          v[u] = q < TM + 2 * h ? potential_at(V0, n_x, bc, (long long)cell0 - h + q) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (q0 + u * kWsBuilders < TM + 2 * h) sV[q0 + u * kWsBuilders] = v[u];
+      }
+      builders_sync();
+    }
+    const int rg = tid & 31, k8 = (tid >> 5) & 7, par = tid >> 8;
+    int cell_d[4];
+    bool valid_d[4];
+    const float* V_d[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int row = row0 + 4 * rg + d;
+      valid_d[d] = row < n_rows;
+      cell_d[d] = (contig || !valid_d[d]) ? 0 : (occ ? __ldg(occ + row) : row % n_x);
+      V_d[d] = V + (size_t)((occ || !valid_d[d]) ? 0 : row / n_x) * n_x;
+    }
+    const bool fast = contig && (h & 3) == 0;
+    for (int pass = 0; pass < n_pass; ++pass) {
+      const int kb0 = pass * half, kb1 = pass ? KB : half, cnt = kb1 - kb0;
+      if (pass > 0) {
+        // the first pass's MMAs must have read A before it is overwritten
+        const bool ok = __all_sync(0xffffffffu, !s_abort && mbar_wait(&a_free, 0u));
+        if (!ok) {
+          if (lane == 0) atomicOr(flags, WMC_FLAG_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+      }
+      for (int kbl = 1 - par; kbl < cnt; kbl += 2)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kbl])) : "memory");
+#pragma unroll 1
+      for (int kbl = par; kbl < cnt; kbl += 2) {
+        const int kb = kb0 + kbl;
+        const int m0 = kb * TK + k8 * 8 + 1;
+        float dv[4][8];
+        if (fast && m0 + 7 <= h - 1) {
+          float P[12], N[12];
+          const float* pp = sV + 4 * rg + h + m0 - 1;
+          const float* pn = sV + 4 * rg + h - m0 - 7;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float4 a = *reinterpret_cast<const float4*>(pp + 4 * q);
+            const float4 b = *reinterpret_cast<const float4*>(pn + 4 * q);
+            P[4 * q] = a.x, P[4 * q + 1] = a.y, P[4 * q + 2] = a.z, P[4 * q + 3] = a.w;
+            N[4 * q] = b.x, N[4 * q + 1] = b.y, N[4 * q + 2] = b.z, N[4 * q + 3] = b.w;
+          }
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) dv[d][e] = __fsub_rn(P[d + e + 1], N[d - e + 7]);
+        } else {
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int m = m0 + e;
+              dv[d][e] = 0.f;
+              if (m <= h - 1) {
+                if (contig) dv[d][e] = __fsub_rn(sV[4 * rg + d + h + m], sV[4 * rg + d + h - m]);
+                else if (valid_d[d])
+                  dv[d][e] = __fsub_rn(potential_at(V_d[d], n_x, bc, (long long)cell_d[d] + m),
+                                       potential_at(V_d[d], n_x, bc, (long long)cell_d[d] - m));
+              }
+            }
+        }
+        uint4 wh[4], wl[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            const uint16_t h0 = to_bits(dv[d][e], WMC_FP16), h1 = to_bits(dv[d][e + 1], WMC_FP16);
+            const uint16_t l0 = to_bits(__fmul_rn(__fsub_rn(dv[d][e], from_bits(h0, WMC_FP16)), 2048.f), WMC_FP16);
+            const uint16_t l1 =
+                to_bits(__fmul_rn(__fsub_rn(dv[d][e + 1], from_bits(h1, WMC_FP16)), 2048.f), WMC_FP16);
+            hw[e / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            lw[e / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+          }
+          wh[d] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          wl[d] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        uint8_t* bh = sAh + (size_t)kbl * kTileBytes;
+        uint8_t* bl = sAl + (size_t)kbl * kTileBytes;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int x = (i + (rg >> 1)) & 3;
+          const uint32_t off = core_offset(4 * rg + x, k8 * 8);
+          *reinterpret_cast<uint4*>(bh + off) = x == 0 ? wh[0] : x == 1 ? wh[1] : x == 2 ? wh[2] : wh[3];
+          *reinterpret_cast<uint4*>(bl + off) = x == 0 ? wl[0] : x == 1 ? wl[1] : x == 2 ? wl[2] : wl[3];
+        }
+        fence_proxy_async_smem();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kbl])) : "memory");
+      }
+    }
+    // epilogue: v = c ((hi-hi pass 0 + hi-hi pass 1) + 2^-11 cross)
+    const int quad = warp & 3, cq = warp >> 2;
+    float* stg = sV + warp * kWsStageFloats;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    const bool vec_ok = (h & 3) == 0 && (reinterpret_cast<uintptr_t>(VWh) & 15) == 0;
+    const bool ok = __all_sync(0xffffffffu, !s_abort && mbar_wait(&acc_full, 0u));
+    if (!ok) {
+      if (lane == 0) atomicOr(flags, WMC_FLAG_TIMEOUT);
+      s_abort = 1;
+    } else {
+      tc_fence_after();
+#pragma unroll 1
+      for (int hf = 0; hf < 2; ++hf) {
+        const int cc = cq * 32 + hf * 16;
+        const int col0 = nt * TN + cc;
+        float a[16], b[16], x[16];
+        tmem_ld16(acc_m0 + lane_base + (uint32_t)cc, a);
+        if (n_pass > 1) tmem_ld16(acc_m1 + lane_base + (uint32_t)cc, b);
+        tmem_ld16(acc_x + lane_base + (uint32_t)cc, x);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          float v = a[q];
+          if (n_pass > 1) v = __fadd_rn(v, b[q]);
+          a[q] = __fmul_rn(c, __fadd_rn(v, __fmul_rn(x[q], 0x1p-11f)));
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          *reinterpret_cast<float4*>(stg + lane * 16 + 4 * (g ^ ((lane >> 1) & 3))) =
+              make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int rr = 8 * i + (lane >> 2), g = lane & 3;
+          const float4 v = *reinterpret_cast<const float4*>(stg + rr * 16 + 4 * (g ^ ((rr >> 1) & 3)));
+          const int grow = row0 + quad * 32 + rr, gcol = col0 + 4 * g;
+          if (grow < n_rows && gcol < h) {
+            float* out = VWh + (size_t)grow * h + gcol;
+            if (vec_ok) {
+              *reinterpret_cast<float4*>(out) = v;
+            } else {
+              out[0] = v.x;
+              if (gcol + 1 < h) out[1] = v.y;
+              if (gcol + 2 < h) out[2] = v.z;
+              if (gcol + 3 < h) out[3] = v.w;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512u);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 struct TcImages {
   int KB, NT;
@@ -797,6 +1093,13 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
     cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_kernel_eval_tc<WMC_FP16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
                                                      base + n16, nullptr, g.KB, c, VWh, flags);
+  } else if (prec == WMC_FP16_SPLIT && (g.KB + 1) / 2 <= kSpMaxHalf &&
+             ws_split_smem_bytes(g.KB, g_h(p)) <= 226 * 1024) {
+    const size_t sm = ws_split_smem_bytes(g.KB, g_h(p));
+    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_kernel_eval_tc_ws_split<<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                           n_occ_host, base + n16, base + 2 * n16, g.KB, c, VWh,
+                                                           flags);
   } else if (prec == WMC_FP16_SPLIT) {
     const size_t sm = tc_smem_bytes(true, g_h(p));
     cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -101,15 +101,15 @@ def _sampled_err(got, wl, V, cells, n_sample, seed):
     return normwise(got[pick], ref)
 
 
-@pytest.mark.parametrize("form", ["bf16", "fp16"])
+@pytest.mark.parametrize("form", ["bf16", "fp16", "fp16_split"])
 @pytest.mark.parametrize("wl,n", [(wi.DOUBLE_BARRIER_16384, 16384 - 77), (wi.DOUBLE_BARRIER_16384, 16384),
                                   (wi.BARRIER_2000, 40_000 + 45)])
 def test_tensorcore_whole_row_form(wmc, form, wl, n):
-    """Row counts that fill the GPU with whole-row CTAs (the resident-A,
-    warp-specialised contraction): every cell of the domain (contiguous
-    windows), a permutation with a ragged last tile, and a list longer than
-    the domain with repeated cells; sampled rows against the FP64 oracle, every
-    row finite, and each repeated cell bit-identical."""
+    """Row counts that fill the GPU (the warp-specialised contractions):
+    every cell of the domain (contiguous windows), a permutation with a ragged
+    last tile, and a list longer than the domain with repeated cells; sampled
+    rows against the FP64 oracle, every row finite, and each repeated cell
+    bit-identical."""
     p = wmc.Params.of(wl)
     V = wi.potential(wl)
     ws = wmc.workspace(p)
@@ -129,7 +129,7 @@ def test_tensorcore_whole_row_form(wmc, form, wl, n):
     assert wmc.get_counters(p, ws)["flags"] == 0
 
 
-@pytest.mark.parametrize("form", ["bf16", "fp16"])
+@pytest.mark.parametrize("form", ["bf16", "fp16", "fp16_split"])
 def test_tensorcore_implicit_rows_many_potentials(wmc, form):
     """Implicit rows (row r = cell r mod n_x of potential r / n_x) over several
     potentials, with n_x not a multiple of the 128-row tile, so that tiles
