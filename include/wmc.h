@@ -195,7 +195,7 @@ wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows,
  * ------------------------------------------------------------------------- */
 
 /* Rule 2 rebuild: enumerates the survivors of the net histogram hist [dev]
- * int32[n_x][n_M] (row-major ids, work items of 4096 particles), marks the
+ * int32[n_x][n_M] (row-major ids, work items of at most 7168 ids of one cell), marks the
  * cells the next drift can reach (occupied cells and their neighbour in each
  * drift direction present) as the occupied list for the kernel, and, if
  * rho [dev] int64[n_x] is not NULL, writes the density (rule 1) of hist.
