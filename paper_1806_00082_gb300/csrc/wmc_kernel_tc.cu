@@ -391,9 +391,12 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
 }
 
 // ---------------------------------------------------------------- warp-specialised form
-// BF16 / FP16: one CTA per 128 rows and a run of column tiles.  The whole A
-// operand (128 x Kp, 16-bit) stays in shared memory, so it is built once and
-// reused by every column tile of the CTA.  Roles (576 threads):
+// BF16 / FP16: one CTA per 128 rows and a run of column tiles of TNW = 128 or
+// 256 columns (the MMA's N; 256 halves the A operand reads per flop and is
+// used for windows wider than 128).  The whole A operand (128 x Kp, 16-bit)
+// stays in shared memory, so it is built once and reused by every column tile
+// of the CTA.  A B stage holds TNW / 128 consecutive 128 x 64 operand images,
+// which in the core-matrix layout are one TNW x 64 operand.  Roles (576 threads):
 //   warps 0-15 build A (four rows and one core-matrix column of every other
 //              block each), signalling a_ready[kb]; then run the epilogue
 //              of each column tile from TMEM (warp w reads lane quadrant w % 4,
@@ -403,7 +406,8 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
 //   warp 16    one thread issues the MMAs: tile j into the FP32 accumulator
 //              buffer j % 2, waiting for A blocks, B stages and a drained
 //              buffer, committing each B stage and each tile;
-//   warp 17    one thread streams the B operand images through a 4-stage ring,
+//   warp 17    one thread streams the B operand images through a ring of 4
+//              (TNW 128) or 2 (TNW 256) stages,
 //              starting as soon as the barriers exist.
 // Synchronisation is by mbarriers and one named barrier among the builders;
 // every wait is bounded and an abort flag makes all roles drain to the final
@@ -417,8 +421,10 @@ constexpr int kWsStageFloats = 32 * 16;  // epilogue staging per warp: 32 rows x
 
 // A blocks, B ring, then one region used first for the potential window
 // (TM + 2h floats, building A) and then for the epilogue staging.
-__host__ __device__ constexpr size_t ws_smem_bytes(int KB, int h) {
-  return (size_t)KB * kTileBytes + (size_t)kWsStages * kTileBytes +
+__host__ __device__ constexpr int ws_stages(int tnw) { return tnw == 256 ? 2 : kWsStages; }
+
+__host__ __device__ constexpr size_t ws_smem_bytes(int KB, int h, int tnw) {
+  return (size_t)KB * kTileBytes + (size_t)ws_stages(tnw) * (tnw / TN) * kTileBytes +
          sizeof(float) * (size_t)((TM + 2 * h) > (kWsBuilders / 32) * kWsStageFloats
                                       ? (TM + 2 * h)
                                       : (kWsBuilders / 32) * kWsStageFloats);
@@ -451,7 +457,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
-template <int PREC>
+template <int PREC, int TNW>
 __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float* __restrict__ V, int n_x, int bc,
                                                                      int Q, const int* __restrict__ occ,
                                                                      const int* __restrict__ n_occ_dev, int n_occ_host,
@@ -459,12 +465,16 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
                                                                      int NT, int n_split, float c,
                                                                      float* __restrict__ VWh,
                                                                      unsigned int* __restrict__ flags) {
-  constexpr int kind_fmt = PREC == WMC_BF16 ? 1 : 0;
-  constexpr uint32_t idesc = idesc_f16(kind_fmt);
+  constexpr uint32_t kind_fmt = PREC == WMC_BF16 ? 1u : 0u;
+  constexpr uint32_t idesc =
+      (1u << 4) | (kind_fmt << 7) | (kind_fmt << 10) | ((uint32_t)(TNW >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  constexpr int STG = ws_stages(TNW);          // B stages
+  constexpr int IMG = TNW / TN;                // 128-column images per stage
+  constexpr uint32_t kStageBytes = IMG * kTileBytes;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                                         // KB blocks of 128 x 64
-  uint8_t* sB = smem + (size_t)KB * kTileBytes;              // kWsStages stages
-  float* sV = reinterpret_cast<float*>(sB + (size_t)kWsStages * kTileBytes);  // shared with the staging
+  uint8_t* sB = smem + (size_t)KB * kTileBytes;              // STG stages of TNW x 64
+  float* sV = reinterpret_cast<float*>(sB + (size_t)STG * kStageBytes);  // shared with the staging
   __shared__ __align__(8) uint64_t a_ready[kWsMaxKB];
   __shared__ __align__(8) uint64_t b_full[kWsStages], b_empty[kWsStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
@@ -477,16 +487,18 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
   const int h = Q / 2;
   if (row0 >= n_rows) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t n_cols = 2u * TN;  // two accumulator buffers of 128 columns
-  // this CTA's column tiles [nt_begin, nt_begin + n_my); local tile j = nt - nt_begin
-  const int nt_begin = (int)(((long long)blockIdx.y * NT) / n_split);
-  const int n_my = (int)(((long long)(blockIdx.y + 1) * NT) / n_split) - nt_begin;
+  const uint32_t n_cols = 2u * TNW;  // two accumulator buffers of TNW columns
+  // NT counts 128-column images; this CTA's TNW-column tiles are
+  // [nt_begin, nt_begin + n_my); local tile j = nt - nt_begin
+  const int NTW = (NT + IMG - 1) / IMG;
+  const int nt_begin = (int)(((long long)blockIdx.y * NTW) / n_split);
+  const int n_my = (int)(((long long)(blockIdx.y + 1) * NTW) / n_split) - nt_begin;
   const int n_tiles = n_my * KB;
 
   if (warp == 0) tmem_alloc(&tmem_slot, n_cols);
   if (tid == 0) {
     for (int q = 0; q < KB; ++q) mbar_init(&a_ready[q], kWsBuilders);
-    for (int q = 0; q < kWsStages; ++q) {
+    for (int q = 0; q < STG; ++q) {
       mbar_init(&b_full[q], 1);
       mbar_init(&b_empty[q], 1);
     }
@@ -508,21 +520,23 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
     if (lane == 0) {
       int issued = 0;
       for (int t = 0; t < n_tiles && !s_abort; ++t) {
-        const int st = t % kWsStages;
-        if (t >= kWsStages && !mbar_wait(&b_empty[st], (uint32_t)(((t / kWsStages) - 1) & 1))) {
+        const int st = t % STG;
+        if (t >= STG && !mbar_wait(&b_empty[st], (uint32_t)(((t / STG) - 1) & 1))) {
           atomicOr(flags, WMC_FLAG_TIMEOUT);
           s_abort = 1;
           break;
         }
-        const int nt = nt_begin + t / KB, kb = t % KB;
-        mbar_expect_tx(&b_full[st], kTileBytes);
-        bulk_g2s(sB + (size_t)st * kTileBytes, img_b + ((size_t)nt * KB + kb) * (kTileBytes / 2), kTileBytes,
-                 &b_full[st]);
+        const int n0 = (nt_begin + t / KB) * IMG, kb = t % KB;
+        const int n_img = min(IMG, NT - n0);  // images past the window stay stale (columns >= h)
+        mbar_expect_tx(&b_full[st], (uint32_t)n_img * kTileBytes);
+        for (int u = 0; u < n_img; ++u)
+          bulk_g2s(sB + (size_t)st * kStageBytes + (size_t)u * kTileBytes,
+                   img_b + ((size_t)(n0 + u) * KB + kb) * (kTileBytes / 2), kTileBytes, &b_full[st]);
         issued = t + 1;
       }
       if (s_abort)  // let the copies still in flight land before the CTA exits (bounded)
-        for (int t = max(0, issued - kWsStages); t < issued; ++t)
-          (void)mbar_wait(&b_full[t % kWsStages], (uint32_t)((t / kWsStages) & 1));
+        for (int t = max(0, issued - STG); t < issued; ++t)
+          (void)mbar_wait(&b_full[t % STG], (uint32_t)((t / STG) & 1));
     }
   } else if (warp == kWsBuilders / 32) {
     // ---- MMA issuer
@@ -535,11 +549,11 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
           break;
         }
         tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)(buf * TN);
+        const uint32_t acc = tmem + (uint32_t)(buf * TNW);
         for (int kb = 0; kb < KB; ++kb) {
-          const int t = j * KB + kb, st = t % kWsStages;
+          const int t = j * KB + kb, st = t % STG;
           if ((j == 0 && !mbar_wait(&a_ready[kb], 0u)) ||
-              !mbar_wait(&b_full[st], (uint32_t)((t / kWsStages) & 1))) {
+              !mbar_wait(&b_full[st], (uint32_t)((t / STG) & 1))) {
             atomicOr(flags, WMC_FLAG_TIMEOUT);
             s_abort = 1;
             break;
@@ -547,7 +561,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
           tc_fence_after();
           const int first = kb == 0;
           const uint32_t a_base = smem_u32(sA + (size_t)kb * kTileBytes);
-          const uint32_t b_base = smem_u32(sB + (size_t)st * kTileBytes);
+          const uint32_t b_base = smem_u32(sB + (size_t)st * kStageBytes);
 #pragma unroll
           for (int s4 = 0; s4 < TK / 16; ++s4)
             mma_f16(acc, smem_desc(a_base + s4 * 2 * kLBO), smem_desc(b_base + s4 * 2 * kLBO), idesc,
@@ -659,7 +673,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
       fence_proxy_async_smem();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kb])) : "memory");
     }
-    // epilogue of each column tile: warp w reads lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31
+    // epilogue of each column tile: warp w reads lanes 32 (w % 4) .. + 31, columns TNW/4 (w / 4) .. + TNW/4 - 1
     const int quad = warp & 3, cq = warp >> 2;
     float* stg = sV + warp * kWsStageFloats;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
@@ -675,11 +689,11 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
       }
       tc_fence_after();
 #pragma unroll 1
-      for (int hf = 0; hf < 2; ++hf) {
-        const int cc = cq * 32 + hf * 16;
-        const int col0 = (nt_begin + j) * TN + cc;
+      for (int hf = 0; hf < TNW / 64; ++hf) {
+        const int cc = cq * (TNW / 4) + hf * 16;
+        const int col0 = (nt_begin + j) * TNW + cc;
         float a[16];
-        tmem_ld16(tmem + (uint32_t)(buf * TN) + lane_base + (uint32_t)cc, a);
+        tmem_ld16(tmem + (uint32_t)(buf * TNW) + lane_base + (uint32_t)cc, a);
         // row `lane` of the piece; its four 16-byte groups are XOR-swizzled by
         // (row / 2) % 4, which keeps both the row-wise writes and the
         // group-wise reads below free of bank conflicts
@@ -1054,33 +1068,41 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   dim3 grid((max_rows + TM - 1) / TM, g.NT);
   const int row_tiles = (max_rows + TM - 1) / TM;
-  const size_t ws_sm = ws_smem_bytes(g.KB, g_h(p));
+  const int tnw = g_h(p) > TN ? 256 : 128;
+  const size_t ws_sm = ws_smem_bytes(g.KB, g_h(p), tnw);
   if ((prec == WMC_BF16 || prec == WMC_FP16) && g.KB <= kWsMaxKB && ws_sm <= 226 * 1024) {
     // warp-specialised form.  The column tiles are split over grid.y by the
     // factor that minimises waves x per-CTA work, with the fixed part of a CTA
-    // (set-up and building A) counted as three column tiles.
+    // (set-up and building A) counted as three 128-column tiles.
     const uint16_t* img = prec == WMC_BF16 ? base : base + n16;
     const long long sms = num_sms();
+    const int ntw = (g.NT * TN + tnw - 1) / tnw;
     int n_split = 1;
     long long best = -1;
-    for (int ns = 1; ns <= g.NT; ns *= 2) {
+    for (int ns = 1; ns <= ntw; ns *= 2) {
       const long long waves = ((long long)row_tiles * ns + sms - 1) / sms;
-      const long long cost = waves * (3 + (g.NT + ns - 1) / ns);
+      const long long cost = waves * (3 + (long long)((ntw + ns - 1) / ns) * (tnw / TN));
       if (best < 0 || cost < best) {
         best = cost;
         n_split = ns;
       }
     }
     const dim3 ws_grid(row_tiles, n_split);
+#define WMC_LAUNCH_WS(PR, TW)                                                                                      \
+  do {                                                                                                             \
+    cudaFuncSetAttribute(k_kernel_eval_tc_ws<PR, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_sm);    \
+    k_kernel_eval_tc_ws<PR, TW><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,  \
+                                                                   n_occ_host, img, g.KB, g.NT, n_split, c, VWh,   \
+                                                                   flags);                                         \
+  } while (0)
     if (prec == WMC_BF16) {
-      cudaFuncSetAttribute(k_kernel_eval_tc_ws<WMC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_sm);
-      k_kernel_eval_tc_ws<WMC_BF16><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
-                                                                 n_occ_host, img, g.KB, g.NT, n_split, c, VWh, flags);
+      if (tnw == 256) WMC_LAUNCH_WS(WMC_BF16, 256);
+      else WMC_LAUNCH_WS(WMC_BF16, 128);
     } else {
-      cudaFuncSetAttribute(k_kernel_eval_tc_ws<WMC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_sm);
-      k_kernel_eval_tc_ws<WMC_FP16><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
-                                                                 n_occ_host, img, g.KB, g.NT, n_split, c, VWh, flags);
+      if (tnw == 256) WMC_LAUNCH_WS(WMC_FP16, 256);
+      else WMC_LAUNCH_WS(WMC_FP16, 128);
     }
+#undef WMC_LAUNCH_WS
     return cudaGetLastError();
   }
   if (prec == WMC_BF16) {
