@@ -33,7 +33,7 @@ namespace wmc {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 64;
-constexpr uint32_t kLBO = 128, kSBO = 1024;
+constexpr uint32_t kSBO = 1024, kKStepBytes = 32;  // atom stride; bytes per K step of 16
 constexpr uint32_t kTileBytes = TN * TK * 2;  // one 128 x 64 16-bit operand image
 constexpr long long kWaitCycles = 2000000000ll;
 
@@ -91,10 +91,21 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// K-major, no-swizzle shared-memory matrix descriptor (version 1).
+// K-major shared-memory matrix descriptor (version 1) of the 128-byte swizzled
+// layout: 8-row atoms of 128-byte rows (64 16-bit K values) 1024 bytes apart
+// (SBO), the 16-byte chunks of row r XOR-swizzled by r % 8; a K step of 16
+// values advances the start address by 32 bytes inside the atom.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(kSBO >> 4) << 32) |
-         (1ull << 46);
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(kSBO >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
+// Dynamic shared memory rounded up to the 1024-byte alignment the swizzled
+// atoms need (launches request kSmemAlignPad extra bytes).
+constexpr uint32_t kSmemAlignPad = 1024;
+__device__ __forceinline__ uint8_t* align_smem(uint8_t* p) {
+  const uint32_t a = smem_u32(p);
+  return p + (((a + 1023u) & ~1023u) - a);
 }
 
 // Instruction descriptor of kind::f16: D FP32, A and B of one 16-bit format
@@ -150,9 +161,11 @@ __device__ __forceinline__ float potential_at(const float* __restrict__ V, int n
   return __ldg(V + (l < 0 ? 0 : n_x - 1));
 }
 
-// Byte offset of element (row, k) of a 128 x 64 K-major core-matrix image.
+// Byte offset of element (row, k) of a 128 x 64 K-major operand block in the
+// 128-byte swizzled layout (row r at 128 r, chunk k / 8 stored at chunk
+// (k / 8) ^ (r % 8)); blocks of consecutive rows concatenate.
 __host__ __device__ __forceinline__ uint32_t core_offset(int row, int k) {
-  return (uint32_t)((row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
+  return (uint32_t)(row * 128 + ((((k >> 3) ^ (row & 7)) & 7) << 4) + (k & 7) * 2);
 }
 
 __device__ __forceinline__ uint16_t to_bits(float x, int prec) {
@@ -207,7 +220,7 @@ __global__ void k_init_tc_images(int Q, int KB, int NT, uint16_t* __restrict__ i
 constexpr int kStages = 2;
 
 __host__ __device__ constexpr size_t tc_smem_bytes(bool split, int h) {
-  return (size_t)(split ? 8 : 4) * kTileBytes + sizeof(float) * (size_t)(TM + 2 * h);
+  return kSmemAlignPad + (size_t)(split ? 8 : 4) * kTileBytes + sizeof(float) * (size_t)(TM + 2 * h);
 }
 
 template <int PREC>
@@ -221,7 +234,8 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
   constexpr int kind_fmt = PREC == WMC_BF16 ? 1 : 0;
   constexpr uint32_t kCols = SPLIT ? 512u : 256u;
   constexpr uint32_t idesc = idesc_f16(kind_fmt);
-  extern __shared__ __align__(1024) uint8_t smem[];
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = align_smem(smem_raw);
   uint8_t* sA[kStages] = {smem, smem + kTileBytes};
   uint8_t* sB[kStages] = {smem + 2 * kTileBytes, smem + 3 * kTileBytes};
   uint8_t* sAl[kStages] = {smem + 4 * kTileBytes, smem + 5 * kTileBytes};  // split form only
@@ -326,12 +340,12 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
         const int first = kb == 0 || kb == half_kb;
 #pragma unroll
         for (int s = 0; s < TK / 16; ++s) {
-          const uint64_t a_hi = smem_desc(smem_u32(sA[st]) + s * 2 * kLBO);
-          const uint64_t b_hi = smem_desc(smem_u32(sB[st]) + s * 2 * kLBO);
+          const uint64_t a_hi = smem_desc(smem_u32(sA[st]) + s * kKStepBytes);
+          const uint64_t b_hi = smem_desc(smem_u32(sB[st]) + s * kKStepBytes);
           mma_f16(acc, a_hi, b_hi, idesc, (first && s == 0) ? 0u : 1u);
           if (SPLIT) {
-            const uint64_t a_lo = smem_desc(smem_u32(sAl[st]) + s * 2 * kLBO);
-            const uint64_t b_lo = smem_desc(smem_u32(sBl[st]) + s * 2 * kLBO);
+            const uint64_t a_lo = smem_desc(smem_u32(sAl[st]) + s * kKStepBytes);
+            const uint64_t b_lo = smem_desc(smem_u32(sBl[st]) + s * kKStepBytes);
             mma_f16(accX, a_hi, b_lo, idesc, (kb == 0 && s == 0) ? 0u : 1u);
             mma_f16(accX, a_lo, b_hi, idesc, 1u);
           }
@@ -424,7 +438,7 @@ constexpr int kWsStageFloats = 32 * 16;  // epilogue staging per warp: 32 rows x
 __host__ __device__ constexpr int ws_stages(int tnw) { return tnw == 256 ? 2 : kWsStages; }
 
 __host__ __device__ constexpr size_t ws_smem_bytes(int KB, int h, int tnw) {
-  return (size_t)KB * kTileBytes + (size_t)ws_stages(tnw) * (tnw / TN) * kTileBytes +
+  return kSmemAlignPad + (size_t)KB * kTileBytes + (size_t)ws_stages(tnw) * (tnw / TN) * kTileBytes +
          sizeof(float) * (size_t)((TM + 2 * h) > (kWsBuilders / 32) * kWsStageFloats
                                       ? (TM + 2 * h)
                                       : (kWsBuilders / 32) * kWsStageFloats);
@@ -471,7 +485,8 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
   constexpr int STG = ws_stages(TNW);          // B stages
   constexpr int IMG = TNW / TN;                // 128-column images per stage
   constexpr uint32_t kStageBytes = IMG * kTileBytes;
-  extern __shared__ __align__(1024) uint8_t smem[];
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = align_smem(smem_raw);
   uint8_t* sA = smem;                                         // KB blocks of 128 x 64
   uint8_t* sB = smem + (size_t)KB * kTileBytes;              // STG stages of TNW x 64
   float* sV = reinterpret_cast<float*>(sB + (size_t)STG * kStageBytes);  // shared with the staging
@@ -564,7 +579,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
           const uint32_t b_base = smem_u32(sB + (size_t)st * kStageBytes);
 #pragma unroll
           for (int s4 = 0; s4 < TK / 16; ++s4)
-            mma_f16(acc, smem_desc(a_base + s4 * 2 * kLBO), smem_desc(b_base + s4 * 2 * kLBO), idesc,
+            mma_f16(acc, smem_desc(a_base + s4 * kKStepBytes), smem_desc(b_base + s4 * kKStepBytes), idesc,
                     (first && s4 == 0) ? 0u : 1u);
           mma_commit(&b_empty[st]);
         }
@@ -748,7 +763,7 @@ constexpr int kSpStages = 2;
 constexpr int kSpMaxHalf = 4;  // half-K blocks resident: KB <= 8 (Q <= 1026)
 
 __host__ __device__ constexpr size_t ws_split_smem_bytes(int KB, int h) {
-  return (size_t)2 * ((KB + 1) / 2) * kTileBytes + (size_t)kSpStages * 2 * kTileBytes +
+  return kSmemAlignPad + (size_t)2 * ((KB + 1) / 2) * kTileBytes + (size_t)kSpStages * 2 * kTileBytes +
          sizeof(float) * (size_t)((TM + 2 * h) > (kWsBuilders / 32) * kWsStageFloats
                                       ? (TM + 2 * h)
                                       : (kWsBuilders / 32) * kWsStageFloats);
@@ -759,7 +774,8 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
     const int* __restrict__ n_occ_dev, int n_occ_host, const uint16_t* __restrict__ img_hi,
     const uint16_t* __restrict__ img_lo, int KB, float c, float* __restrict__ VWh, unsigned int* __restrict__ flags) {
   constexpr uint32_t idesc = idesc_f16(0u);  // FP16 x FP16 -> FP32
-  extern __shared__ __align__(1024) uint8_t smem[];
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = align_smem(smem_raw);
   const int half = (KB + 1) / 2;
   uint8_t* sAh = smem;                                        // half blocks of A_hi
   uint8_t* sAl = smem + (size_t)half * kTileBytes;             // half blocks of A_lo
@@ -840,7 +856,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
           const uint32_t bh = smem_u32(sB + (size_t)st * 2 * kTileBytes), bl = bh + kTileBytes;
 #pragma unroll
           for (int s4 = 0; s4 < TK / 16; ++s4) {
-            const uint32_t o = s4 * 2 * kLBO;
+            const uint32_t o = s4 * kKStepBytes;
             const uint64_t dah = smem_desc(ah + o), dbh = smem_desc(bh + o);
             mma_f16(acc_m, dah, dbh, idesc, (kb == kb0 && s4 == 0) ? 0u : 1u);
             mma_f16(acc_x, dah, smem_desc(bl + o), idesc, (kb == 0 && s4 == 0) ? 0u : 1u);
