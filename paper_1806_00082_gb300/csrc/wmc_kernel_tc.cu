@@ -129,6 +129,8 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void tmem_wait16(uint32_t* r);
+
 // 16 consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
@@ -138,9 +140,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  tmem_wait16(r);
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Split form of tmem_ld16: the load is issued into r, and tmem_wait16 waits
+// for all loads in flight while naming r as read-write, so that no use of r
+// can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 // 32 consecutive FP32 columns of this thread's TMEM lane, waited for.
@@ -519,7 +541,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(&acc_full[q], 1);
-      mbar_init(&acc_empty[q], kWsBuilders);
+      mbar_init(&acc_empty[q], kWsBuilders / 32);  // one arrival per epilogue warp
     }
     mbar_init(&drain, 1);
     fence_mbar_init();
@@ -695,28 +717,38 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
     const bool vec_ok = (h & 3) == 0 && (reinterpret_cast<uintptr_t>(VWh) & 15) == 0;
     for (int j = 0; j < n_my; ++j) {
       const int buf = j & 1;
-      // warp-uniform decision: the TMEM loads below are warp-collective
-      const bool ok = __all_sync(0xffffffffu, !s_abort && mbar_wait(&acc_full[buf], (uint32_t)((j >> 1) & 1)));
+      // lane 0 waits for the tile; the decision is warp-uniform because the
+      // TMEM loads below are warp-collective
+      int okw = 1;
+      if (lane == 0) okw = !s_abort && mbar_wait(&acc_full[buf], (uint32_t)((j >> 1) & 1));
+      const bool ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
       if (!ok) {
         if (lane == 0) atomicOr(flags, WMC_FLAG_TIMEOUT);
         s_abort = 1;
         break;
       }
       tc_fence_after();
-#pragma unroll 1
-      for (int hf = 0; hf < TNW / 64; ++hf) {
+      // pieces of 16 columns; the load of piece hf + 1 is in flight while
+      // piece hf is scaled, transposed and stored
+      constexpr int NP = TNW / 64;
+      uint32_t rg2[2][16];
+      const uint32_t tbase = tmem + (uint32_t)(buf * TNW) + lane_base + (uint32_t)(cq * (TNW / 4));
+      tmem_ld16_issue(tbase, rg2[0]);
+      tmem_wait16(rg2[0]);
+#pragma unroll
+      for (int hf = 0; hf < NP; ++hf) {
+        if (hf + 1 < NP) tmem_ld16_issue(tbase + (uint32_t)((hf + 1) * 16), rg2[(hf + 1) & 1]);
+        const uint32_t* a = rg2[hf & 1];
         const int cc = cq * (TNW / 4) + hf * 16;
         const int col0 = (nt_begin + j) * TNW + cc;
-        float a[16];
-        tmem_ld16(tmem + (uint32_t)(buf * TNW) + lane_base + (uint32_t)cc, a);
         // row `lane` of the piece; its four 16-byte groups are XOR-swizzled by
         // (row / 2) % 4, which keeps both the row-wise writes and the
         // group-wise reads below free of bank conflicts
 #pragma unroll
         for (int g = 0; g < 4; ++g)
           *reinterpret_cast<float4*>(stg + lane * 16 + 4 * (g ^ ((lane >> 1) & 3))) =
-              make_float4(__fmul_rn(c, a[4 * g]), __fmul_rn(c, a[4 * g + 1]), __fmul_rn(c, a[4 * g + 2]),
-                          __fmul_rn(c, a[4 * g + 3]));
+              make_float4(__fmul_rn(c, __uint_as_float(a[4 * g])), __fmul_rn(c, __uint_as_float(a[4 * g + 1])),
+                          __fmul_rn(c, __uint_as_float(a[4 * g + 2])), __fmul_rn(c, __uint_as_float(a[4 * g + 3])));
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -736,9 +768,12 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
           }
         }
         __syncwarp();
+        if (hf + 1 < NP) tmem_wait16(rg2[(hf + 1) & 1]);
       }
       tc_fence_before();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
     }
   }
   tc_fence_before();
