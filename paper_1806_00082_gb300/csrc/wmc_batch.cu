@@ -439,11 +439,15 @@ __global__ __launch_bounds__(kBatchRowWarps * 32) void k_b_kernel_rows(
       s_dv[m - 1] = m <= h - 1 ? __fsub_rn(pot(Vs, s.n_x, s.bc, (long long)i + m), pot(Vs, s.n_x, s.bc, (long long)i - m))
                                : 0.f;
     }
+    bool nz = false;  // a flat potential over the window gives an exactly zero row: skip the sums
+#pragma unroll
+    for (int q = 0; q < C; ++q) nz |= s_dv[lane + 32 * q] != 0.f;
+    nz = __any_sync(0xffffffffu, nz);
     __syncwarp();
     float sacc[C], eacc[C];
 #pragma unroll
     for (int cc = 0; cc < C; ++cc) sacc[cc] = eacc[cc] = 0.f;
-    for (int m0 = 1; m0 <= h - 1; m0 += 32) {
+    for (int m0 = 1; nz && m0 <= h - 1; m0 += 32) {
       float part[C];
 #pragma unroll
       for (int cc = 0; cc < C; ++cc) part[cc] = 0.f;
@@ -476,7 +480,7 @@ __global__ __launch_bounds__(kBatchRowWarps * 32) void k_b_kernel_rows(
     double g;
     int sc;
     long long tot;
-    warp_row_cdf(xres, Q, r0, n_M, s.log2_nM, lane, cdf + (size_t)row * NM, g, sc, tot);
+    warp_row_cdf(xres, Q, r0, n_M, s.log2_nM, lane, cdf + (size_t)row * NM, g, sc, tot, false);
     if (lane == 0) {
       gamma[row] = g;
       const unsigned long long thr = g > 0.0 ? event_threshold(g, s.dt, flags) : 0ull;
@@ -507,18 +511,19 @@ struct BatchStepArgs {
 
 // One warp per work item: an item is a run of 32 x per_thread ids of one row
 // (quad-aligned to the global ids), so a sparse row costs one warp, not a
-// block.  Each warp owns its slice of shared memory (row prefix, signed
-// counts, and the three output rows i-1, i, i+1 it accumulates into) and
-// takes items from the global ticket without block-wide barriers.
+// block.  Each warp owns its slice of shared memory (row prefix and signed
+// counts) and takes items from the global ticket without block-wide barriers;
+// parents and children go to the output histogram with global atomics, one
+// per run of ids in a bucket (lanes ending in the same bucket combine first),
+// so a sparse item touches only the buckets it holds.
 constexpr int kBStepWarps = 8;
 
 __global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a) {
   extern __shared__ int smem[];
   const int NM = a.NM;
   const int tid = threadIdx.x, lane = tid & 31;
-  int* s_pre = smem + (size_t)(tid >> 5) * (5 * NM + 1);
+  int* s_pre = smem + (size_t)(tid >> 5) * (2 * NM + 1);
   int* s_n = s_pre + (NM + 1);
-  int* s_acc = s_n + NM;
   __shared__ unsigned long long s_red[5][kBStepWarps];
   const uint32_t t = a.hdr->step;
   const int n_items = a.hdr->n_items;
@@ -545,9 +550,9 @@ __global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a)
     const unsigned long long thr_p = i + 1 < n_x ? __ldg(a.thr_cell + cg + 1) : 0ull;
     const uint32_t sim = S.sim, k0 = S.k0, k1 = S.k1;
     const int32_t* hrow = a.hist_in + S.hist_off;
+    int32_t* hout = a.hist_out + S.hist_off + (size_t)(i - 1) * n_M;  // rows i-1, i, i+1 at hout + d n_M
     const uint32_t* xlo = a.xlo + S.tab_off;
     const uint32_t* xhi = a.xhi + S.tab_off;
-    for (int q = lane; q < 3 * n_M; q += 32) s_acc[q] = 0;
     warp_row_prefix(hrow, i, n_M, s_n, s_pre, lane);
     __syncwarp();
 
@@ -582,10 +587,10 @@ __global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a)
           if (id < g0 || id >= g1) continue;
           if (id >= end_g) {
             const int stay = n_tot - n_mov;
-            if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
+            if (stay) atomicAdd(hout + (size_t)n_M + k, sgn * stay);
             if (n_mov) {
               if ((unsigned)(i + dir) < (unsigned)n_x) {
-                atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * n_mov);
+                atomicAdd(hout + (size_t)(dir + 1) * n_M + k, sgn * n_mov);
               } else {
                 absorbed += n_mov;
                 abs_signed += sgn * n_mov;
@@ -626,7 +631,7 @@ __global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a)
                 }
                 kc = ((kc % n_M) + n_M) % n_M;
               }
-              atomicAdd(&s_acc[dd * n_M + kc], sc2[qq]);
+              atomicAdd(hout + (size_t)dd * n_M + kc, sc2[qq]);
             }
           }
         }
@@ -637,23 +642,14 @@ __global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a)
     const int stay = __reduce_add_sync(peers, n_tot - n_mov);
     const int mov = __reduce_add_sync(peers, n_mov);
     if (key >= 0 && lane == __ffs(peers) - 1) {
-      if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
+      if (stay) atomicAdd(hout + (size_t)n_M + k, sgn * stay);
       if (mov) {
         if ((unsigned)(i + dir) < (unsigned)n_x) {
-          atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * mov);
+          atomicAdd(hout + (size_t)(dir + 1) * n_M + k, sgn * mov);
         } else {
           absorbed += mov;
           abs_signed += sgn * mov;
         }
-      }
-    }
-    __syncwarp();
-    int32_t* orow_base = a.hist_out + S.hist_off;
-    for (int q = lane; q < 3 * n_M; q += 32) {
-      const int v = s_acc[q];
-      if (v) {
-        const int dd = q / n_M, kc = q - dd * n_M;
-        atomicAdd(orow_base + (size_t)(i - 1 + dd) * n_M + kc, v);
       }
     }
     __syncwarp();
@@ -693,7 +689,7 @@ __global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a)
 __global__ void k_b_set_step(DevHeader* hdr, uint32_t step) { hdr->step = step; }
 
 // ---------------------------------------------------------------- host driver
-size_t b_step_smem(int NM) { return sizeof(int) * (size_t)kBStepWarps * (5 * NM + 1); }
+size_t b_step_smem(int NM) { return sizeof(int) * (size_t)kBStepWarps * (2 * NM + 1); }
 
 int b_step_grid(int NM) {
   int per_sm = 0;

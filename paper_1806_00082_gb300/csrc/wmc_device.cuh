@@ -77,10 +77,13 @@ __device__ __forceinline__ double scaled_total(long long total, int s) {
 // integer additions per lane; lanes write contiguous runs of the row-major CDF.
 // Column k has momentum residue (r0 + k) mod Q (r0 = -n_M/2 mod Q); xres(rr)
 // returns max(V_W, 0) at residue rr, stepped incrementally along a lane's run.
+// zero_rows: also write the all-zero CDF of a row without positive entries
+// (the simulation step never reads it: such a row has gamma = 0, so no pair is
+// drawn from it).
 template <class XRes>
 __device__ __forceinline__ void warp_row_cdf(XRes xres, int Q, int r0, int n_M, int log2_nM, int lane,
                                              long long* __restrict__ out, double& gamma_out, int& scale_out,
-                                             long long& total_out) {
+                                             long long& total_out, bool zero_rows = true) {
   const int E = (n_M + 31) >> 5;
   const int k0 = min(lane * E, n_M), k1 = min(k0 + E, n_M);
   const int rr0 = (r0 + k0) % Q;
@@ -91,7 +94,7 @@ __device__ __forceinline__ void warp_row_cdf(XRes xres, int Q, int r0, int n_M, 
   }
   mx = __reduce_max_sync(0xffffffffu, mx);
   if (mx == 0u) {
-    if (out)
+    if (out && zero_rows)
       for (int k = k0; k < k1; ++k) out[k] = 0;
     gamma_out = 0.0;
     scale_out = 0;

@@ -160,7 +160,8 @@ __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2
   double g;
   int sc;
   long long tot;
-  warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, cdf ? cdf + (size_t)row * n_M : nullptr, g, sc, tot);
+  warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, cdf ? cdf + (size_t)row * n_M : nullptr, g, sc, tot,
+               gthr == nullptr);  // the step's rows (with thresholds) skip all-zero CDFs
   if (lane == 0) {
     gamma[row] = g;
     if (scale) scale[row] = sc;
@@ -355,13 +356,19 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
                                : 0.f;
       }
     }
+    bool nz = false;  // rows over a flat potential are exactly zero: skip the sums
+#pragma unroll
+    for (int g = 0; g < R; ++g)
+#pragma unroll
+      for (int q = 0; q < C; ++q) nz |= s_dv[g * 32 * C + lane + 32 * q] != 0.f;
+    nz = __any_sync(0xffffffffu, nz);
     __syncwarp();
     float sacc[R][C], eacc[R][C];
 #pragma unroll
     for (int g = 0; g < R; ++g)
 #pragma unroll
       for (int cc = 0; cc < C; ++cc) sacc[g][cc] = eacc[g][cc] = 0.f;
-    for (int m0 = 1; m0 <= h - 1; m0 += 32) {   // chunks of 32 window terms
+    for (int m0 = 1; nz && m0 <= h - 1; m0 += 32) {   // chunks of 32 window terms
       float part[R][C];
 #pragma unroll
       for (int g = 0; g < R; ++g)
@@ -416,7 +423,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
         double gm;
         int sc;
         long long tot;
-        warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, cdf + (size_t)row * n_M, gm, sc, tot);
+        warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, cdf + (size_t)row * n_M, gm, sc, tot, false);
         if (lane == 0) {
           gamma[row] = gm;
           const unsigned long long thr = gm > 0.0 ? event_threshold(gm, dt, flags) : 0ull;
