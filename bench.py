@@ -315,6 +315,9 @@ def end_to_end(wmc, torch, p, V, ws, stream, h0, t0, n=10):
     a = torch.empty_like(h0)
     b = torch.empty_like(h0)
     with torch.cuda.stream(stream):
+        # warm-up call: builds the cached one-step graph outside the timed region
+        a.copy_(host_in, non_blocking=True)
+        wmc.run(p, V, a, b, t0, 1, ws)
         wmc.reset_counters(p, ws)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)

@@ -196,7 +196,51 @@ struct GraphCache {
   int device;
   cudaGraphExec_t exec = nullptr;
 };
-static GraphCache g_graph;
+static GraphCache g_graph;   // the step pair a -> b -> a
+static GraphCache g_graph1;  // one step a -> b and the copy back to a (odd step counts)
+
+// Launches the cached graph `gc` for these arguments, capturing `body` into it
+// first if the cache holds another configuration.
+template <class Body>
+static wmc_status launch_cached(GraphCache& gc, const wmc_params* p, const float* V, const int32_t* a,
+                                const int32_t* b, const void* ws, wmc_precision prec, cudaStream_t s, int launches,
+                                Body body) {
+  std::lock_guard<std::mutex> lock(gc.mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const bool hit = gc.valid && memcmp(&gc.p, p, sizeof(wmc_params)) == 0 && gc.V == V && gc.a == a && gc.b == b &&
+                   gc.ws == ws && gc.prec == (int)prec && gc.stream == s && gc.device == dev;
+  if (!hit) {
+    if (gc.exec) {
+      cudaGraphExecDestroy(gc.exec);
+      gc.exec = nullptr;
+    }
+    gc.valid = false;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WMC_ERR_CUDA;
+    const wmc_status st = body();
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != WMC_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return st != WMC_OK ? st : WMC_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return WMC_ERR_CUDA;
+    gc.valid = true;
+    gc.p = *p;
+    gc.V = V;
+    gc.a = a;
+    gc.b = b;
+    gc.ws = ws;
+    gc.prec = (int)prec;
+    gc.stream = s;
+    gc.device = dev;
+  }
+  for (int q = 0; q < launches; ++q)
+    if (cudaGraphLaunch(gc.exec, s) != cudaSuccess) return WMC_ERR_CUDA;
+  return WMC_OK;
+}
 
 }  // namespace wmc
 
@@ -336,57 +380,34 @@ wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t
   k_set_step<<<1, 1, 0, s>>>(v.hdr, t_first - 1u);
   if (cudaGetLastError() != cudaSuccess) return WMC_ERR_CUDA;
   const int pairs = n_steps / 2;
-  if (use_graph && s != nullptr && pairs > 0) {
-    std::lock_guard<std::mutex> lock(g_graph.mu);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const bool hit = g_graph.valid && memcmp(&g_graph.p, p, sizeof(wmc_params)) == 0 && g_graph.V == V &&
-                     g_graph.a == hist_a && g_graph.b == hist_b && g_graph.ws == ws && g_graph.prec == (int)prec &&
-                     g_graph.stream == s && g_graph.device == dev;
-    if (!hit) {
-      if (g_graph.exec) {
-        cudaGraphExecDestroy(g_graph.exec);
-        g_graph.exec = nullptr;
-      }
-      g_graph.valid = false;
-      cudaGraph_t graph = nullptr;
-      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WMC_ERR_CUDA;
-      wmc_status st = one_step(*p, v, V, hist_a, hist_b, prec, 1, 0, s);
-      if (st == WMC_OK) st = one_step(*p, v, V, hist_b, hist_a, prec, 1, 0, s);
-      cudaError_t e = cudaStreamEndCapture(s, &graph);
-      if (st != WMC_OK || e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return WMC_ERR_CUDA;
-      }
-      e = cudaGraphInstantiate(&g_graph.exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return WMC_ERR_CUDA;
-      g_graph.valid = true;
-      g_graph.p = *p;
-      g_graph.V = V;
-      g_graph.a = hist_a;
-      g_graph.b = hist_b;
-      g_graph.ws = ws;
-      g_graph.prec = (int)prec;
-      g_graph.stream = s;
-      g_graph.device = dev;
-    }
-    for (int q = 0; q < pairs; ++q)
-      if (cudaGraphLaunch(g_graph.exec, s) != cudaSuccess) return WMC_ERR_CUDA;
-  } else {
-    for (int q = 0; q < pairs; ++q) {
-      wmc_status st = one_step(*p, v, V, hist_a, hist_b, prec, 1, 0, s);
-      if (st == WMC_OK) st = one_step(*p, v, V, hist_b, hist_a, prec, 1, 0, s);
+  const size_t state_bytes = sizeof(int32_t) * (size_t)p->n_x * (size_t)p->n_M;
+  // the odd last step: a -> b, then the state copied back to a
+  auto odd_step = [&]() -> wmc_status {
+    const wmc_status st = one_step(*p, v, V, hist_a, hist_b, prec, 1, 0, s);
+    if (st != WMC_OK) return st;
+    return cudaMemcpyAsync(hist_a, hist_b, state_bytes, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? WMC_OK
+                                                                                                   : WMC_ERR_CUDA;
+  };
+  if (use_graph && s != nullptr) {
+    if (pairs > 0) {
+      const wmc_status st = launch_cached(g_graph, p, V, hist_a, hist_b, ws, prec, s, pairs, [&]() -> wmc_status {
+        const wmc_status st1 = one_step(*p, v, V, hist_a, hist_b, prec, 1, 0, s);
+        return st1 == WMC_OK ? one_step(*p, v, V, hist_b, hist_a, prec, 1, 0, s) : st1;
+      });
       if (st != WMC_OK) return st;
     }
+    if (n_steps & 1) {
+      const wmc_status st = launch_cached(g_graph1, p, V, hist_a, hist_b, ws, prec, s, 1, odd_step);
+      if (st != WMC_OK) return st;
+    }
+    return WMC_OK;
   }
-  if (n_steps & 1) {
+  for (int q = 0; q < pairs; ++q) {
     wmc_status st = one_step(*p, v, V, hist_a, hist_b, prec, 1, 0, s);
+    if (st == WMC_OK) st = one_step(*p, v, V, hist_b, hist_a, prec, 1, 0, s);
     if (st != WMC_OK) return st;
-    if (cudaMemcpyAsync(hist_a, hist_b, sizeof(int32_t) * (size_t)p->n_x * (size_t)p->n_M,
-                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return WMC_ERR_CUDA;
   }
+  if (n_steps & 1) return odd_step();
   return WMC_OK;
 }
 

@@ -333,6 +333,21 @@ def test_odd_step_count_and_continuation(wmc):
     b1, _ = gpu_run(wmc, torch, p, V, h0, 1, 3)
     b2, _ = gpu_run(wmc, torch, p, V, b1, 4, 4)
     np.testing.assert_array_equal(a, b2)
+    a_direct, _ = gpu_run(wmc, torch, p, V, h0, 1, 7, use_graph=False)
+    np.testing.assert_array_equal(a, a_direct)
+    # seven one-step calls on one workspace (the cached odd-step graph is reused
+    # with a new first step each time)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    Vd = torch.from_numpy(V).cuda()
+    x = torch.from_numpy(h0).cuda()
+    y = torch.empty_like(x)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for t in range(1, 8):
+            wmc.run(p, Vd, x, y, t, 1, ws, wmc.FP32, True)
+    s.synchronize()
+    np.testing.assert_array_equal(x.cpu().numpy(), a)
 
 
 # --------------------------------------------------------------------------- rebuild, density, flags
