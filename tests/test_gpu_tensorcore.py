@@ -148,3 +148,31 @@ def test_tensorcore_implicit_rows_many_potentials(wmc, form):
         err = _sampled_err(got[b * wl.n_x:(b + 1) * wl.n_x], wl, Vs[b], cells, 120, b)
         assert err <= TOL[form], (form, b, err)
     assert wmc.get_counters(p, ws)["flags"] == 0
+
+
+_REF = {}  # FP64 reference rows shared by the parametrised forms
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16", "fp16_split"])
+def test_tensorcore_wide_window(wmc, form):
+    """A window wider than the resident-A forms hold (Q = n_M = 2048): the
+    per-tile kernel with streamed A, on a ragged list of cells around the
+    barriers, against the FP64 oracle."""
+    wl = wi.DOUBLE_BARRIER_16384.replace(Q=2048, n_M=2048)
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    cells = np.concatenate([np.arange(8192 - 40, 8192 + 40), [0, 1, wl.n_x - 1, 4000, 12000]]).astype(np.int32)
+    got = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), torch.from_numpy(cells).cuda(), ws,
+                          prec=wmc.PRECISIONS[form]).cpu().numpy()
+    if "wide" not in _REF:
+        _REF["wide"] = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, cells)[:, wl.Q // 2:]
+    ref = _REF["wide"]
+    assert np.all(np.isfinite(got))
+    # the split form accumulates the hi x hi products in FP32 over two halves of
+    # the 1023-term window (no compensation inside the tensor core): about
+    # twice its Q = 1024 error, measured 2.1e-6
+    tol = 3e-6 if form == "fp16_split" else TOL[form]
+    assert normwise(got, ref) <= tol, (form, normwise(got, ref))
+    assert wmc.get_counters(p, ws)["flags"] == 0
