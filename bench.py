@@ -349,11 +349,11 @@ def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
     h = w.Q // 2
     flops = 2.0 * w.n_x * (h - 1) ** 2
     # normwise error bounds asserted by tests/test_gpu_parity.py and tests/test_gpu_tensorcore.py
-    bounds = {"fp32": 1e-6, "bf16": 1.5e-2, "fp16": 1e-3, "fp16_split": 1e-6}
+    bounds = {"fp32": 1e-6, "bf16": 1.5e-2, "fp16": 1e-3, "fp16_split": 1e-6, "tf32x3": 2.5e-6}
     res = {}
     with torch.cuda.stream(stream):
         wmc.init(p, ws)
-        for form in ("fp32", "bf16", "fp16", "fp16_split"):
+        for form in ("fp32", "bf16", "fp16", "fp16_split", "tf32x3"):
             prec = wmc.PRECISIONS[form]
             for _ in range(3):
                 wmc.kernel_eval(p, V, occ, ws, prec=prec, out=out)
@@ -372,11 +372,16 @@ def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
             if form == "fp32":
                 r["bound"] = "fp32 pipe (SIMT)"
             else:
-                issued = flops * (3 if form == "fp16_split" else 1)
-                peak = peaks["bf16_tflops"] * 1e12
+                issued = flops * (3 if form in ("fp16_split", "tf32x3") else 1)
+                if form == "tf32x3":  # TF32 pipe: the BF16 peak x the nominal ratio 1.1 / 2.25 PFLOP/s
+                    peak = peaks["bf16_tflops"] * 1e12 * (1.1 / 2.25)
+                    psrc = f"{src} bf16 dense x 1.1/2.25 (nominal tf32/bf16)"
+                else:
+                    peak = peaks["bf16_tflops"] * 1e12
+                    psrc = f"{src} bf16 dense (fp16 same rate)"
                 r["roofline"] = {"bound": "tensor", "achieved": issued / sec / 1e12, "peak": peak / 1e12,
                                  "unit": "TFLOP/s", "frac": issued / sec / peak, "traffic": None,
-                                 "peak_source": f"{src} bf16 dense (fp16 same rate)"}
+                                 "peak_source": psrc}
             res[form] = r
     return {"workload": f"{w.name}, all {w.n_x} cells, n_M = {w.n_M}", "forms": res}
 

@@ -339,7 +339,8 @@ wmc_status wmc_potential_tanh_vjp(const wmc_params* p, const float* theta, int32
 wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_pot, wmc_precision prec, float* VWh,
                                 void* ws, wmc_stream_t stream) {
   if (!params_ok(p) || !V || !VWh || !ws || n_pot < 0) return WMC_ERR_ARG;
-  if (prec != WMC_FP32 && prec != WMC_BF16 && prec != WMC_FP16 && prec != WMC_FP16_SPLIT) return WMC_ERR_UNSUPPORTED;
+  if (prec != WMC_FP32 && prec != WMC_BF16 && prec != WMC_FP16 && prec != WMC_FP16_SPLIT && prec != WMC_TF32X3)
+    return WMC_ERR_UNSUPPORTED;
   const long long rows = (long long)n_pot * p->n_x;
   if (rows == 0) return WMC_OK;
   if (rows > 0x7fffffffll) return WMC_ERR_ARG;

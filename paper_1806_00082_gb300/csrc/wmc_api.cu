@@ -110,7 +110,7 @@ __global__ void k_reset_counters(DevHeader* hdr) {
 static wmc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WMC_OK : WMC_ERR_CUDA; }
 
 static bool prec_supported(wmc_precision prec) {
-  return prec == WMC_FP32 || prec == WMC_BF16 || prec == WMC_FP16 || prec == WMC_FP16_SPLIT;
+  return prec == WMC_FP32 || prec == WMC_BF16 || prec == WMC_FP16 || prec == WMC_FP16_SPLIT || prec == WMC_TF32X3;
 }
 
 // Kernel rows, CDFs and thresholds of the occupied list in the workspace:

@@ -124,6 +124,24 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       : "memory");
 }
 
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// x rounded to TF32 (nearest, ties away from zero), as FP32 bits with the low
+// 13 mantissa bits zero.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -227,6 +245,32 @@ __global__ void k_init_tc_images(int Q, int KB, int NT, uint16_t* __restrict__ i
     const __half hi = __float2half_rn(v);
     img_hi[off] = __half_as_ushort(hi);
     img_lo[off] = __half_as_ushort(__float2half_rn((v - __half2float(hi)) * 2048.f));
+  }
+}
+
+// The same sine matrix as TF32 hi/lo pairs (hi = tf32(v), lo = tf32(v - hi)),
+// in 128 x 32 blocks of the swizzled layout (four 4-byte values per chunk).
+__global__ void k_init_tc_images32(int Q, int KB32, int NT, uint32_t* __restrict__ img_hi,
+                                   uint32_t* __restrict__ img_lo) {
+  const int h = Q / 2;
+  const long long total = (long long)NT * KB32 * TN * 32;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int blk = (int)(q / (TN * 32));
+    const int e = (int)(q % (TN * 32));
+    const int n = e / 32, k = e % 32;
+    const int nt = blk / KB32, kb = blk % KB32;
+    const int m = kb * 32 + k + 1, r = nt * TN + n;
+    float v = 0.f;
+    if (m <= h - 1 && r < h) {
+      const long long t = ((long long)m * r) % Q;
+      v = __double2float_rn(sinpi(2.0 * (double)t / (double)Q));
+    }
+    // chunk k / 4 of row n, value k % 4 in it
+    const size_t off = (size_t)blk * (kTileBytes / 4) + (core_offset(n, (k >> 2) * 8) >> 2) + (k & 3);
+    const uint32_t hi = to_tf32(v);
+    img_hi[off] = hi;
+    img_lo[off] = to_tf32(v - __uint_as_float(hi));
   }
 }
 
@@ -784,37 +828,53 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
   }
 }
 
-// ---------------------------------------------------------------- warp-specialised split form
+// ---------------------------------------------------------------- warp-specialised split forms
 // FP16 hi/lo split: A = A_hi + 2^-11 A_lo, B = B_hi + 2^-11 B_lo, and
 //   A B ~ A_hi B_hi + 2^-11 (A_hi B_lo + A_lo B_hi)
-// (the A_lo B_lo term is below FP32 rounding).  One CTA per 128 rows and one
-// column tile.  K runs in two passes, [0, half) and [half, KB) blocks, each
-// into its own FP32 accumulator of A_hi B_hi (as the K halves of the other
-// forms), with the cross terms in a third; the half-K A_hi / A_lo blocks of a
-// pass stay in shared memory while B_hi / B_lo stream through a 2-stage ring.
-// Roles as in k_kernel_eval_tc_ws; the builders start the second pass once
-// the MMAs of the first have released A (a_free).
+// (the A_lo B_lo term is below FP32 rounding).  3xTF32 (TF32 = true) is the
+// same with TF32 parts and no scaling (TF32 keeps the FP32 exponent range):
+// A = A_hi + A_lo with A_hi = tf32(A), A_lo = tf32(A - A_hi).  A 16 KB operand
+// block holds 128 rows x 64 FP16 or x 32 TF32 values.  One CTA per 128 rows
+// and one column tile.  K runs in passes of `bp` blocks (the A_hi / A_lo
+// blocks of a pass stay in shared memory while B_hi / B_lo stream through a
+// 2-stage ring); the first half of the passes accumulates A_hi B_hi into one
+// FP32 accumulator and the second half into another (the K halves of the
+// other forms), the cross terms go to a third.  Roles as in
+// k_kernel_eval_tc_ws; the builders start a pass once the MMAs of the previous
+// one have released A (a_free).
 constexpr int kSpStages = 2;
-constexpr int kSpMaxHalf = 4;  // half-K blocks resident: KB <= 8 (Q <= 1026)
+constexpr int kSpMaxHalf = 4;  // blocks resident per pass
 
-__host__ __device__ constexpr size_t ws_split_smem_bytes(int KB, int h) {
-  return kSmemAlignPad + (size_t)2 * ((KB + 1) / 2) * kTileBytes + (size_t)kSpStages * 2 * kTileBytes +
+// blocks per pass: half of K for FP16 (one or two passes), 4 for TF32
+__host__ __device__ constexpr int split_pass_blocks(int KB, bool tf32) {
+  return tf32 ? 4 : ((KB + 1) / 2 < 4 ? (KB + 1) / 2 : 4);
+}
+
+__host__ __device__ constexpr size_t ws_split_smem_bytes(int KB, int h, bool tf32 = false) {
+  return kSmemAlignPad + (size_t)2 * split_pass_blocks(KB, tf32) * kTileBytes + (size_t)kSpStages * 2 * kTileBytes +
          sizeof(float) * (size_t)((TM + 2 * h) > (kWsBuilders / 32) * kWsStageFloats
                                       ? (TM + 2 * h)
                                       : (kWsBuilders / 32) * kWsStageFloats);
 }
 
+template <bool TF32>
 __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
     const float* __restrict__ V, int n_x, int bc, int Q, const int* __restrict__ occ,
-    const int* __restrict__ n_occ_dev, int n_occ_host, const uint16_t* __restrict__ img_hi,
-    const uint16_t* __restrict__ img_lo, int KB, float c, float* __restrict__ VWh, unsigned int* __restrict__ flags) {
-  constexpr uint32_t idesc = idesc_f16(0u);  // FP16 x FP16 -> FP32
+    const int* __restrict__ n_occ_dev, int n_occ_host, const void* __restrict__ img_hi_v,
+    const void* __restrict__ img_lo_v, int KB, float c, float* __restrict__ VWh, unsigned int* __restrict__ flags) {
+  // FP16 x FP16 -> FP32 (format 0) or TF32 x TF32 -> FP32 (format 2)
+  constexpr uint32_t idesc = idesc_f16(TF32 ? 2u : 0u);
+  constexpr int KBLK = TF32 ? 32 : TK;   // K values per operand block
+  constexpr int EPC = KBLK / 8;          // values per 16-byte chunk
+  constexpr float kLoScale = TF32 ? 1.f : 0x1p-11f;
+  const uint8_t* img_hi = static_cast<const uint8_t*>(img_hi_v);
+  const uint8_t* img_lo = static_cast<const uint8_t*>(img_lo_v);
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = align_smem(smem_raw);
-  const int half = (KB + 1) / 2;
-  uint8_t* sAh = smem;                                        // half blocks of A_hi
-  uint8_t* sAl = smem + (size_t)half * kTileBytes;             // half blocks of A_lo
-  uint8_t* sB = smem + (size_t)2 * half * kTileBytes;          // stages of (B_hi, B_lo)
+  const int bp = split_pass_blocks(KB, TF32);                 // blocks per pass
+  uint8_t* sAh = smem;                                        // bp blocks of A_hi
+  uint8_t* sAl = smem + (size_t)bp * kTileBytes;               // bp blocks of A_lo
+  uint8_t* sB = smem + (size_t)2 * bp * kTileBytes;            // stages of (B_hi, B_lo)
   float* sV = reinterpret_cast<float*>(sB + (size_t)kSpStages * 2 * kTileBytes);  // shared with the staging
   __shared__ __align__(8) uint64_t a_ready[kSpMaxHalf];
   __shared__ __align__(8) uint64_t b_full[kSpStages], b_empty[kSpStages];
@@ -828,7 +888,8 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
   if (row0 >= n_rows) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nt = blockIdx.y;
-  const int n_pass = KB > half ? 2 : 1;
+  const int n_pass = (KB + bp - 1) / bp;
+  const int pass_m1 = (n_pass + 1) / 2;  // first pass accumulating into the second hi x hi accumulator
   const int n_tiles = KB;  // B tiles streamed: one per K block
 
   if (warp == 0) tmem_alloc(&tmem_slot, 512u);
@@ -862,7 +923,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
           break;
         }
         uint8_t* dst = sB + (size_t)st * 2 * kTileBytes;
-        const size_t off = ((size_t)nt * KB + t) * (kTileBytes / 2);
+        const size_t off = ((size_t)nt * KB + t) * kTileBytes;  // bytes
         mbar_expect_tx(&b_full[st], 2 * kTileBytes);
         bulk_g2s(dst, img_hi + off, kTileBytes, &b_full[st]);
         bulk_g2s(dst + kTileBytes, img_lo + off, kTileBytes, &b_full[st]);
@@ -876,8 +937,8 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
     // ---- MMA issuer
     if (lane == 0) {
       for (int pass = 0; pass < n_pass && !s_abort; ++pass) {
-        const int kb0 = pass * half, kb1 = pass ? KB : half;
-        const uint32_t acc_m = pass ? acc_m1 : acc_m0;
+        const int kb0 = pass * bp, kb1 = min(KB, kb0 + bp);
+        const uint32_t acc_m = pass >= pass_m1 ? acc_m1 : acc_m0;
         for (int kb = kb0; kb < kb1; ++kb) {
           const int kbl = kb - kb0, st = kb % kSpStages;
           if (!mbar_wait(&a_ready[kbl], (uint32_t)(pass & 1)) ||
@@ -893,9 +954,16 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
           for (int s4 = 0; s4 < TK / 16; ++s4) {
             const uint32_t o = s4 * kKStepBytes;
             const uint64_t dah = smem_desc(ah + o), dbh = smem_desc(bh + o);
-            mma_f16(acc_m, dah, dbh, idesc, (kb == kb0 && s4 == 0) ? 0u : 1u);
-            mma_f16(acc_x, dah, smem_desc(bl + o), idesc, (kb == 0 && s4 == 0) ? 0u : 1u);
-            mma_f16(acc_x, smem_desc(al + o), dbh, idesc, 1u);
+            const bool first_m = kb == kb0 && s4 == 0 && (pass == 0 || pass == pass_m1);
+            if (TF32) {
+              mma_tf32(acc_m, dah, dbh, idesc, first_m ? 0u : 1u);
+              mma_tf32(acc_x, dah, smem_desc(bl + o), idesc, (kb == 0 && s4 == 0) ? 0u : 1u);
+              mma_tf32(acc_x, smem_desc(al + o), dbh, idesc, 1u);
+            } else {
+              mma_f16(acc_m, dah, dbh, idesc, first_m ? 0u : 1u);
+              mma_f16(acc_x, dah, smem_desc(bl + o), idesc, (kb == 0 && s4 == 0) ? 0u : 1u);
+              mma_f16(acc_x, smem_desc(al + o), dbh, idesc, 1u);
+            }
           }
           mma_commit(&b_empty[st]);
         }
@@ -946,10 +1014,10 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
     }
     const bool fast = contig && (h & 3) == 0;
     for (int pass = 0; pass < n_pass; ++pass) {
-      const int kb0 = pass * half, kb1 = pass ? KB : half, cnt = kb1 - kb0;
+      const int kb0 = pass * bp, kb1 = min(KB, kb0 + bp), cnt = kb1 - kb0;
       if (pass > 0) {
-        // the first pass's MMAs must have read A before it is overwritten
-        const bool ok = __all_sync(0xffffffffu, !s_abort && mbar_wait(&a_free, 0u));
+        // the previous pass's MMAs must have read A before it is overwritten
+        const bool ok = __all_sync(0xffffffffu, !s_abort && mbar_wait(&a_free, (uint32_t)((pass - 1) & 1)));
         if (!ok) {
           if (lane == 0) atomicOr(flags, WMC_FLAG_TIMEOUT);
           s_abort = 1;
@@ -961,14 +1029,16 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
 #pragma unroll 1
       for (int kbl = par; kbl < cnt; kbl += 2) {
         const int kb = kb0 + kbl;
-        const int m0 = kb * TK + k8 * 8 + 1;
-        float dv[4][8];
-        if (fast && m0 + 7 <= h - 1) {
-          float P[12], N[12];
+        const int m0 = kb * KBLK + k8 * EPC + 1;
+        float dv[4][EPC];
+        if (fast && m0 + EPC - 1 <= h - 1) {
+          // P[j] = V at offset m0 - 1 + j right of row 4 rg, N[j] = V at offset m0 + EPC - 1 - j left of it
+          constexpr int NW = EPC + 4;
+          float P[NW], N[NW];
           const float* pp = sV + 4 * rg + h + m0 - 1;
-          const float* pn = sV + 4 * rg + h - m0 - 7;
+          const float* pn = sV + 4 * rg + h - m0 - (EPC - 1);
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
+          for (int q = 0; q < NW / 4; ++q) {
             const float4 a = *reinterpret_cast<const float4*>(pp + 4 * q);
             const float4 b = *reinterpret_cast<const float4*>(pn + 4 * q);
             P[4 * q] = a.x, P[4 * q + 1] = a.y, P[4 * q + 2] = a.z, P[4 * q + 3] = a.w;
@@ -977,12 +1047,12 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
 #pragma unroll
           for (int d = 0; d < 4; ++d)
 #pragma unroll
-            for (int e = 0; e < 8; ++e) dv[d][e] = __fsub_rn(P[d + e + 1], N[d - e + 7]);
+            for (int e = 0; e < EPC; ++e) dv[d][e] = __fsub_rn(P[d + e + 1], N[d - e + EPC - 1]);
         } else {
 #pragma unroll
           for (int d = 0; d < 4; ++d)
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
+            for (int e = 0; e < EPC; ++e) {
               const int m = m0 + e;
               dv[d][e] = 0.f;
               if (m <= h - 1) {
@@ -997,14 +1067,22 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
           uint32_t hw[4], lw[4];
+          if (TF32) {
 #pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            const uint16_t h0 = to_bits(dv[d][e], WMC_FP16), h1 = to_bits(dv[d][e + 1], WMC_FP16);
-            const uint16_t l0 = to_bits(__fmul_rn(__fsub_rn(dv[d][e], from_bits(h0, WMC_FP16)), 2048.f), WMC_FP16);
-            const uint16_t l1 =
-                to_bits(__fmul_rn(__fsub_rn(dv[d][e + 1], from_bits(h1, WMC_FP16)), 2048.f), WMC_FP16);
-            hw[e / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-            lw[e / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            for (int e = 0; e < 4; ++e) {
+              hw[e] = to_tf32(dv[d][e]);
+              lw[e] = to_tf32(__fsub_rn(dv[d][e], __uint_as_float(hw[e])));
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+              const uint16_t h0 = to_bits(dv[d][e], WMC_FP16), h1 = to_bits(dv[d][e + 1], WMC_FP16);
+              const uint16_t l0 = to_bits(__fmul_rn(__fsub_rn(dv[d][e], from_bits(h0, WMC_FP16)), 2048.f), WMC_FP16);
+              const uint16_t l1 =
+                  to_bits(__fmul_rn(__fsub_rn(dv[d][e + 1], from_bits(h1, WMC_FP16)), 2048.f), WMC_FP16);
+              hw[e / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+              lw[e / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
           }
           wh[d] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           wl[d] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -1022,7 +1100,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kbl])) : "memory");
       }
     }
-    // epilogue: v = c ((hi-hi pass 0 + hi-hi pass 1) + 2^-11 cross)
+    // epilogue: v = c ((hi-hi first half + hi-hi second half) + scale x cross)
     const int quad = warp & 3, cq = warp >> 2;
     float* stg = sV + warp * kWsStageFloats;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
@@ -1045,7 +1123,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
         for (int q = 0; q < 16; ++q) {
           float v = a[q];
           if (n_pass > 1) v = __fadd_rn(v, b[q]);
-          a[q] = __fmul_rn(c, __fadd_rn(v, __fmul_rn(x[q], 0x1p-11f)));
+          a[q] = __fmul_rn(c, __fadd_rn(v, __fmul_rn(x[q], kLoScale)));
         }
 #pragma unroll
         for (int g = 0; g < 4; ++g)
@@ -1083,8 +1161,9 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
 
 // ---------------------------------------------------------------- host side
 struct TcImages {
-  int KB, NT;
-  size_t bytes_per_image;  // NT * KB * kTileBytes
+  int KB, NT, KB32;          // 16-bit K blocks (64 values), column tiles, TF32 K blocks (32 values)
+  size_t bytes_per_image;    // NT * KB * kTileBytes (BF16, FP16 hi, FP16 lo)
+  size_t bytes_per_image32;  // NT * KB32 * kTileBytes (TF32 hi, TF32 lo)
 };
 
 static int g_h(const wmc_params& p) { return p.Q / 2; }
@@ -1095,17 +1174,25 @@ static TcImages tc_geometry(const wmc_params& p) {
   g.KB = (h - 1 + TK - 1) / TK;
   if (g.KB < 1) g.KB = 1;
   g.NT = (h + TN - 1) / TN;
+  g.KB32 = (h - 1 + 31) / 32;
+  if (g.KB32 < 1) g.KB32 = 1;
   g.bytes_per_image = (size_t)g.NT * g.KB * kTileBytes;
+  g.bytes_per_image32 = (size_t)g.NT * g.KB32 * kTileBytes;
   return g;
 }
 
-size_t tc_images_bytes(const wmc_params& p) { return 3 * tc_geometry(p).bytes_per_image; }
+size_t tc_images_bytes(const wmc_params& p) {
+  const TcImages g = tc_geometry(p);
+  return 3 * g.bytes_per_image + 2 * g.bytes_per_image32;
+}
 
 cudaError_t launch_init_tc_images(const wmc_params& p, void* images, cudaStream_t s) {
   const TcImages g = tc_geometry(p);
   uint16_t* base = static_cast<uint16_t*>(images);
   const size_t n16 = g.bytes_per_image / 2;
   k_init_tc_images<<<256, 256, 0, s>>>(p.Q, g.KB, g.NT, base, base + n16, base + 2 * n16);
+  uint32_t* b32 = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(images) + 3 * g.bytes_per_image);
+  k_init_tc_images32<<<256, 256, 0, s>>>(p.Q, g.KB32, g.NT, b32, b32 + g.bytes_per_image32 / 4);
   return cudaGetLastError();
 }
 
@@ -1166,13 +1253,19 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
     cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_kernel_eval_tc<WMC_FP16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
                                                      base + n16, nullptr, g.KB, c, VWh, flags);
-  } else if (prec == WMC_FP16_SPLIT && (g.KB + 1) / 2 <= kSpMaxHalf &&
-             ws_split_smem_bytes(g.KB, g_h(p)) <= 226 * 1024) {
+  } else if (prec == WMC_FP16_SPLIT && ws_split_smem_bytes(g.KB, g_h(p)) <= 226 * 1024) {
     const size_t sm = ws_split_smem_bytes(g.KB, g_h(p));
-    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_kernel_eval_tc_ws_split<<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
-                                                           n_occ_host, base + n16, base + 2 * n16, g.KB, c, VWh,
-                                                           flags);
+    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_kernel_eval_tc_ws_split<false><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                                  n_occ_host, base + n16, base + 2 * n16, g.KB, c,
+                                                                  VWh, flags);
+  } else if (prec == WMC_TF32X3 && ws_split_smem_bytes(g.KB32, g_h(p), true) <= 226 * 1024) {
+    const size_t sm = ws_split_smem_bytes(g.KB32, g_h(p), true);
+    const uint8_t* b32 = reinterpret_cast<const uint8_t*>(images) + 3 * g.bytes_per_image;
+    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_kernel_eval_tc_ws_split<true><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                                 n_occ_host, b32, b32 + g.bytes_per_image32,
+                                                                 g.KB32, c, VWh, flags);
   } else if (prec == WMC_FP16_SPLIT) {
     const size_t sm = tc_smem_bytes(true, g_h(p));
     cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
