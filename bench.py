@@ -151,6 +151,20 @@ def reference_arm(args, w):
 
 
 # ---------------------------------------------------------------- native arm
+def reduce_over_ranks(ms, particle_steps, device=None):
+    """(max over ranks of the timed milliseconds, sum over ranks of the
+    particle-steps) -- the whole-job time is the slowest replica's.  A single
+    process returns its own values."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(ms), float(particle_steps)
+    tt = torch.tensor([ms, particle_steps], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(tt[1])
+
+
 def native_arm(args, w):
     import torch
     from paper_1806_00082_gb300 import build, wmc
@@ -202,16 +216,7 @@ def native_arm(args, w):
             torch.distributed.barrier()
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
         c = wmc.get_counters(p, ws)
-    ps_local = float(c["particle_steps"])
-    ms_max = ms
-    if world > 1:
-        tt = torch.tensor([ms, ps_local], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.SUM)
-        ms_max, ps_total = float(mx[0]), float(tt[1])
-    else:
-        ps_total = ps_local
+    ms_max, ps_total = reduce_over_ranks(ms, float(c["particle_steps"]), dev)
     value = ps_total / (ms_max * 1e-3)
 
     # ---- dominant kernel: the particle step, timed alone with events on its stream
@@ -240,7 +245,8 @@ def native_arm(args, w):
                    "dt_fs": w.dt_s / 1e-15, "kernel": "fp32 (compensated)",
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed iterations (2 steps each)"},
         "clocks": clk.summary(),
-        "gpu_launches": 5 * steps + n_iter,
+        # per step: k_rows, k_plan, k_kernel_rows_small, k_step; per wmc_run call: k_set_step
+        "gpu_launches": 4 * steps + n_iter,
         "e2e": e2e,
         "roofline": roof,
         "cpu_baseline": cpu,
