@@ -132,6 +132,16 @@ wmc_status wmc_init(const wmc_params* p, void* ws, size_t ws_bytes, wmc_stream_t
 /* Zeroes the counters and flags of an initialised workspace. */
 wmc_status wmc_reset_counters(const wmc_params* p, void* ws, wmc_stream_t stream);
 
+/* Failure-detection check of the device wait pattern the tensor-core kernels
+ * use: one device thread waits until the 32-bit word *signal [dev] is non-zero
+ * or max_cycles SM clock cycles have passed; if it gives up it sets
+ * WMC_FLAG_TIMEOUT in the workspace flags (read with wmc_get_counters, cleared
+ * by wmc_reset_counters) and returns, so the context stays usable.  The
+ * library writes nothing else; max_cycles 0 .. 2^34 (about eight seconds).
+ * Stream-ordered. */
+wmc_status wmc_check_wait(const wmc_params* p, const uint32_t* signal, uint64_t max_cycles, void* ws,
+                          wmc_stream_t stream);
+
 /* Reads the counters (synchronises the stream).  out [host]. */
 wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* out, wmc_stream_t stream);
 

@@ -107,6 +107,21 @@ __global__ void k_reset_counters(DevHeader* hdr) {
   hdr->flags = 0;
 }
 
+// One thread waits for *signal != 0 for at most max_cycles clock cycles (the
+// bounded-wait pattern of the tensor-core kernels); giving up sets the
+// timeout flag.
+__global__ void k_check_wait(const uint32_t* signal, long long max_cycles, DevHeader* hdr) {
+  const volatile uint32_t* sig = signal;
+  const long long t0 = clock64();
+  while (*sig == 0u) {
+    if (clock64() - t0 > max_cycles) {
+      atomicOr(&hdr->flags, WMC_FLAG_TIMEOUT);
+      return;
+    }
+    __nanosleep(256);
+  }
+}
+
 static wmc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WMC_OK : WMC_ERR_CUDA; }
 
 static bool prec_supported(wmc_precision prec) {
@@ -285,6 +300,14 @@ wmc_status wmc_reset_counters(const wmc_params* p, void* ws, wmc_stream_t stream
   if (!params_ok(p) || !ws) return WMC_ERR_ARG;
   const View v = view(*p, ws);
   k_reset_counters<<<1, 1, 0, (cudaStream_t)stream>>>(v.hdr);
+  return cuda_status(cudaGetLastError());
+}
+
+wmc_status wmc_check_wait(const wmc_params* p, const uint32_t* signal, uint64_t max_cycles, void* ws,
+                          wmc_stream_t stream) {
+  if (!params_ok(p) || !signal || !ws || max_cycles > (1ull << 34)) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  k_check_wait<<<1, 1, 0, (cudaStream_t)stream>>>(signal, (long long)max_cycles, v.hdr);
   return cuda_status(cudaGetLastError());
 }
 

@@ -31,7 +31,7 @@ EXPORTS = (
     "wmc_kernel_table_occupied", "wmc_step", "wmc_run", "wmc_density", "wmc_materialize", "wmc_philox4x32_10",
     "wmc_kernel_eval_noalloc", "wmc_batch_workspace_size", "wmc_batch_layout", "wmc_batch_init", "wmc_batch_run",
     "wmc_batch_autotune", "wmc_batch_get_counters", "wmc_potential_tanh", "wmc_potential_tanh_vjp",
-    "wmc_kernel_eval_rows", "wmc_kernel_vjp",
+    "wmc_kernel_eval_rows", "wmc_kernel_vjp", "wmc_check_wait",
 )
 
 
@@ -123,6 +123,7 @@ def load(path: str | None = None):
             "wmc_density": ([pp, vp, vp, vp], i32),
             "wmc_materialize": ([pp, vp, u32, vp, vp, vp, vp, i64, vp, vp], i32),
             "wmc_philox4x32_10": ([vp, u32, u32, i64, vp, vp], i32),
+            "wmc_check_wait": ([pp, vp, ctypes.c_uint64, vp, vp], i32),
             "wmc_kernel_eval_noalloc": ([pp, vp, vp, i32, vp, vp], i32),
             "wmc_batch_workspace_size": ([pp, i32], ctypes.c_size_t),
             "wmc_batch_layout": ([pp, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], i32),
@@ -183,6 +184,13 @@ def init(p: Params, ws: torch.Tensor) -> None:
 
 def reset_counters(p: Params, ws: torch.Tensor) -> None:
     _check("wmc_reset_counters", load().wmc_reset_counters(ctypes.byref(p), _ptr(ws), _stream()))
+
+
+def check_wait(p: Params, signal: torch.Tensor, max_cycles: int, ws: torch.Tensor) -> None:
+    """wmc_check_wait: a bounded device wait on signal (uint32/int32 [1]); sets
+    the timeout flag in ws if nothing sets the word within max_cycles."""
+    _check("wmc_check_wait", load().wmc_check_wait(ctypes.byref(p), _ptr(signal), int(max_cycles), _ptr(ws),
+                                                   _stream()))
 
 
 def get_counters(p: Params, ws: torch.Tensor) -> dict:

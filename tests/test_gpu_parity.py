@@ -375,6 +375,30 @@ def test_materialize_matches_oracle(wmc):
     assert wmc.get_counters(p, ws)["flags"] & wmc.FLAG_CAPACITY
 
 
+def test_bounded_wait_timeout_is_reported_and_context_survives(wmc):
+    """Failure detection without a fault: a device wait on a word nothing sets
+    gives up after its cycle budget and raises the timeout flag; the flag is
+    cleared by a counter reset, a wait on a set word passes, and the next
+    kernel call on the same context is correct."""
+    wl = wi.BARRIER_100
+    p = wmc.Params.of(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    sig = torch.zeros(1, dtype=torch.int32, device="cuda")
+    wmc.check_wait(p, sig, 2_000_000, ws)  # about a millisecond
+    assert wmc.get_counters(p, ws)["flags"] & wmc.FLAG_TIMEOUT
+    wmc.reset_counters(p, ws)
+    assert wmc.get_counters(p, ws)["flags"] == 0
+    sig.fill_(1)
+    wmc.check_wait(p, sig, 2_000_000, ws)
+    assert wmc.get_counters(p, ws)["flags"] == 0
+    V = wi.potential(wl)
+    occ = torch.arange(wl.n_x, dtype=torch.int32, device="cuda")
+    got = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), occ, ws).cpu().numpy()
+    ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, np.arange(wl.n_x))[:, wl.Q // 2:]
+    assert normwise(got, ref) <= KERNEL_TOL
+
+
 def test_rate_flag(wmc):
     """gamma dt >= 1 is flagged, never clamped silently."""
     wl = wi.BARRIER_100.replace(dt_s=2e-15)
