@@ -338,6 +338,7 @@ wmc_status wmc_potential_tanh_vjp(const wmc_params* p, const float* theta, int32
 
 wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_pot, wmc_precision prec, float* VWh,
                                 void* ws, wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_kernel_eval_rows");
   if (!params_ok(p) || !V || !VWh || !ws || n_pot < 0) return WMC_ERR_ARG;
   if (prec != WMC_FP32 && prec != WMC_BF16 && prec != WMC_FP16 && prec != WMC_FP16_SPLIT && prec != WMC_TF32X3)
     return WMC_ERR_UNSUPPORTED;
@@ -359,6 +360,7 @@ wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_p
 
 wmc_status wmc_kernel_vjp(const wmc_params* p, const float* VWh, const float* gVW, const float* g_gamma,
                           int32_t n_pot, float* Abar, float* Vbar, void* ws, wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_kernel_vjp");
   if (!params_ok(p) || !VWh || !Abar || !Vbar || !ws || n_pot < 0 || (!gVW && !g_gamma)) return WMC_ERR_ARG;
   if (p->bc_potential != 0 || p->Q / 2 > 128) return WMC_ERR_UNSUPPORTED;
   const View v = view(*p, ws);

@@ -177,7 +177,11 @@ static bool aux_stream(AuxStream& out) {
 static wmc_status one_step(const wmc_params& p, const View& v, const float* V, const int32_t* in, int32_t* out,
                            wmc_precision prec, int device_step, uint32_t t, cudaStream_t s) {
   // the per-cell scan also zeroes the output histogram
-  cudaError_t e = launch_rows(p, v, in, nullptr, s, out);
+  cudaError_t e;
+  {
+    NvtxRange r("wmc rebuild: per-cell scan");
+    e = launch_rows(p, v, in, nullptr, s, out);
+  }
   if (e != cudaSuccess) return WMC_ERR_CUDA;
   AuxStream aux;
   if (prec == WMC_FP32 && small_window(p) && aux_stream(aux)) {
@@ -185,17 +189,30 @@ static wmc_status one_step(const wmc_params& p, const View& v, const float* V, c
     // runs beside it on the second stream; the step waits for both
     if (cudaEventRecord(aux.fork, s) != cudaSuccess || cudaStreamWaitEvent(aux.s, aux.fork, 0) != cudaSuccess)
       return WMC_ERR_CUDA;
-    e = launch_plan_scan(p, v, device_step, 0, aux.s);
+    {
+      NvtxRange r("wmc rebuild: plan");
+      e = launch_plan_scan(p, v, device_step, 0, aux.s);
+    }
     if (e != cudaSuccess) return WMC_ERR_CUDA;
     if (cudaEventRecord(aux.join, aux.s) != cudaSuccess) return WMC_ERR_CUDA;
-    e = kernel_and_cdf_occupied(p, v, V, prec, s);
+    {
+      NvtxRange r("wmc kernel: rows, gamma, CDF");
+      e = kernel_and_cdf_occupied(p, v, V, prec, s);
+    }
     if (cudaStreamWaitEvent(s, aux.join, 0) != cudaSuccess || e != cudaSuccess) return WMC_ERR_CUDA;
   } else {
-    e = launch_plan_scan(p, v, device_step, 1, s);
+    {
+      NvtxRange r("wmc rebuild: plan");
+      e = launch_plan_scan(p, v, device_step, 1, s);
+    }
     if (e != cudaSuccess) return WMC_ERR_CUDA;
-    e = kernel_and_cdf_occupied(p, v, V, prec, s);
+    {
+      NvtxRange r("wmc kernel: rows, gamma, CDF");
+      e = kernel_and_cdf_occupied(p, v, V, prec, s);
+    }
     if (e != cudaSuccess) return WMC_ERR_CUDA;
   }
+  NvtxRange r("wmc step: drift, pairs, histogram");
   e = launch_step(p, v, in, t, device_step, out, s);
   return cuda_status(e);
 }
@@ -335,6 +352,7 @@ wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* o
 
 wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
                            wmc_precision prec, float* VWh, void* ws, wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_kernel_eval");
   if (!params_ok(p) || !V || !ws || n_occ < 0 || (n_occ > 0 && (!occ || !VWh))) return WMC_ERR_ARG;
   if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   if (n_occ == 0) return WMC_OK;
@@ -357,6 +375,7 @@ wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows,
 }
 
 wmc_status wmc_annihilate(const wmc_params* p, const int32_t* hist, int64_t* rho, void* ws, wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_annihilate");
   if (!params_ok(p) || !hist || !ws) return WMC_ERR_ARG;
   const View v = view(*p, ws);
   return cuda_status(launch_plan(*p, v, hist, rho, 0, (cudaStream_t)stream));
@@ -384,6 +403,7 @@ wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, vo
 
 wmc_status wmc_step(const wmc_params* p, const int32_t* hist_in, uint32_t t, int32_t* hist_out, void* ws,
                     wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_step");
   if (!params_ok(p) || !hist_in || !hist_out || !ws || hist_in == hist_out || t == 0) return WMC_ERR_ARG;
   const View v = view(*p, ws);
   cudaStream_t s = (cudaStream_t)stream;
@@ -394,6 +414,7 @@ wmc_status wmc_step(const wmc_params* p, const int32_t* hist_in, uint32_t t, int
 
 wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t* hist_b, uint32_t t_first,
                    int32_t n_steps, wmc_precision prec, int32_t use_graph, void* ws, wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_run");
   if (!params_ok(p) || !V || !hist_a || !hist_b || hist_a == hist_b || !ws || n_steps < 0 || t_first == 0)
     return WMC_ERR_ARG;
   if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;

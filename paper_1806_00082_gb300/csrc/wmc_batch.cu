@@ -832,6 +832,7 @@ wmc_status wmc_batch_init(const wmc_params* ps, int32_t n_sims, void* ws, size_t
 wmc_status wmc_batch_run(const wmc_params* ps, int32_t n_sims, const float* V, int32_t* hist_a, int32_t* hist_b,
                          uint32_t t_first, int32_t n_steps, int32_t per_thread, int32_t use_graph, void* ws,
                          wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_batch_run");
   if (!batch_ok(ps, n_sims) || !V || !hist_a || !hist_b || hist_a == hist_b || !ws || n_steps < 0 || t_first == 0)
     return WMC_ERR_ARG;
   if (per_thread == 0) per_thread = 16;

@@ -5,9 +5,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "wmc.h"
 
 namespace wmc {
+
+// Host-side NVTX range for one phase of a call (visible to profilers that
+// record NVTX; a no-op otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr double kHbarEVs = 6.582119569e-16;  // hbar [eV s]
 constexpr double kHbarJs = 1.054571817e-34;   // hbar [J s]
