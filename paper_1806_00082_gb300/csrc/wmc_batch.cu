@@ -557,11 +557,18 @@ __global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a)
     __syncwarp();
 
     const uint32_t Ti = (uint32_t)s_pre[n_M];
+    // the item is [item0, item1) of the quad-aligned id range of the cell; its
+    // ids are spread over the 32 lanes in quad-aligned spans, so a sparse cell
+    // keeps every lane busy
     const unsigned long long A = base & ~3u;
-    const unsigned long long lo64 = A + (unsigned long long)ch * chunk + (unsigned long long)lane * PER;
     const unsigned long long row_end = (unsigned long long)base + Ti;
+    const unsigned long long item0 = A + (unsigned long long)ch * chunk;
+    const unsigned long long item1 = item0 + chunk < row_end ? item0 + chunk : row_end;
+    const unsigned long long len = item1 > item0 ? item1 - item0 : 0ull;
+    const unsigned long long span = ((len + 127ull) / 128ull) * 4ull;
+    const unsigned long long lo64 = item0 + (unsigned long long)lane * span;
     const unsigned long long g0_64 = lo64 > base ? lo64 : base;
-    const unsigned long long g1_64 = lo64 + PER < row_end ? lo64 + PER : row_end;
+    const unsigned long long g1_64 = lo64 + span < item1 ? lo64 + span : item1;
     const uint32_t g0 = g0_64 < g1_64 ? (uint32_t)g0_64 : 0u;
     const uint32_t g1 = g0_64 < g1_64 ? (uint32_t)g1_64 : 0u;
     const bool need_gen = (thr_m | thr_0 | thr_p) != 0ull;

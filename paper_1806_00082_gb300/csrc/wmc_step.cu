@@ -177,11 +177,18 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
       const unsigned long long thr_m = m.thr_m, thr_0 = m.thr_0, thr_p = m.thr_p;
       const int w = tid - 32;  // worker index
       const uint32_t Ti = (uint32_t)s_pre[n_M];
+      // the item is [item0, item1) of the quad-aligned id range of the cell; its
+      // ids are spread over all workers in quad-aligned spans (a cell's last,
+      // partial item then keeps every worker busy too)
       const unsigned long long A = base & ~3u;
-      const unsigned long long lo64 = A + (unsigned long long)ch * kChunk + (unsigned long long)w * kPerThread;
       const unsigned long long row_end = (unsigned long long)base + Ti;
+      const unsigned long long item0 = A + (unsigned long long)ch * kChunk;
+      const unsigned long long item1 = item0 + kChunk < row_end ? item0 + kChunk : row_end;
+      const unsigned long long len = item1 > item0 ? item1 - item0 : 0ull;
+      const unsigned long long span = ((len + 4ull * kStepWorkers - 1) / (4ull * kStepWorkers)) * 4ull;
+      const unsigned long long lo64 = item0 + (unsigned long long)w * span;
       const unsigned long long g0_64 = lo64 > base ? lo64 : base;
-      const unsigned long long g1_64 = lo64 + kPerThread < row_end ? lo64 + kPerThread : row_end;
+      const unsigned long long g1_64 = lo64 + span < item1 ? lo64 + span : item1;
       // ids stay below 2^32 (the plan guarantees it); compare in 64 bits first
       const uint32_t g0 = g0_64 < g1_64 ? (uint32_t)g0_64 : 0u;
       const uint32_t g1 = g0_64 < g1_64 ? (uint32_t)g1_64 : 0u;
