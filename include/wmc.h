@@ -264,8 +264,8 @@ wmc_status wmc_batch_init(const wmc_params* ps, int32_t n_sims, void* ws, size_t
 
 /* n_steps steps of every simulation from hist_a (state after step
  * t_first - 1), hist_b the second buffer, final state in hist_a.
- * per_thread: survivor ids per thread of a work item (4, 8, 16, 32 or 64; 0 =
- * 16), e.g. from wmc_batch_autotune; results do not depend on it.  use_graph
+ * per_thread: survivor ids per lane of a work item (4, 8, 16, 32, 64, 128 or
+ * 256; 0 = 16), e.g. from wmc_batch_autotune; results do not depend on it.  use_graph
  * as for wmc_run. */
 wmc_status wmc_batch_run(const wmc_params* ps, int32_t n_sims, const float* V, int32_t* hist_a, int32_t* hist_b,
                          uint32_t t_first, int32_t n_steps, int32_t per_thread, int32_t use_graph, void* ws,

@@ -762,7 +762,7 @@ struct BatchGraph {
 };
 BatchGraph g_bgraph;
 
-bool valid_per(int per) { return per == 4 || per == 8 || per == 16 || per == 32 || per == 64; }
+bool valid_per(int per) { return per == 4 || per == 8 || per == 16 || per == 32 || per == 64 || per == 128 || per == 256; }
 
 }  // namespace
 }  // namespace wmc
@@ -913,13 +913,13 @@ wmc_status wmc_batch_autotune(const wmc_params* ps, int32_t n_sims, const float*
   const BatchView v = batch_view(L, ws);
   cudaStream_t s = (cudaStream_t)stream;
   const int grid = b_step_grid(L.NM);
-  const int cands[4] = {8, 16, 32, 64};
+  const int cands[5] = {16, 32, 64, 128, 256};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return WMC_ERR_CUDA;
   float best = 1e30f;
   int best_per = 16;
   for (int r = 0; r < 2; ++r) {  // second round measures warm
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 5; ++q) {
       k_b_set_step<<<1, 1, 0, s>>>(v.hdr, t - 1u);
       cudaEventRecord(e0, s);
       if (b_one_step(L, v, n_sims, V, hist, scratch, cands[q], grid, s) != cudaSuccess) return WMC_ERR_CUDA;

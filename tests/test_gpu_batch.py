@@ -68,7 +68,7 @@ def test_batch_work_item_sizes_and_graph(wmc):
     wls[2] = wls[2].replace(packet=wi.Packet(wls[2].length_m / 2 - 8e-9, 4e-9, 0.1, 20_000))
     ps, co, ho, V, H = _batch(wmc, wls)
     ref, _ = _run_batch(wmc, ps, V, H, 3, 5, per=16)
-    for per in (8, 32, 64):
+    for per in (4, 8, 32, 64, 128, 256):
         got, _ = _run_batch(wmc, ps, V, H, 3, 5, per=per)
         np.testing.assert_array_equal(got, ref)
     got, _ = _run_batch(wmc, ps, V, H, 3, 5, per=16, use_graph=False)
@@ -78,7 +78,7 @@ def test_batch_work_item_sizes_and_graph(wmc):
     a = torch.from_numpy(H).cuda()
     scratch = torch.empty_like(a)
     best = wmc.batch_autotune(ps, torch.from_numpy(V).cuda(), a, scratch, 1, ws)
-    assert best in (8, 16, 32, 64)
+    assert best in (16, 32, 64, 128, 256)
     np.testing.assert_array_equal(a.cpu().numpy(), H)
 
 
