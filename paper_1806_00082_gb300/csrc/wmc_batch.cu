@@ -205,16 +205,35 @@ __global__ void k_b_rows(const int32_t* __restrict__ hist, const SimDesc* __rest
   if (c >= n_cells) return;
   const SimDesc& s = d[__ldg(cell_sim + c)];
   const long long i = c - s.cell_off;
-  const int32_t* row = hist + s.hist_off + i * s.n_M;
-  const float* Ds = D + s.tab_off;
+  const int n_M = s.n_M;
+  const int32_t* row = hist + s.hist_off + i * n_M;
+  // the drift D[M] = fl32(M d1), d1 > 0, has the sign of M: a column right of
+  // the centre drifts right, left of it left (a D that rounds to zero only
+  // marks a neighbour that needs its kernel anyway, which changes no result)
   unsigned long long a = 0;
   unsigned bits = 0;
-  for (int k = lane; k < s.n_M; k += 32) {
-    const int nv = __ldg(row + k);
-    if (nv) {
-      a += (unsigned long long)(nv < 0 ? -(long long)nv : (long long)nv);
-      const float dv = __ldg(Ds + k);
-      bits |= 1u | (dv > 0.f ? 2u : 0u) | (dv < 0.f ? 4u : 0u);
+  if ((n_M & 3) == 0 && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+    const int4* row4 = reinterpret_cast<const int4*>(row);
+    for (int q = lane; q < n_M / 4; q += 32) {
+      const int4 n4 = __ldg(row4 + q);
+      const int nv[4] = {n4.x, n4.y, n4.z, n4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (nv[e]) {
+          const int M = 4 * q + e - n_M / 2;
+          a += (unsigned long long)(nv[e] < 0 ? -(long long)nv[e] : (long long)nv[e]);
+          bits |= 1u | (M > 0 ? 2u : 0u) | (M < 0 ? 4u : 0u);
+        }
+      }
+    }
+  } else {
+    for (int k = lane; k < n_M; k += 32) {
+      const int nv = __ldg(row + k);
+      if (nv) {
+        const int M = k - n_M / 2;
+        a += (unsigned long long)(nv < 0 ? -(long long)nv : (long long)nv);
+        bits |= 1u | (M > 0 ? 2u : 0u) | (M < 0 ? 4u : 0u);
+      }
     }
   }
 #pragma unroll
