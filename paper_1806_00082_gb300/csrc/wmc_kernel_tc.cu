@@ -1,28 +1,33 @@
 // Wigner-kernel contraction on the 5th-generation tensor cores (tcgen05):
-// the precision forms of wmc_kernel_eval (BF16, FP16, FP16 hi/lo split).
+// the precision forms of wmc_kernel_eval (BF16, FP16, FP16 hi/lo split, 3xTF32).
 //
 //   VWh[row][r] = c * sum_{m=1}^{h-1} A[row][m] S[m][r],  A[row][m] = V(i+m) - V(i-m)
 //
-// One CTA of 128 threads computes a 128-row x 128-column output tile.  For each
-// K block of 64 window terms:
-//   - thread 0 starts bulk (TMA) copies of the precomputed sine-matrix operand
-//     image(s) of this tile and K block into shared memory, completing on an
-//     mbarrier;
-//   - every thread builds its row of the A operand (64 potential differences,
-//     rounded to the input type) in shared memory;
-//   - after a proxy fence and a barrier, thread 0 issues four
-//     tcgen05.mma (M = 128, N = 128, K = 16) per product into accumulators in
-//     tensor memory and commits them to a second mbarrier, which every thread
-//     waits on before the shared buffers are rewritten.
-// Operands use the K-major layout without swizzle: 8-row x 16-byte core
-// matrices, 128 bytes apart along K (LBO) and 1024 bytes apart along M/N (SBO).
-// Accumulation: the main product is split over two K halves held in separate
-// FP32 accumulators; the split form's cross terms (A_hi B_lo + A_lo B_hi, both
-// lo parts scaled by 2^11) go to a third.  The epilogue reads them with
-// tcgen05.ld and combines them in FP32.
+// The sine matrix S is precomputed once per workspace as operand images in
+// global memory (BF16, FP16 hi, FP16 lo, TF32 hi, TF32 lo) in 16 KB blocks of
+// 128 rows in the layout below; A is generated in shared memory from
+// the potential and never written to global memory.  Three kernels:
+//   - k_kernel_eval_tc_ws<BF16 | FP16, N>: warp-specialised (16 builder /
+//     epilogue warps, one MMA-issuing thread, one bulk-copy thread), the whole
+//     A operand of a 128-row tile resident in shared memory, B streamed
+//     through a ring of stages, M = 128, N = 256 (128 for narrow windows),
+//     two TMEM accumulator buffers so that the epilogue of one column tile
+//     overlaps the MMAs of the next;
+//   - k_kernel_eval_tc_ws_split<FP16 | TF32>: the hi/lo split forms, three MMAs
+//     per K step (hi x hi, hi x lo, lo x hi), A resident per K pass;
+//   - k_kernel_eval_tc: a per-tile kernel with both operands streamed, for
+//     BF16 / FP16 windows whose A operand does not fit in shared memory.
+// Operands use the K-major 128-byte swizzled layout: rows of 128 bytes
+// (64 16-bit or 32 TF32 values), 8-row atoms 1024 bytes apart, the 16-byte
+// chunks of row r XOR-swizzled by r % 8; shared-memory blocks are aligned to
+// 1024 bytes.  Accumulation is FP32 in TMEM; the main product is split over
+// two K halves held in separate accumulators and the split forms' cross terms
+// go to a third; the epilogue reads them with tcgen05.ld and combines them in
+// FP32.
 //
 // Every wait is bounded (about one second of SM clock); on a timeout the CTA
-// sets WMC_FLAG_TIMEOUT, stops issuing work, and still frees its tensor memory.
+// sets WMC_FLAG_TIMEOUT, stops issuing work, lets its copies and MMAs in
+// flight complete (bounded again) and still frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
