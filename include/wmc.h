@@ -142,6 +142,23 @@ wmc_status wmc_reset_counters(const wmc_params* p, void* ws, wmc_stream_t stream
 wmc_status wmc_check_wait(const wmc_params* p, const uint32_t* signal, uint64_t max_cycles, void* ws,
                           wmc_stream_t stream);
 
+/* Timing of the particle-step kernel (a measurement aid; the paper has no
+ * counterpart).  While enable != 0, every wmc_step and every step of wmc_run
+ * records two CUDA events owned by the library on the launching stream, right
+ * before and right after the particle-step kernel (one pair per device; when
+ * the stream is being captured they become event-record nodes, and the cached
+ * step graphs are recaptured whenever the setting changes).  The recorded
+ * events add no work to the step and change none of its results.  Host call;
+ * always WMC_OK. */
+wmc_status wmc_step_timing(int32_t enable);
+
+/* Waits for the most recently recorded pair of the current device and writes
+ * the milliseconds between them to *ms [host]: the duration of the last
+ * particle-step kernel that ran with timing on (of a step-pair graph, the
+ * second step's).  WMC_ERR_ARG for a null ms, WMC_ERR_UNSUPPORTED if no pair
+ * has been recorded on this device, WMC_ERR_CUDA on a CUDA error. */
+wmc_status wmc_step_timing_read(float* ms);
+
 /* Reads the counters (synchronises the stream).  out [host]. */
 wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* out, wmc_stream_t stream);
 

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "wmc_internal.cuh"
@@ -217,6 +218,36 @@ static wmc_status one_step(const wmc_params& p, const View& v, const float* V, c
   return cuda_status(e);
 }
 
+// Events around the particle-step kernel, one pair per device, created on first
+// use; `on` is read by every step launch, `recorded` once a pair has been
+// enqueued (or captured) on that device.
+struct StepTiming {
+  std::mutex mu;
+  std::atomic<int> on{0};
+  cudaEvent_t ev[8][2] = {};
+  bool recorded[8] = {};
+};
+static StepTiming g_timing;
+
+int step_timing_on() { return g_timing.on.load(); }
+
+cudaError_t step_timing_record(cudaStream_t s, bool end) {
+  if (!g_timing.on.load()) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 8) return cudaSuccess;  // devices beyond the table are not timed
+  std::lock_guard<std::mutex> lock(g_timing.mu);
+  cudaEvent_t& ev = g_timing.ev[dev][end ? 1 : 0];
+  if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return e;
+  e = cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                          : cudaEventRecord(ev, s);
+  if (e == cudaSuccess && end) g_timing.recorded[dev] = true;
+  return e;
+}
+
 // One cached executable graph of the step pair a -> b -> a.
 struct GraphCache {
   std::mutex mu;
@@ -226,6 +257,7 @@ struct GraphCache {
   int prec;
   cudaStream_t stream;
   int device;
+  int timing;
   cudaGraphExec_t exec = nullptr;
 };
 static GraphCache g_graph;   // the step pair a -> b -> a
@@ -241,7 +273,8 @@ static wmc_status launch_cached(GraphCache& gc, const wmc_params* p, const float
   int dev = 0;
   cudaGetDevice(&dev);
   const bool hit = gc.valid && memcmp(&gc.p, p, sizeof(wmc_params)) == 0 && gc.V == V && gc.a == a && gc.b == b &&
-                   gc.ws == ws && gc.prec == (int)prec && gc.stream == s && gc.device == dev;
+                   gc.ws == ws && gc.prec == (int)prec && gc.stream == s && gc.device == dev &&
+                   gc.timing == step_timing_on();
   if (!hit) {
     if (gc.exec) {
       cudaGraphExecDestroy(gc.exec);
@@ -268,6 +301,7 @@ static wmc_status launch_cached(GraphCache& gc, const wmc_params* p, const float
     gc.prec = (int)prec;
     gc.stream = s;
     gc.device = dev;
+    gc.timing = step_timing_on();
   }
   for (int q = 0; q < launches; ++q)
     if (cudaGraphLaunch(gc.exec, s) != cudaSuccess) return WMC_ERR_CUDA;
@@ -326,6 +360,26 @@ wmc_status wmc_check_wait(const wmc_params* p, const uint32_t* signal, uint64_t 
   const View v = view(*p, ws);
   k_check_wait<<<1, 1, 0, (cudaStream_t)stream>>>(signal, (long long)max_cycles, v.hdr);
   return cuda_status(cudaGetLastError());
+}
+
+wmc_status wmc_step_timing(int32_t enable) {
+  g_timing.on.store(enable ? 1 : 0);
+  return WMC_OK;
+}
+
+wmc_status wmc_step_timing_read(float* ms) {
+  if (!ms) return WMC_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return WMC_ERR_CUDA;
+  cudaEvent_t b = nullptr, e = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_timing.mu);
+    if (dev < 0 || dev >= 8 || !g_timing.recorded[dev]) return WMC_ERR_UNSUPPORTED;
+    b = g_timing.ev[dev][0];
+    e = g_timing.ev[dev][1];
+  }
+  if (cudaEventSynchronize(e) != cudaSuccess) return WMC_ERR_CUDA;
+  return cudaEventElapsedTime(ms, b, e) == cudaSuccess ? WMC_OK : WMC_ERR_CUDA;
 }
 
 wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* out, wmc_stream_t stream) {

@@ -169,6 +169,12 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, long lo
                           cudaStream_t s);
 
 int num_sms();
+// Optional CUDA events around the particle-step kernel (wmc_step_timing): records
+// the begin (end = false) or end event of the current device on s, as an
+// event-record node when s is being captured.  No-op while timing is off.
+cudaError_t step_timing_record(cudaStream_t s, bool end);
+// Whether step timing is on (part of the key of the cached step graphs).
+int step_timing_on();
 // Caches the step kernel's launch shape for this device (call outside graph capture).
 void prepare_step(const wmc_params& p);
 

@@ -360,8 +360,12 @@ cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_
   a.t = t;
   a.t_from_device = t_from_device;
   a.rows_by_cell = 0;
-  k_step<<<step_grid(p.n_M), kStepThreads, step_smem(p.n_M), s>>>(a);
-  return cudaGetLastError();
+  const int grid = step_grid(p.n_M);
+  cudaError_t e = step_timing_record(s, false);
+  if (e != cudaSuccess) return e;
+  k_step<<<grid, kStepThreads, step_smem(p.n_M), s>>>(a);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? step_timing_record(s, true) : e;
 }
 
 // ---------------------------------------------------------------- explicit survivors

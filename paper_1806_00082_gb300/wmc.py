@@ -31,7 +31,7 @@ EXPORTS = (
     "wmc_kernel_table_occupied", "wmc_step", "wmc_run", "wmc_density", "wmc_materialize", "wmc_philox4x32_10",
     "wmc_kernel_eval_noalloc", "wmc_batch_workspace_size", "wmc_batch_layout", "wmc_batch_init", "wmc_batch_run",
     "wmc_batch_autotune", "wmc_batch_get_counters", "wmc_potential_tanh", "wmc_potential_tanh_vjp",
-    "wmc_kernel_eval_rows", "wmc_kernel_vjp", "wmc_check_wait",
+    "wmc_kernel_eval_rows", "wmc_kernel_vjp", "wmc_check_wait", "wmc_step_timing", "wmc_step_timing_read",
 )
 
 
@@ -124,6 +124,8 @@ def load(path: str | None = None):
             "wmc_materialize": ([pp, vp, u32, vp, vp, vp, vp, i64, vp, vp], i32),
             "wmc_philox4x32_10": ([vp, u32, u32, i64, vp, vp], i32),
             "wmc_check_wait": ([pp, vp, ctypes.c_uint64, vp, vp], i32),
+            "wmc_step_timing": ([i32], i32),
+            "wmc_step_timing_read": ([ctypes.POINTER(ctypes.c_float)], i32),
             "wmc_kernel_eval_noalloc": ([pp, vp, vp, i32, vp, vp], i32),
             "wmc_batch_workspace_size": ([pp, i32], ctypes.c_size_t),
             "wmc_batch_layout": ([pp, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], i32),
@@ -191,6 +193,20 @@ def check_wait(p: Params, signal: torch.Tensor, max_cycles: int, ws: torch.Tenso
     the timeout flag in ws if nothing sets the word within max_cycles."""
     _check("wmc_check_wait", load().wmc_check_wait(ctypes.byref(p), _ptr(signal), int(max_cycles), _ptr(ws),
                                                    _stream()))
+
+
+def step_timing(enable: bool) -> None:
+    """wmc_step_timing: switches the library's events around the particle-step
+    kernel on or off."""
+    _check("wmc_step_timing", load().wmc_step_timing(1 if enable else 0))
+
+
+def step_timing_read() -> float:
+    """wmc_step_timing_read: milliseconds of the last particle-step kernel that
+    ran with timing on (waits for it)."""
+    ms = ctypes.c_float(0.0)
+    _check("wmc_step_timing_read", load().wmc_step_timing_read(ctypes.byref(ms)))
+    return float(ms.value)
 
 
 def get_counters(p: Params, ws: torch.Tensor) -> dict:

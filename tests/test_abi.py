@@ -62,6 +62,8 @@ def test_host_side_argument_checks(lib):
     assert L.wmc_kernel_eval(ctypes.byref(p), None, None, 0, 0, None, None, None) == 1
     assert L.wmc_check_wait(ctypes.byref(p), None, 1000, ctypes.c_void_p(256), None) == 1
     assert L.wmc_check_wait(ctypes.byref(p), ctypes.c_void_p(256), 1 << 40, ctypes.c_void_p(256), None) == 1
+    assert L.wmc_step_timing_read(None) == 1
+    assert L.wmc_step_timing(0) == 0
     assert L.wmc_status_string(3) == b"gamma dt >= 1"
 
 

@@ -350,6 +350,30 @@ def test_odd_step_count_and_continuation(wmc):
     np.testing.assert_array_equal(x.cpu().numpy(), a)
 
 
+def test_step_timing_events_change_nothing(wmc):
+    """The library's events around the particle-step kernel (graph nodes in the
+    cached step graph, plain records on the direct path) leave every result
+    bit-identical and bracket a positive duration."""
+    wl = wi.BARRIER_100.replace(packet=wi.Packet(45e-9, 5e-9, 0.1, 50_000))
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    h0 = wi.initial_histogram(wl)
+    ref, c_ref = gpu_run(wmc, torch, p, V, h0, 1, 6)
+    wmc.step_timing(True)
+    try:
+        got_graph, c_graph = gpu_run(wmc, torch, p, V, h0, 1, 6)
+        ms_graph = wmc.step_timing_read()
+        got_direct, _ = gpu_run(wmc, torch, p, V, h0, 1, 5, use_graph=False)
+        ms_direct = wmc.step_timing_read()
+    finally:
+        wmc.step_timing(False)
+    np.testing.assert_array_equal(got_graph, ref)
+    assert c_graph["pairs"] == c_ref["pairs"] and c_graph["particle_steps"] == c_ref["particle_steps"]
+    ref5, _ = gpu_run(wmc, torch, p, V, h0, 1, 5, use_graph=False)
+    np.testing.assert_array_equal(got_direct, ref5)
+    assert 0.0 < ms_graph < 100.0 and 0.0 < ms_direct < 100.0
+
+
 # --------------------------------------------------------------------------- rebuild, density, flags
 def test_materialize_matches_oracle(wmc):
     wl = wi.BARRIER_100
