@@ -307,21 +307,58 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
   float* s_dv = s_row + 32 * C;                                   // row g: dV(m) at s_dv[g 32 C + m - 1]
   const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
   if ((int)(blockIdx.x * kRowWarps * R) >= n_rows) return;
-  if (reach && (int)(gridDim.x * kRowWarps * R) >= n_rows) {
-    // one pass over the rows: a block none of whose cells needs a kernel only
-    // writes their zero outputs and skips staging the sine matrix
-    const int row = (int)(blockIdx.x * kRowWarps * R) + (int)threadIdx.x;
-    const bool need = threadIdx.x < kRowWarps * R && row < n_rows && cell_needs_kernel(reach, row, n_x);
-    if (!__syncthreads_or(need)) {
-      if (gamma && threadIdx.x < kRowWarps * R && row < n_rows) {
-        gamma[row] = 0.0;
-        gthr[row] = 0ull;
-        if (thr_cell) thr_cell[row] = 0ull;
+  // one pass over the rows (reach mode, the grid covers every row): each warp
+  // loads its rows' reach bits and potential differences at once, before any
+  // decision, and keeps them for the row loop
+  const bool one_pass = reach && (int)(gridDim.x * kRowWarps * R) >= n_rows;
+  unsigned row_ok = 0u;  // bit g: row g of this warp needs its kernel
+  bool stage_B = true;
+  if (one_pass) {
+    float dv[R][C];
+    bool any_ok = false, nz = false;
+#pragma unroll
+    for (int g = 0; g < R; ++g) {
+      const int rw = (int)((blockIdx.x * kRowWarps + wid) * R) + g;
+      if (rw < n_rows && cell_needs_kernel(reach, rw, n_x)) row_ok |= 1u << g;
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        const int m = lane + 1 + 32 * q;
+        dv[g][q] = (rw < n_rows && m <= h - 1)
+                       ? __fsub_rn(pot(V, n_x, bc, (long long)rw + m), pot(V, n_x, bc, (long long)rw - m))
+                       : 0.f;
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < R; ++g) {
+      const bool okg = (row_ok >> g) & 1u;
+      any_ok |= okg;
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        if (!okg) dv[g][q] = 0.f;
+        nz |= dv[g][q] != 0.f;
+        s_dv[g * 32 * C + lane + 32 * q] = dv[g][q];
+      }
+    }
+    // a block none of whose cells needs a kernel only writes their zero
+    // outputs; one whose needed cells all see a flat potential over the window
+    // (their rows are exactly zero, the sums are skipped) needs no sine matrix
+    if (!__syncthreads_or(any_ok)) {
+      if (gamma && lane == 0) {
+#pragma unroll
+        for (int g = 0; g < R; ++g) {
+          const int rw = (int)((blockIdx.x * kRowWarps + wid) * R) + g;
+          if (rw < n_rows) {
+            gamma[rw] = 0.0;
+            gthr[rw] = 0ull;
+            if (thr_cell) thr_cell[rw] = 0ull;
+          }
+        }
       }
       return;
     }
+    stage_B = __syncthreads_or(nz);
   }
-  {
+  if (stage_B) {
     // stage the sine rows with eight loads in flight per thread
     const int nB = (h - 1) * h;
     for (int q0 = threadIdx.x; q0 < nB; q0 += 8 * kRowWarps * 32) {
@@ -343,7 +380,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
   const int r0 = ((-(n_M / 2)) % Q + Q) % Q;
   for (int row0 = (blockIdx.x * kRowWarps + wid) * R; row0 < n_rows; row0 += gridDim.x * kRowWarps * R) {
 #pragma unroll
-    for (int g = 0; g < R; ++g) {
+    for (int g = 0; g < R && !one_pass; ++g) {  // (one pass: loaded above)
       const int row = row0 + g;
       const bool ok = row < n_rows && (!reach || cell_needs_kernel(reach, row, n_x));
       const int i = ok ? (occ ? __ldg(occ + row) : row % n_x) : 0;
@@ -399,7 +436,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
     for (int g = 0; g < R; ++g) {
       const int row = row0 + g;
       if (row >= n_rows) break;
-      if (reach && !cell_needs_kernel(reach, row, n_x)) {
+      if (reach && !(one_pass ? ((row_ok >> g) & 1u) != 0u : cell_needs_kernel(reach, row, n_x))) {
         if (gamma && lane == 0) {
           gamma[row] = 0.0;
           gthr[row] = 0ull;
