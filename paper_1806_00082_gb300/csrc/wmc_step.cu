@@ -25,6 +25,7 @@ struct StepArgs {
   int32_t* hist_out;
   const unsigned long long* R;
   const int2* items;
+  long long max_items;  // capacity of items
   const int* row_map;
   const long long* cdf;  // [rows][n_M] fixed-point CDF
   const unsigned long long* thr_cell;
@@ -145,8 +146,11 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
     m.i = m.ch = 0;
     m.base = 0u;
     m.thr_m = m.thr_0 = m.thr_p = 0ull;
+    // the descriptor load goes out before the item count is known (any index
+    // below the capacity is readable; the count decides whether it is used)
+    int2 it = make_int2(0, 0);
+    if (item < a.max_items) it = __ldg(a.items + item);
     if (item < n_items) {
-      const int2 it = __ldg(a.items + item);
       m.i = it.x;
       m.ch = it.y;
       m.base = (uint32_t)__ldg(a.R + m.i);
@@ -344,6 +348,7 @@ cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_
   a.hist_out = hist_out;
   a.R = v.R;
   a.items = v.items;
+  a.max_items = layout(p).max_items;
   a.row_map = v.row_map;
   a.cdf = v.cdf;
   a.thr_cell = v.thr_cell;
