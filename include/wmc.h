@@ -253,7 +253,9 @@ wmc_status wmc_step(const wmc_params* p, const int32_t* hist_in, uint32_t t, int
  * buffer; the final state is left in hist_a.  prec selects the kernel form.
  * use_graph != 0 captures the step pair, and for an odd n_steps the last step
  * with its copy back to hist_a, in cached CUDA graphs (not on the legacy
- * default stream, where it runs the calls directly). */
+ * default stream, where it runs the calls directly); the graphs of the last
+ * four configurations (parameters, buffers, workspace, precision, stream) are
+ * kept, so alternating between buffer sets does not recapture. */
 wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t* hist_b, uint32_t t_first,
                    int32_t n_steps, wmc_precision prec, int32_t use_graph, void* ws, wmc_stream_t stream);
 

@@ -248,10 +248,15 @@ cudaError_t step_timing_record(cudaStream_t s, bool end) {
   return e;
 }
 
-// One cached executable graph of the step pair a -> b -> a.
-struct GraphCache {
-  std::mutex mu;
+// Cached executable graphs of the step pair a -> b -> a (or of one step), one
+// per configuration (parameters, buffers, workspace, precision, stream,
+// device, step timing), for the last few configurations used: a caller that
+// alternates between buffer sets (copies of the next state overlapping the
+// current step) reuses its graphs instead of recapturing.
+constexpr int kGraphSlots = 4;
+struct GraphSlot {
   bool valid = false;
+  unsigned long long last_use = 0;
   wmc_params p;
   const void *V, *a, *b, *ws;
   int prec;
@@ -260,11 +265,16 @@ struct GraphCache {
   int timing;
   cudaGraphExec_t exec = nullptr;
 };
+struct GraphCache {
+  std::mutex mu;
+  unsigned long long uses = 0;
+  GraphSlot slot[kGraphSlots];
+};
 static GraphCache g_graph;   // the step pair a -> b -> a
 static GraphCache g_graph1;  // one step a -> b and the copy back to a (odd step counts)
 
-// Launches the cached graph `gc` for these arguments, capturing `body` into it
-// first if the cache holds another configuration.
+// Launches the cached graph of these arguments, capturing `body` into the
+// least recently used slot first if no slot holds this configuration.
 template <class Body>
 static wmc_status launch_cached(GraphCache& gc, const wmc_params* p, const float* V, const int32_t* a,
                                 const int32_t* b, const void* ws, wmc_precision prec, cudaStream_t s, int launches,
@@ -272,15 +282,24 @@ static wmc_status launch_cached(GraphCache& gc, const wmc_params* p, const float
   std::lock_guard<std::mutex> lock(gc.mu);
   int dev = 0;
   cudaGetDevice(&dev);
-  const bool hit = gc.valid && memcmp(&gc.p, p, sizeof(wmc_params)) == 0 && gc.V == V && gc.a == a && gc.b == b &&
-                   gc.ws == ws && gc.prec == (int)prec && gc.stream == s && gc.device == dev &&
-                   gc.timing == step_timing_on();
-  if (!hit) {
-    if (gc.exec) {
-      cudaGraphExecDestroy(gc.exec);
-      gc.exec = nullptr;
+  const int timing = step_timing_on();
+  GraphSlot* hit = nullptr;
+  GraphSlot* victim = &gc.slot[0];
+  for (GraphSlot& g : gc.slot) {
+    if (g.valid && memcmp(&g.p, p, sizeof(wmc_params)) == 0 && g.V == V && g.a == a && g.b == b && g.ws == ws &&
+        g.prec == (int)prec && g.stream == s && g.device == dev && g.timing == timing) {
+      hit = &g;
+      break;
     }
-    gc.valid = false;
+    if (!g.valid || (victim->valid && g.last_use < victim->last_use)) victim = &g;
+  }
+  if (!hit) {
+    GraphSlot& gs = *victim;
+    if (gs.exec) {
+      cudaGraphExecDestroy(gs.exec);
+      gs.exec = nullptr;
+    }
+    gs.valid = false;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WMC_ERR_CUDA;
     const wmc_status st = body();
@@ -289,22 +308,24 @@ static wmc_status launch_cached(GraphCache& gc, const wmc_params* p, const float
       if (graph) cudaGraphDestroy(graph);
       return st != WMC_OK ? st : WMC_ERR_CUDA;
     }
-    e = cudaGraphInstantiate(&gc.exec, graph, 0);
+    e = cudaGraphInstantiate(&gs.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return WMC_ERR_CUDA;
-    gc.valid = true;
-    gc.p = *p;
-    gc.V = V;
-    gc.a = a;
-    gc.b = b;
-    gc.ws = ws;
-    gc.prec = (int)prec;
-    gc.stream = s;
-    gc.device = dev;
-    gc.timing = step_timing_on();
+    gs.valid = true;
+    gs.p = *p;
+    gs.V = V;
+    gs.a = a;
+    gs.b = b;
+    gs.ws = ws;
+    gs.prec = (int)prec;
+    gs.stream = s;
+    gs.device = dev;
+    gs.timing = timing;
+    hit = &gs;
   }
+  hit->last_use = ++gc.uses;
   for (int q = 0; q < launches; ++q)
-    if (cudaGraphLaunch(gc.exec, s) != cudaSuccess) return WMC_ERR_CUDA;
+    if (cudaGraphLaunch(hit->exec, s) != cudaSuccess) return WMC_ERR_CUDA;
   return WMC_OK;
 }
 
