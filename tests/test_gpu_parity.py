@@ -350,6 +350,31 @@ def test_odd_step_count_and_continuation(wmc):
     np.testing.assert_array_equal(x.cpu().numpy(), a)
 
 
+def test_graph_cache_alternating_buffer_sets(wmc):
+    """Five buffer sets stepped in turn on one workspace and stream (more sets
+    than cached graphs per kind, so slots are reused and recaptured): after
+    three rounds of three steps every set holds the nine-step state of the
+    direct call sequence."""
+    wl = wi.BARRIER_100.replace(packet=wi.Packet(45e-9, 5e-9, 0.1, 50_000))
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    h0 = wi.initial_histogram(wl)
+    ref, _ = gpu_run(wmc, torch, p, V, h0, 1, 9, use_graph=False)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    Vd = torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).cuda()
+    x0 = torch.from_numpy(np.ascontiguousarray(h0, dtype=np.int32)).cuda()
+    sets = [(x0.clone(), torch.empty_like(x0)) for _ in range(5)]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for rnd in range(3):
+            for a, b in sets:
+                wmc.run(p, Vd, a, b, 1 + 3 * rnd, 3, ws, wmc.FP32, True)
+    s.synchronize()
+    for a, _ in sets:
+        np.testing.assert_array_equal(a.cpu().numpy(), ref)
+
+
 def test_step_timing_events_change_nothing(wmc):
     """The library's events around the particle-step kernel (graph nodes in the
     cached step graph, plain records on the direct path) leave every result
