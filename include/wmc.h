@@ -145,7 +145,8 @@ wmc_status wmc_check_wait(const wmc_params* p, const uint32_t* signal, uint64_t 
 /* Timing of the particle-step kernel (a measurement aid; the paper has no
  * counterpart).  While enable != 0, every wmc_step and every step of wmc_run
  * records two CUDA events owned by the library on the launching stream, right
- * before and right after the particle-step kernel (one pair per device; when
+ * before and right after the particle-step kernel (one pair per device, for
+ * devices 0-7; steps on other devices are not timed; when
  * the stream is being captured they become event-record nodes, and the cached
  * step graphs are recaptured whenever the setting changes).  The recorded
  * events add no work to the step and change none of its results.  Host call;
