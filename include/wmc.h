@@ -148,9 +148,9 @@ wmc_status wmc_check_wait(const wmc_params* p, const uint32_t* signal, uint64_t 
  * before and right after the particle-step kernel (one pair per device, for
  * devices 0-7; steps on other devices are not timed; when
  * the stream is being captured they become event-record nodes, and the cached
- * step graphs are recaptured whenever the setting changes).  The recorded
- * events add no work to the step and change none of its results.  Host call;
- * always WMC_OK. */
+ * step graphs are recaptured whenever the setting changes).  The events add
+ * latency to a step graph (a few microseconds per event node) but no work,
+ * and change none of its results.  Host call; always WMC_OK. */
 wmc_status wmc_step_timing(int32_t enable);
 
 /* Waits for the most recently recorded pair of the current device and writes
