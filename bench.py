@@ -6,7 +6,9 @@ A step is one pass of the whole hot path over the ensemble: survivor
 enumeration and occupied cells (rule 2 rebuild), the Wigner kernel on the
 occupied cells with gamma and the momentum CDF, and the particle step (drift,
 absorption, pair creation, signed histogram).  The default workload is the
-2000-cell barrier with 1e7 particles (FP32 kernel).  `value` is particle-steps/s
+16384-cell noisy double barrier (Q = n_M = 1024) with 1e8 particles, where
+every occupied cell creates pairs; the 2000-cell barrier (1e7 particles, whose
+early steps create no pairs) is a secondary drift-only leg.  `value` is particle-steps/s
 over all ranks; N > 1 runs independent replicas (one simulation per rank, its
 own Philox stream), so scaling is weak.  `--impl reference` times the CPU
 oracle on the host cores on a bounded sample of the same workload.
@@ -534,7 +536,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="barrier-2000", choices=sorted(wi.WORKLOADS))
+    ap.add_argument("--workload", default="double-barrier-16384", choices=sorted(wi.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--leg", default="all", choices=["all", "kernel", "batched", "adjoint"],

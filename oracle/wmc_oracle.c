@@ -147,12 +147,35 @@ double wmco_kernel_value(const wmco_params* p, const double* V, int32_t i, int32
   return -acc / (WMCO_HBAR_EVS * (double)p->Q);
 }
 
-/* Rows of the kernel over the momentum grid: out[r][k] = V_W(rows[r]; k - n_M/2). */
+/* Rows of the kernel over the momentum grid: out[r][k] = V_W(rows[r]; k - n_M/2).
+ * The same sum as wmco_kernel_value, term by term and in the same order; the
+ * Q sine values sin(2 pi t / Q) and the 2h + 1 differences of a row are
+ * computed once and looked up, so every term is the identical FP64 product
+ * and the result is bit-for-bit that of wmco_kernel_value. */
 void wmco_kernel_rows(const wmco_params* p, const double* V, int32_t n_rows, const int32_t* rows,
                       double* out) {
-  for (int32_t r = 0; r < n_rows; ++r)
-    for (int32_t k = 0; k < p->n_M; ++k)
-      out[(int64_t)r * p->n_M + k] = wmco_kernel_value(p, V, rows[r], k - p->n_M / 2);
+  const int32_t Q = p->Q, h = Q / 2;
+  double* S = (double*)malloc(sizeof(double) * (size_t)Q);
+  double* dV = (double*)malloc(sizeof(double) * (size_t)(2 * h + 1));
+  for (int32_t t = 0; t < Q; ++t) S[t] = wmco_sine(Q, t);
+  for (int32_t r = 0; r < n_rows; ++r) {
+    const int32_t i = rows[r];
+    for (int32_t m = -h; m <= h; ++m) dV[m + h] = pot(p, V, (int64_t)i + m) - pot(p, V, (int64_t)i - m);
+    for (int32_t k = 0; k < p->n_M; ++k) {
+      const int64_t M = k - p->n_M / 2;
+      const int64_t step = ((M % Q) + Q) % Q;          /* (m + 1) M - m M, reduced mod Q */
+      int64_t t = (((int64_t)(-h) * M) % Q + Q) % Q;   /* (m M) mod Q at m = -h */
+      double acc = 0.0;
+      for (int32_t m = -h; m <= h; ++m) {
+        acc += S[t] * dV[m + h];
+        t += step;
+        if (t >= Q) t -= Q;
+      }
+      out[(int64_t)r * p->n_M + k] = -acc / (WMCO_HBAR_EVS * (double)Q);
+    }
+  }
+  free(S);
+  free(dV);
 }
 
 /* Smallest L with 2^L >= n. */

@@ -39,8 +39,9 @@ def gpu_run_table(wmc, torch, p, half_table, hist0, t_first, n_steps):
     return out, wmc.get_counters(p, ws)
 
 
-def gpu_run(wmc, torch, p, V, hist0, t_first, n_steps, use_graph=True):
-    """Production loop: wmc_run with the FP32 kernel evaluated on occupied cells."""
+def gpu_run(wmc, torch, p, V, hist0, t_first, n_steps, use_graph=True, prec=None):
+    """Production loop: wmc_run with the kernel (FP32 unless prec says otherwise)
+    evaluated on occupied cells."""
     ws = wmc.workspace(p)
     wmc.init(p, ws)
     Vd = torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).cuda()
@@ -48,7 +49,7 @@ def gpu_run(wmc, torch, p, V, hist0, t_first, n_steps, use_graph=True):
     b = torch.empty_like(a)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        wmc.run(p, Vd, a, b, t_first, n_steps, ws, wmc.FP32, use_graph)
+        wmc.run(p, Vd, a, b, t_first, n_steps, ws, wmc.FP32 if prec is None else prec, use_graph)
         c = wmc.get_counters(p, ws)
     s.synchronize()
     return a.cpu().numpy(), c
@@ -56,3 +57,28 @@ def gpu_run(wmc, torch, p, V, hist0, t_first, n_steps, use_graph=True):
 
 def normwise(a, b):
     return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def full_from_half(half, Q, n_M):
+    """Kernel rows over the momentum grid M = k - n_M/2 from half-period rows
+    (V_W odd and Q-periodic in M, zero at M = 0 and M = Q/2): the layout the
+    oracle's simulator takes a table in."""
+    h = Q // 2
+    half = np.asarray(half, np.float32)
+    r = (np.arange(n_M) - n_M // 2) % Q
+    out = np.zeros((half.shape[0], n_M), np.float32)
+    lo = (r > 0) & (r < h)
+    hi = r > h
+    out[:, lo] = half[:, r[lo]]
+    out[:, hi] = -half[:, Q - r[hi]]
+    return out
+
+
+def reach_rows(hist0, n_steps, n_x):
+    """Cells a particle of hist0 can be in during the next n_steps steps (a
+    drift moves at most one cell per step)."""
+    occ = np.flatnonzero(np.abs(hist0).sum(axis=1))
+    if occ.size == 0:
+        return occ
+    lo, hi = max(0, occ.min() - n_steps - 1), min(n_x, occ.max() + n_steps + 2)
+    return np.arange(lo, hi)

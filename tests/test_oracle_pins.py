@@ -71,6 +71,22 @@ def test_sine_table(Q):
 
 
 # --------------------------------------------------------------------------- kernel closed forms
+def test_kernel_rows_equal_single_value_sum():
+    """The row routine (sine values and differences looked up from per-call
+    tables) gives bit-for-bit the single-value sum of Eq. (wigner-1d-discrete)
+    term by term, for n_M below, at and above the period, both boundary modes
+    and rows at and beyond the window edges."""
+    rng = np.random.default_rng(11)
+    for n_x, Q, n_M, bc in [(40, 8, 8, 0), (60, 16, 48, 1), (90, 32, 64, 0), (70, 30, 20, 1)]:
+        p = _p(n_x=n_x, Q=Q, n_M=n_M, bc=bc)
+        V = rng.uniform(-0.3, 0.3, n_x)
+        rows = np.array([0, 1, Q // 2 - 1, Q // 2, n_x // 2, n_x - 2, n_x - 1])
+        got = oracle.kernel_rows(p, V, rows)
+        for r, i in enumerate(rows):
+            for k in range(n_M):
+                assert got[r, k] == oracle.kernel_value(p, V, int(i), k - n_M // 2), (n_x, Q, n_M, bc, i, k)
+
+
 def _dirichlet_sine_sum(p, q, phi):
     """sum_{m=p}^{q} sin(m phi) in closed form."""
     if p > q:
