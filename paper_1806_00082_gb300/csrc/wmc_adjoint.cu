@@ -352,7 +352,7 @@ wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_p
     e = launch_kernel_eval_tc(*p, (int)prec, V, nullptr, nullptr, (int)rows, (int)rows, v.tc, VWh, &v.hdr->flags, s);
   else if (small_window(*p))
     e = launch_kernel_rows_small(*p, V, nullptr, nullptr, (int)rows, (int)rows, v.B, VWh, nullptr, nullptr, nullptr,
-                                 nullptr, nullptr, s);
+                                 nullptr, nullptr, nullptr, s);
   else
     e = launch_kernel_eval(*p, V, nullptr, nullptr, (int)rows, (int)rows, v.B, VWh, s);
   return e == cudaSuccess ? WMC_OK : WMC_ERR_CUDA;

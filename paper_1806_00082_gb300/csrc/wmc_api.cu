@@ -43,7 +43,8 @@ Layout layout(const wmc_params& p) {
   L.occ = o; o = align256(o + sizeof(int) * nx);
   L.row_map = o; o = align256(o + sizeof(int) * nx);
   L.VWh = o; o = align256(o + sizeof(float) * nx * (size_t)L.h);
-  L.cdf = o; o = align256(o + sizeof(long long) * nx * nM);
+  L.ccdf = o; o = align256(o + sizeof(long long) * nx * kCdfBlocks);
+  L.scale = o; o = align256(o + sizeof(int) * nx);
   L.gamma = o; o = align256(o + sizeof(double) * nx);
   L.gthr = o; o = align256(o + sizeof(unsigned long long) * nx);
   L.thr_cell = o; o = align256(o + sizeof(unsigned long long) * nx);
@@ -52,6 +53,13 @@ Layout layout(const wmc_params& p) {
   L.xhi = o; o = align256(o + sizeof(uint32_t) * nM);
   L.max_items = kMaxItemsBase + 2 * (long long)nx;
   L.items = o; o = align256(o + sizeof(int2) * (size_t)L.max_items);
+  // pair queue: one entry per created pair of a step (events beyond it are
+  // processed inside the step kernel instead)
+  {
+    const size_t want = nx * nM / 8;
+    L.pair_cap = (unsigned)(want < (1u << 16) ? (1u << 16) : (want > (1u << 21) ? (1u << 21) : want));
+  }
+  L.pairs = o; o = align256(o + sizeof(uint4) * (size_t)L.pair_cap);
   L.B = o; o = align256(o + sizeof(float) * (size_t)L.Kp * (size_t)L.Np);
   L.tc = o; o = align256(o + tc_images_bytes(p));
   L.total = o;
@@ -70,7 +78,8 @@ View view(const wmc_params& p, void* ws) {
   v.occ = reinterpret_cast<int*>(b + L.occ);
   v.row_map = reinterpret_cast<int*>(b + L.row_map);
   v.VWh = reinterpret_cast<float*>(b + L.VWh);
-  v.cdf = reinterpret_cast<long long*>(b + L.cdf);
+  v.ccdf = reinterpret_cast<long long*>(b + L.ccdf);
+  v.scale = reinterpret_cast<int*>(b + L.scale);
   v.gamma = reinterpret_cast<double*>(b + L.gamma);
   v.gthr = reinterpret_cast<unsigned long long*>(b + L.gthr);
   v.D = reinterpret_cast<float*>(b + L.D);
@@ -78,6 +87,7 @@ View view(const wmc_params& p, void* ws) {
   v.xhi = reinterpret_cast<uint32_t*>(b + L.xhi);
   v.thr_cell = reinterpret_cast<unsigned long long*>(b + L.thr_cell);
   v.items = reinterpret_cast<int2*>(b + L.items);
+  v.pairs = reinterpret_cast<uint4*>(b + L.pairs);
   v.B = reinterpret_cast<float*>(b + L.B);
   v.tc = b + L.tc;
   return v;
@@ -138,16 +148,16 @@ static cudaError_t kernel_and_cdf_occupied(const wmc_params& p, const View& v, c
     cudaError_t e = launch_kernel_eval_tc(p, (int)prec, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.tc, v.VWh,
                                           &v.hdr->flags, s);
     if (e != cudaSuccess) return e;
-    return launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
-                      &v.hdr->flags, s, v.hdr);
+    return launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, nullptr, v.gamma, v.scale, v.gthr, v.occ, v.thr_cell,
+                      &v.hdr->flags, s, v.hdr, v.ccdf);
   }
   if (small_window(p))  // every cell a row, evaluated where the reach bits need it
-    return launch_kernel_rows_small(p, V, nullptr, nullptr, p.n_x, p.n_x, v.B, v.VWh, v.cdf, v.gamma, v.gthr,
-                                    v.thr_cell, &v.hdr->flags, s, v.reach, v.hdr);
+    return launch_kernel_rows_small(p, V, nullptr, nullptr, p.n_x, p.n_x, v.B, v.VWh, v.ccdf, v.scale, v.gamma,
+                                    v.gthr, v.thr_cell, &v.hdr->flags, s, v.reach, v.hdr);
   cudaError_t e = launch_kernel_eval(p, V, v.occ, &v.hdr->n_occ, 0, p.n_x, v.B, v.VWh, s);
   if (e != cudaSuccess) return e;
-  return launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
-                    &v.hdr->flags, s, v.hdr);
+  return launch_cdf(p, v.VWh, &v.hdr->n_occ, 0, p.n_x, nullptr, v.gamma, v.scale, v.gthr, v.occ, v.thr_cell,
+                    &v.hdr->flags, s, v.hdr, v.ccdf);
 }
 
 // A second stream per device and a fork/join event pair, for running the
@@ -437,7 +447,7 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
                                              (cudaStream_t)stream));
   if (small_window(*p))
     return cuda_status(launch_kernel_rows_small(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, nullptr, nullptr,
-                                                nullptr, nullptr, nullptr, (cudaStream_t)stream));
+                                                nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream));
   return cuda_status(launch_kernel_eval(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, (cudaStream_t)stream));
 }
 
@@ -471,8 +481,8 @@ wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, vo
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_gather_table(*p, table, v.occ, &v.hdr->n_occ, p->n_x, v.VWh, s);
   if (e == cudaSuccess)
-    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, v.cdf, v.gamma, nullptr, v.gthr, v.occ, v.thr_cell,
-                   &v.hdr->flags, s, v.hdr);
+    e = launch_cdf(*p, v.VWh, &v.hdr->n_occ, 0, p->n_x, nullptr, v.gamma, v.scale, v.gthr, v.occ, v.thr_cell,
+                   &v.hdr->flags, s, v.hdr, v.ccdf);
   return cuda_status(e);
 }
 

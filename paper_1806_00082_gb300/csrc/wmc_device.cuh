@@ -80,10 +80,14 @@ __device__ __forceinline__ double scaled_total(long long total, int s) {
 // zero_rows: also write the all-zero CDF of a row without positive entries
 // (the simulation step never reads it: such a row has gamma = 0, so no pair is
 // drawn from it).
+// coarse (optional): the row's coarse CDF, lane l's inclusive sum at coarse[l]
+// (the CDF at the last column of block l), written for rows with positive
+// entries.
 template <class XRes>
 __device__ __forceinline__ void warp_row_cdf(XRes xres, int Q, int r0, int n_M, int log2_nM, int lane,
                                              long long* __restrict__ out, double& gamma_out, int& scale_out,
-                                             long long& total_out, bool zero_rows = true) {
+                                             long long& total_out, bool zero_rows = true,
+                                             long long* __restrict__ coarse = nullptr) {
   const int E = (n_M + 31) >> 5;
   const int k0 = min(lane * E, n_M), k1 = min(k0 + E, n_M);
   const int rr0 = (r0 + k0) % Q;
@@ -114,6 +118,7 @@ __device__ __forceinline__ void warp_row_cdf(XRes xres, int Q, int r0, int n_M, 
     if (lane >= off) incl += u;
   }
   const long long total = __shfl_sync(0xffffffffu, incl, 31);
+  if (coarse) coarse[lane] = incl;
   if (out) {
     long long run = incl - local;
     for (int k = k0, rr = rr0; k < k1; ++k) {
@@ -197,6 +202,32 @@ __device__ __forceinline__ int sample_cdf_row(const long long* __restrict__ c, i
     if (__ldg(c + mid) > target) hi = mid; else lo = mid + 1;
   }
   return lo;
+}
+
+// Index of p' for the 53-bit uniform integer U2 from a coarse CDF: cc[l] is the
+// CDF at the last column of lane block l (E columns each, E = ceil(n_M / 32))
+// and the block's own columns are re-quantised from the kernel row v (scale
+// s), so the result is the smallest k with C[k] > floor(U2 C[n_M - 1] / 2^53)
+// exactly as with the full CDF.  Column k has residue (r0 + k) mod Q.
+__device__ __forceinline__ int sample_coarse_row(const float* __restrict__ v, const long long* __restrict__ cc,
+                                                 int s, int Q, int r0, int n_M, unsigned long long U2) {
+  const unsigned long long Qtot = (unsigned long long)__ldg(cc + kCdfBlocks - 1);
+  const long long target = (long long)((__umul64hi(U2, Qtot) << 11) | ((U2 * Qtot) >> 53));
+  int lo = 0, hi = kCdfBlocks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(cc + mid) > target) hi = mid; else lo = mid + 1;
+  }
+  const int E = (n_M + kCdfBlocks - 1) / kCdfBlocks;
+  const int k0 = min(lo * E, n_M), k1 = min(k0 + E, n_M);
+  long long run = lo ? __ldg(cc + lo - 1) : 0ll;
+  int rr = (r0 + k0) % Q;
+  for (int k = k0; k < k1; ++k) {
+    run += quantise(positive_part(v, Q, rr), s);
+    if (run > target) return k;
+    if (++rr == Q) rr = 0;
+  }
+  return k1 - 1;  // not reached: block lo's sum exceeds the target
 }
 
 // Smallest j in [0, 2^24] with fl32(j 2^-24 + d) >= edge (2^24 if none); the

@@ -36,15 +36,18 @@ constexpr uint32_t kPurposePick = 3u;
 // are cut into work items on a grid of kChunk ids aligned to A = R[i] rounded
 // down to a multiple of 4: item c of cell i holds the ids in
 // [A + c kChunk, A + (c+1) kChunk) that belong to the cell, so every Philox
-// call of a thread (four consecutive ids) stays within one item.  A cell has
-// ceil((T[i] + 3) / kChunk) items (the last may be empty).  A block takes one
-// item at a time, each of its threads kPerThread consecutive ids.
+// call (four consecutive ids) stays within one item.  A cell has
+// ceil((T[i] + 3) / kChunk) items (the last may be empty).  A warp of the
+// particle-step kernel takes one item at a time, each lane a quad-aligned run
+// of at most kChunk / 32 consecutive ids.
 constexpr int kStepThreads = 256;
-constexpr int kStepWorkers = kStepThreads - 32;  // warp 0 of a step block prepares the next work item
-constexpr int kPerThread = 32;
-constexpr int kChunk = kStepWorkers * kPerThread;
+constexpr int kStepWarps = kStepThreads / 32;
+constexpr int kChunk = 4096;
 constexpr int kMaxStepBlocks = 8192;
 constexpr long long kMaxItemsBase = 1ll << 20;   // item descriptors: 2^32 / kChunk + n_x
+// Lane blocks of the coarse momentum CDF: a row's n_M columns are cut into 32
+// blocks of E = ceil(n_M / 32) consecutive columns (block l is [l E, (l+1) E)).
+constexpr int kCdfBlocks = 32;
 
 constexpr unsigned kMagic = 0x574d4331u;  // "WMC1": set by wmc_init
 
@@ -65,13 +68,16 @@ struct DevHeader {
   unsigned int item_ticket;  // next work item of the running step launch
   unsigned int blocks_done;  // step blocks finished (the last one resets both)
   unsigned int rows_by_cell; // 1: the kernel stage wrote its rows at the cell index, 0: at the occupied-list index
-  unsigned int pad[2];
+  unsigned int pair_count;   // pair events queued by the particle-step kernel (reset by the pair kernel)
+  unsigned int pairs_done;   // pair-kernel blocks finished (the last one resets the queue and the ticket)
 };
 
 // Byte offsets of the workspace regions (all 256-aligned).
 struct Layout {
-  size_t header, T, R, IP, reach, occ, row_map, VWh, cdf, gamma, gthr, thr_cell, D, xlo, xhi, items, B, tc, total;
+  size_t header, T, R, IP, reach, occ, row_map, VWh, ccdf, scale, gamma, gthr, thr_cell, D, xlo, xhi, items, pairs, B,
+      tc, total;
   long long max_items;
+  unsigned pair_cap;  // entries of the pair queue
   int h;     // Q / 2
   int Kp;    // contraction length h - 1 padded to a multiple of 32
   int Np;    // output columns h padded to a multiple of 64
@@ -90,7 +96,8 @@ struct View {
   int* occ;                // [n_x] occupied-cell list (ascending)
   int* row_map;            // [n_x] cell -> row of occ, or -1
   float* VWh;              // [n_x][h] kernel half-period rows, by occ row
-  long long* cdf;          // [n_x][n_M] fixed-point CDF by occ row
+  long long* ccdf;         // [n_x][kCdfBlocks] coarse fixed-point CDF by occ row (inclusive block sums)
+  int* scale;              // [n_x] fixed-point scale s of each row
   double* gamma;           // [n_x] gamma by occ row
   unsigned long long* gthr;// [n_x] event threshold by occ row: word < gthr <=> word 2^-32 < gamma dt
   unsigned long long* thr_cell;  // [n_x] the same by cell (0 for cells without a kernel row)
@@ -98,6 +105,7 @@ struct View {
   uint32_t* xlo;           // [n_M] offset word w crosses left iff w < xlo[k]
   uint32_t* xhi;           // [n_M] ... crosses right iff w > xhi[k]
   int2* items;             // [max_items] work items (cell, chunk)
+  uint4* pairs;            // [pair_cap] pair events (id, cell, column, sign < 0) queued by the step
   float* B;                // [Kp][Np] sine matrix S[m][r], m = kk + 1
   void* tc;                // tensor-core operand images of S (BF16, FP16 hi, FP16 lo)
 };
@@ -114,11 +122,28 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
   }
   return c;
+}
+
+// Two Philox4x32-10 evaluations under one key and one key schedule.
+__device__ __forceinline__ void philox4x32_10_x2(uint4& a, uint4& b, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * a.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * a.z;
+    const unsigned long long q0 = (unsigned long long)0xD2511F53u * b.x;
+    const unsigned long long q1 = (unsigned long long)0xCD9E8D57u * b.z;
+    a = make_uint4((uint32_t)(p1 >> 32) ^ a.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ a.w ^ k1, (uint32_t)p0);
+    b = make_uint4((uint32_t)(q1 >> 32) ^ b.y ^ k0, (uint32_t)q1, (uint32_t)(q0 >> 32) ^ b.w ^ k1, (uint32_t)q0);
+  }
 }
 
 // Work items of a cell holding t survivors (an upper bound when its first id
@@ -143,10 +168,10 @@ cudaError_t launch_kernel_eval(const wmc_params& p, const float* V, const int* o
 // outputs may all be null (kernel rows only).
 bool small_window(const wmc_params& p);
 cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
-                                     int n_occ_host, int max_rows, const float* B, float* VWh, long long* cdf,
-                                     double* gamma, unsigned long long* gthr, unsigned long long* thr_cell,
-                                     unsigned int* flags, cudaStream_t s, const unsigned char* reach = nullptr,
-                                     DevHeader* hdr = nullptr);
+                                     int n_occ_host, int max_rows, const float* B, float* VWh, long long* ccdf,
+                                     int* scale, double* gamma, unsigned long long* gthr,
+                                     unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s,
+                                     const unsigned char* reach = nullptr, DevHeader* hdr = nullptr);
 cudaError_t launch_gather_table(const wmc_params& p, const float* table, const int* occ, const int* n_occ_dev,
                                 int max_rows, float* VWh, cudaStream_t s);
 // Tensor-core contraction (BF16, FP16, FP16 hi/lo split).
@@ -155,11 +180,12 @@ cudaError_t launch_init_tc_images(const wmc_params& p, void* images, cudaStream_
 cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V, const int* occ, const int* n_occ_dev,
                                   int n_occ_host, int max_rows, const void* images, float* VWh, unsigned int* flags,
                                   cudaStream_t s);
-// CDF of rows, row-major cdf[row][n_M]; cdf/scale/gthr/thr_cell/flags may be null.
+// CDF of rows: row-major cdf[row][n_M] and/or the coarse form ccdf[row][kCdfBlocks];
+// cdf/ccdf/scale/gthr/thr_cell/flags may be null.
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host,
                        int max_rows, long long* cdf, double* gamma, int* scale, unsigned long long* gthr,
                        const int* occ, unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s,
-                       DevHeader* hdr = nullptr);
+                       DevHeader* hdr = nullptr, long long* ccdf = nullptr);
 cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_in, uint32_t t, int t_from_device,
                         int32_t* hist_out, cudaStream_t s);
 cudaError_t launch_materialize(const wmc_params& p, const View& v, const int32_t* hist, uint32_t t, int32_t* cell,

@@ -148,7 +148,7 @@ __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2
                                                        const int* __restrict__ occ,
                                                        unsigned long long* __restrict__ thr_cell,
                                                        unsigned int* __restrict__ flags, double dt,
-                                                       DevHeader* __restrict__ hdr) {
+                                                       DevHeader* __restrict__ hdr, long long* __restrict__ ccdf) {
   const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_host;
   if (hdr && blockIdx.x == 0 && threadIdx.x == 0) hdr->rows_by_cell = 0u;  // rows follow the occupied list
   const int lane = threadIdx.x & 31;
@@ -161,7 +161,8 @@ __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2
   int sc;
   long long tot;
   warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, cdf ? cdf + (size_t)row * n_M : nullptr, g, sc, tot,
-               gthr == nullptr);  // the step's rows (with thresholds) skip all-zero CDFs
+               gthr == nullptr,  // the step's rows (with thresholds) skip all-zero CDFs
+               ccdf ? ccdf + (size_t)row * kCdfBlocks : nullptr);
   if (lane == 0) {
     gamma[row] = g;
     if (scale) scale[row] = sc;
@@ -292,7 +293,7 @@ template <int C, int R>  // output columns per lane: h <= 32 C
 __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
     const float* __restrict__ V, int n_x, int bc, int Q, int n_M, int log2_nM, const int* __restrict__ occ,
     const int* __restrict__ n_occ_dev, int n_occ_host, const float* __restrict__ B, int Np, float c,
-    float* __restrict__ VWh, long long* __restrict__ cdf, double* __restrict__ gamma,
+    float* __restrict__ VWh, long long* __restrict__ ccdf, int* __restrict__ scale, double* __restrict__ gamma,
     unsigned long long* __restrict__ gthr, unsigned long long* __restrict__ thr_cell, unsigned int* __restrict__ flags,
     double dt, const unsigned char* __restrict__ reach, DevHeader* __restrict__ hdr) {
   // reach != nullptr (one potential, occ == nullptr): row r is cell r, evaluated
@@ -460,9 +461,11 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
         double gm;
         int sc;
         long long tot;
-        warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, cdf + (size_t)row * n_M, gm, sc, tot, false);
+        warp_row_cdf(xres, Q, r0, n_M, log2_nM, lane, nullptr, gm, sc, tot, false,
+                     ccdf + (size_t)row * kCdfBlocks);
         if (lane == 0) {
           gamma[row] = gm;
+          scale[row] = sc;
           const unsigned long long thr = gm > 0.0 ? event_threshold(gm, dt, flags) : 0ull;
           gthr[row] = thr;
           if (thr_cell) thr_cell[occ ? __ldg(occ + row) : row % n_x] = thr;
@@ -481,10 +484,10 @@ static size_t rows_small_smem(int h, int R) {
 }
 
 cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
-                                     int n_occ_host, int max_rows, const float* B, float* VWh, long long* cdf,
-                                     double* gamma, unsigned long long* gthr, unsigned long long* thr_cell,
-                                     unsigned int* flags, cudaStream_t s, const unsigned char* reach,
-                                     DevHeader* hdr) {
+                                     int n_occ_host, int max_rows, const float* B, float* VWh, long long* ccdf,
+                                     int* scale, double* gamma, unsigned long long* gthr,
+                                     unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s,
+                                     const unsigned char* reach, DevHeader* hdr) {
   if (max_rows <= 0) return cudaSuccess;
   const Layout L = layout(p);
   const int h = L.h;
@@ -499,9 +502,9 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
     if (sm > 48 * 1024)                                                                                           \
       cudaFuncSetAttribute(k_kernel_rows_small<CC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);    \
     k_kernel_rows_small<CC, RR><<<blocks, kRowWarps * 32, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, p.n_M, lg, occ, \
-                                                                   n_occ_dev, n_occ_host, B, L.Np, c, VWh, cdf,   \
-                                                                   gamma, gthr, thr_cell, flags, p.dt_s, reach,   \
-                                                                   hdr);                                          \
+                                                                   n_occ_dev, n_occ_host, B, L.Np, c, VWh, ccdf,  \
+                                                                   scale, gamma, gthr, thr_cell, flags, p.dt_s,   \
+                                                                   reach, hdr);                                   \
   } while (0)
   if (R == 4) {
     if (h <= 32) WMC_LAUNCH_ROWS(1, 4);
@@ -519,9 +522,10 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
 
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host, int max_rows,
                        long long* cdf, double* gamma, int* scale, unsigned long long* gthr, const int* occ,
-                       unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s, DevHeader* hdr) {
+                       unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s, DevHeader* hdr,
+                       long long* ccdf) {
   if (max_rows <= 0) return cudaSuccess;
-  if (!cdf && !gthr && !n_rows_dev) {  // gamma (and scale) only
+  if (!cdf && !ccdf && !gthr && !n_rows_dev) {  // gamma (and scale) only
     const int h = p.Q / 2, ca = p.n_M / p.Q, cb = p.n_M - ca * p.Q, r0 = ((-(p.n_M / 2)) % p.Q + p.Q) % p.Q;
     int blocks = (max_rows + kCdfWarps - 1) / kCdfWarps;
     if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
@@ -538,7 +542,7 @@ cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_
   }
   k_cdf<<<(max_rows + kCdfWarps - 1) / kCdfWarps, kCdfWarps * 32, 0, s>>>(
       p.n_M, p.Q, ceil_log2(p.n_M), VWh, n_rows_dev, n_rows_host, cdf, gamma, scale, gthr, occ, thr_cell, flags,
-      p.dt_s, hdr);
+      p.dt_s, hdr, ccdf);
   return cudaGetLastError();
 }
 

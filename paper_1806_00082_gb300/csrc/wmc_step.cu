@@ -6,37 +6,438 @@
 // The survivors are never stored: after annihilation every particle of bucket
 // (i, M) carries the same cell, momentum and sign, and its offset is a Philox
 // draw of its id, so the histogram and the id prefix describe the ensemble
-// exactly.  A block takes work items (up to kChunk ids of one cell, aligned
-// so that each Philox call serves four consecutive ids of one thread) in a
-// fixed round-robin order; while its seven worker warps step the particles of
-// one item, warp 0 loads the next item's descriptor and row prefix into the
-// other of two shared buffers, so that latency is off the critical path.  The
-// block privatises the three histogram rows its particles can land in (i-1, i,
-// i+1) in shared memory and flushes them with one global atomic per non-zero
-// bucket.  A particle moves iff its offset word passes the integer threshold
-// of its momentum column, so a quad of ids inside one bucket costs one Philox
-// call and a handful of compares.
+// exactly.  Two kernels:
+//   k_step   -- each warp takes work items (at most kChunk ids of one cell)
+//               from a ticket counter, stages the cell's row prefix in its own
+//               shared memory (no block barriers), and gives each lane a
+//               quad-aligned run of ids: one Philox call per four ids for the
+//               offsets (REPOS, step t - 1) and one for the pair-creation words
+//               (GEN, step t) under a shared key schedule; a particle moves iff
+//               its offset word passes the integer threshold of its momentum
+//               column.  Parents are counted per bucket and added to the next
+//               histogram with one reduction per bucket run; pair events are
+//               queued in shared memory and appended to a global queue;
+//   k_pairs  -- one thread per queued event: the PICK draw, p' from the coarse
+//               CDF of the cell's kernel row, and the two children.
+// Events beyond the queue's capacity are completed inside k_step (same
+// arithmetic), so any rate is handled.
 #include "wmc_device.cuh"
 
 namespace wmc {
+
+constexpr int kPairQ = 256;  // per-warp event queue (one quad iteration adds at most 128)
 
 struct StepArgs {
   const int32_t* hist_in;
   int32_t* hist_out;
   const unsigned long long* R;
   const int2* items;
-  long long max_items;  // capacity of items
   const int* row_map;
-  const long long* cdf;  // [rows][n_M] fixed-point CDF
+  const float* VWh;           // kernel rows [rows][Q/2]
+  const long long* ccdf;      // coarse CDF [rows][kCdfBlocks]
+  const int* scale;           // fixed-point scale of each row
   const unsigned long long* thr_cell;
   const uint32_t* xlo;
   const uint32_t* xhi;
+  uint4* pairs;               // queued events (id, cell, column, sign < 0)
+  unsigned pair_cap;
   DevHeader* hdr;
-  int n_x, n_M, Q, child_wrap;
+  int n_x, n_M, Q, r0, child_wrap;
   uint32_t sim, k0, k1, t;
   int t_from_device;
-  int rows_by_cell;  // read from the header at kernel start
 };
+
+// p' of the pair created by particle id (column k, sign sgn) in cell c and the
+// children c (k + M', +sgn), (k - M', -sgn); rows follow the cell index or the
+// occupied list as the kernel stage laid them out.
+__device__ __forceinline__ void pair_children(const StepArgs& a, int rows_by_cell, uint32_t id, uint32_t t, int c,
+                                              int k, int sgn, unsigned long long& pairs, unsigned long long& dropped,
+                                              long long& drop_signed) {
+  const int n_M = a.n_M, h = a.Q / 2;
+  const int orow = rows_by_cell ? c : __ldg(a.row_map + c);
+  const uint4 wp = philox4x32_10(make_uint4(id, t, kPurposePick, a.sim), a.k0, a.k1);
+  const unsigned long long U2 = ((unsigned long long)(wp.x >> 5) << 26) | (unsigned long long)(wp.y >> 6);
+  const int kp = sample_coarse_row(a.VWh + (size_t)orow * h, a.ccdf + (size_t)orow * kCdfBlocks,
+                                   __ldg(a.scale + orow), a.Q, a.r0, n_M, U2);
+  ++pairs;
+  const int Mp = kp - n_M / 2;
+  const int kc2[2] = {k + Mp, k - Mp};
+  const int sc2[2] = {sgn, -sgn};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int kc = kc2[q];
+    if (kc < 0 || kc >= n_M) {
+      if (!a.child_wrap) {
+        ++dropped;
+        drop_signed += sc2[q];
+        continue;
+      }
+      kc = ((kc % n_M) + n_M) % n_M;
+    }
+    atomicAdd(a.hist_out + (size_t)c * n_M + kc, sc2[q]);
+  }
+}
+
+// The same with the counters added to the header at once: the step kernel's
+// rare path for events beyond the queue's capacity.
+__device__ __forceinline__ void pair_children_direct(const StepArgs& a, int rows_by_cell, uint32_t id, uint32_t t,
+                                                     int c, int k, int sgn) {
+  unsigned long long pairs = 0, dropped = 0;
+  long long drop_signed = 0;
+  pair_children(a, rows_by_cell, id, t, c, k, sgn, pairs, dropped, drop_signed);
+  atomicAdd(&a.hdr->pairs, pairs);
+  if (dropped) {
+    atomicAdd(&a.hdr->dropped, dropped);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->dropped_signed), (unsigned long long)drop_signed);
+  }
+}
+
+// Sums five per-thread counters over the block into the header (one atomic each).
+__device__ __forceinline__ void block_counters(DevHeader* hdr, unsigned long long pairs, unsigned long long absorbed,
+                                               long long abs_signed, unsigned long long dropped,
+                                               long long drop_signed) {
+  __shared__ unsigned long long s_red[5][kStepWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long vals[5] = {pairs, absorbed, (unsigned long long)abs_signed, dropped,
+                                (unsigned long long)drop_signed};
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    unsigned long long v = vals[j];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) s_red[j][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    unsigned long long v = 0;
+    for (int w = 0; w < kStepWarps; ++w) v += s_red[threadIdx.x][w];
+    if (v) {
+      unsigned long long* dst[5] = {&hdr->pairs, &hdr->absorbed, reinterpret_cast<unsigned long long*>(&hdr->absorbed_signed),
+                                    &hdr->dropped, reinterpret_cast<unsigned long long*>(&hdr->dropped_signed)};
+      atomicAdd(dst[threadIdx.x], v);
+    }
+  }
+}
+
+// Shared memory of a step block: the per-column move test (flip, threshold)
+// of the block, then per warp the row prefix in a padded layout (column k at
+// k + floor(k / E), E = ceil(n_M / 32), so that lane l's block of E columns
+// is contiguous and bank-conflict free), the sign bits and the event queue.
+__host__ __device__ __forceinline__ int step_warp_words(int n_M) {
+  const int E = (n_M + 31) >> 5;
+  return 32 * (E + 1) + 1 + E + kPairQ;
+}
+
+static size_t step_smem(int n_M) {
+  return sizeof(uint32_t) * (2 * (size_t)n_M + (size_t)kStepWarps * step_warp_words(n_M));
+}
+
+__global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
+  extern __shared__ __align__(16) uint32_t smem_step[];
+  __shared__ int s_qn[kStepWarps];
+  const int n_M = a.n_M;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int E = (n_M + 31) >> 5;
+  uint2* s_xm = reinterpret_cast<uint2*>(smem_step);
+  uint32_t* wsm = smem_step + 2 * n_M + wid * step_warp_words(n_M);
+  int* s_pp = reinterpret_cast<int*>(wsm);        // padded row prefix, 32 (E + 1) + 1 ints
+  uint32_t* s_sg = wsm + 32 * (E + 1) + 1;         // sign bits (1: positive), E words
+  uint32_t* s_q = s_sg + E;                        // event queue
+  const int rows_by_cell = (int)a.hdr->rows_by_cell;
+  const uint32_t t = a.t_from_device ? a.hdr->step : a.t;
+  const int n_items = a.hdr->n_items;
+  // move test of column k: moves iff (w ^ flip) > thr, i.e. w > xhi (rightward
+  // drift), w < xlo (leftward, by complementing), never (thr = 2^32 - 1)
+  for (int k = tid; k < n_M; k += kStepThreads) {
+    const uint32_t lo = a.xlo[k], hi = a.xhi[k];
+    s_xm[k] = hi != 0xffffffffu ? make_uint2(0u, hi) : (lo ? make_uint2(0xffffffffu, ~lo) : make_uint2(0u, 0xffffffffu));
+  }
+  if (lane == 0) s_qn[wid] = 0;
+  __syncthreads();
+  const uint32_t magicE = (uint32_t)((0x100000000ull + (unsigned)E - 1ull) / (unsigned)E);  // ceil(2^32 / E)
+  auto pidx = [&](int k) { return k + (int)__umulhi((uint32_t)k, magicE); };
+
+  int cur_i = -1;
+  uint32_t base = 0u;
+  unsigned long long thr_m = 0, thr_0 = 0, thr_p = 0;
+
+  int item = 0;
+  if (lane == 0) item = (int)atomicAdd(&a.hdr->item_ticket, 1u);
+  item = __shfl_sync(0xffffffffu, item, 0);
+  while (item < n_items) {
+    int nxt = 0;
+    if (lane == 0) nxt = (int)atomicAdd(&a.hdr->item_ticket, 1u);  // consumed at the end of this item
+    const int2 it = __ldg(a.items + item);
+    const int i = it.x, ch = it.y;
+    if (i != cur_i) {
+      // stage the row: |n| into the padded buffer, sign bits, then the
+      // exclusive prefix in place (lane l over its block of E columns)
+      const int32_t* row = a.hist_in + (size_t)i * n_M;
+      for (int k0 = 0; k0 < n_M; k0 += 32) {
+        const int k = k0 + lane;
+        const int n = k < n_M ? __ldg(row + k) : 0;
+        if (k < n_M) s_pp[pidx(k)] = n < 0 ? -n : n;
+        const uint32_t b = __ballot_sync(0xffffffffu, n > 0);
+        if (lane == 0) s_sg[k0 >> 5] = b;
+      }
+      __syncwarp();
+      const int kb0 = min(lane * E, n_M), kb1 = min(kb0 + E, n_M);
+      int* blk = s_pp + lane * (E + 1);
+      int local = 0;
+      for (int j = 0; j < kb1 - kb0; ++j) local += blk[j];
+      int incl = local;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+      }
+      int run = incl - local;
+      for (int j = 0; j < kb1 - kb0; ++j) {
+        const int v = blk[j];
+        blk[j] = run;
+        run += v;
+      }
+      __syncwarp();
+      if (lane == 31) s_pp[pidx(n_M)] = incl;
+      base = (uint32_t)__ldg(a.R + i);
+      thr_m = i > 0 ? __ldg(a.thr_cell + i - 1) : 0ull;
+      thr_0 = __ldg(a.thr_cell + i);
+      thr_p = i + 1 < a.n_x ? __ldg(a.thr_cell + i + 1) : 0ull;
+      cur_i = i;
+      __syncwarp();
+    }
+    const bool need_gen = (thr_m | thr_0 | thr_p) != 0ull;
+    const uint32_t Ti = (uint32_t)s_pp[pidx(n_M)];
+    // the item is [item0, item1) of the quad-aligned id range of the cell; each
+    // lane takes a quad-aligned span of it
+    const unsigned long long A = base & ~3u;
+    const unsigned long long row_end = (unsigned long long)base + Ti;
+    const unsigned long long item0 = A + (unsigned long long)ch * kChunk;
+    const unsigned long long item1 = item0 + kChunk < row_end ? item0 + kChunk : row_end;
+    const uint32_t len = item1 > item0 ? (uint32_t)(item1 - item0) : 0u;
+    const uint32_t span = ((len + 127u) >> 7) << 2;
+    const unsigned long long lo64 = item0 + (unsigned long long)lane * span;
+    const unsigned long long g0_64 = lo64 > base ? lo64 : base;
+    const unsigned long long g1_64 = lo64 + span < item1 ? lo64 + span : item1;
+    const bool has = g0_64 < g1_64;
+    const uint32_t g0 = has ? (uint32_t)g0_64 : 0u, g1 = has ? (uint32_t)g1_64 : 0u;
+    const uint32_t i0 = (uint32_t)item0;
+
+    // bucket state
+    int k = 0, sgn = 1, dir = 0, tgt = i;
+    uint32_t end = 0u, flip = 0u, mthr = 0xffffffffu, rej = 0u;
+    unsigned long long e_st = 0ull, e_mv = 0ull;
+    bool full = false;
+    int n_st = 0, n_mv = 0;
+    auto load_bucket = [&]() {
+      end = base + (uint32_t)s_pp[pidx(k + 1)];
+      sgn = ((s_sg[k >> 5] >> (k & 31)) & 1u) ? 1 : -1;
+      const uint2 xm = s_xm[k];
+      flip = xm.x;
+      mthr = xm.y;
+      dir = flip ? -1 : (mthr != 0xffffffffu ? 1 : 0);
+      tgt = i + dir;
+      e_st = thr_0;
+      e_mv = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
+      const unsigned long long emax = e_st > e_mv ? e_st : e_mv;
+      full = emax >> 32 != 0ull;
+      rej = full ? 0xffffffffu : (uint32_t)emax;
+    };
+    auto flush_bucket = [&]() {
+      if (n_st) atomicAdd(a.hist_out + (size_t)i * n_M + k, sgn * n_st);
+      if (n_mv) {
+        if ((unsigned)tgt < (unsigned)a.n_x) {
+          atomicAdd(a.hist_out + (size_t)tgt * n_M + k, sgn * n_mv);
+        } else {  // left the domain (edge cells only): counted at once
+          atomicAdd(&a.hdr->absorbed, (unsigned long long)n_mv);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->absorbed_signed),
+                    (unsigned long long)(long long)(sgn * n_mv));
+        }
+      }
+      n_st = n_mv = 0;
+    };
+    auto push = [&](uint32_t id, int mv) {
+      const int pos = atomicAdd(&s_qn[wid], 1);
+      if (pos < kPairQ)  // always (the queue is drained whenever it could fill within one quad iteration)
+        s_q[pos] = (id - i0) | ((uint32_t)k << 12) | ((uint32_t)(mv ? dir + 1 : 1) << 24) | (sgn < 0 ? 1u << 26 : 0u);
+    };
+    // queued events of this item to the global queue (warp-collective)
+    auto flush_queue = [&]() {
+      __syncwarp();
+      const int n = min(s_qn[wid], kPairQ);
+      if (n) {
+        unsigned qb = 0u;
+        if (lane == 0) qb = atomicAdd(&a.hdr->pair_count, (unsigned)n);
+        qb = __shfl_sync(0xffffffffu, qb, 0);
+        for (int e = lane; e < n; e += 32) {
+          const uint32_t q = s_q[e];
+          const uint32_t id = i0 + (q & 4095u);
+          const int kk = (int)((q >> 12) & 4095u), c = i - 1 + (int)((q >> 24) & 3u);
+          const int sg = (q >> 26) & 1u ? -1 : 1;
+          const unsigned slot = qb + (unsigned)e;
+          if (slot >= qb && slot < a.pair_cap)
+            a.pairs[slot] = make_uint4(id, (uint32_t)c, (uint32_t)kk, sg < 0 ? 1u : 0u);
+          else
+            pair_children_direct(a, rows_by_cell, id, t, c, kk, sg);
+        }
+        __syncwarp();
+        if (lane == 0) s_qn[wid] = 0;
+      }
+      __syncwarp();
+    };
+
+    if (has) {
+      // largest k with prefix(k) <= g0 - base: the bucket of the lane's first id
+      const int lid = (int)(g0 - base);
+      int lo = 0, hi = n_M;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_pp[pidx(mid)] <= lid) lo = mid; else hi = mid;
+      }
+      k = lo;
+      load_bucket();
+    }
+    const int nq = (int)(span >> 2);
+    const uint32_t q_first = (uint32_t)(lo64 >> 2);
+#pragma unroll 1
+    for (int jq = 0; jq < nq; ++jq) {
+      const uint32_t q = q_first + (uint32_t)jq;
+      const uint32_t qa = q << 2;
+      if (has && qa < g1 && qa + 4u > g0) {
+        uint4 wr = make_uint4(q, t - 1u, kPurposeRepos, a.sim);
+        uint4 wg = make_uint4(q, t, kPurposeGen, a.sim);
+        if (need_gen) philox4x32_10_x2(wr, wg, a.k0, a.k1);
+        else wr = philox4x32_10(wr, a.k0, a.k1);
+        if (qa >= g0 && qa + 4u <= g1 && qa + 4u <= end) {
+          // four consecutive ids of bucket k
+          const int m0 = (wr.x ^ flip) > mthr, m1 = (wr.y ^ flip) > mthr;
+          const int m2 = (wr.z ^ flip) > mthr, m3 = (wr.w ^ flip) > mthr;
+          const int nm = m0 + m1 + m2 + m3;
+          n_mv += nm;
+          n_st += 4 - nm;
+          if (need_gen) {
+            const uint32_t umin = min(min(wg.x, wg.y), min(wg.z, wg.w));
+            if (umin < rej || full) {
+              if ((unsigned long long)wg.x < (m0 ? e_mv : e_st)) push(qa, m0);
+              if ((unsigned long long)wg.y < (m1 ? e_mv : e_st)) push(qa + 1u, m1);
+              if ((unsigned long long)wg.z < (m2 ? e_mv : e_st)) push(qa + 2u, m2);
+              if ((unsigned long long)wg.w < (m3 ? e_mv : e_st)) push(qa + 3u, m3);
+            }
+          }
+        } else {
+          const uint32_t w4[4] = {wr.x, wr.y, wr.z, wr.w};
+          const uint32_t u4[4] = {wg.x, wg.y, wg.z, wg.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t id = qa + (uint32_t)j;
+            if (id < g0 || id >= g1) continue;
+            if (id >= end) {  // next non-empty bucket
+              flush_bucket();
+              do { ++k; } while (k < n_M - 1 && base + (uint32_t)s_pp[pidx(k + 1)] <= id);
+              load_bucket();
+            }
+            const int mv = (w4[j] ^ flip) > mthr;
+            n_mv += mv;
+            n_st += 1 - mv;
+            if (need_gen && (unsigned long long)u4[j] < (mv ? e_mv : e_st)) push(id, mv);
+          }
+        }
+      }
+      __syncwarp();
+      if (s_qn[wid] > kPairQ - 128) flush_queue();
+    }
+    if (has) flush_bucket();
+    flush_queue();
+    item = __shfl_sync(0xffffffffu, nxt, 0);
+  }
+  if (blockIdx.x == 0 && tid == 0 && n_items > 0) atomicAdd(&a.hdr->particle_steps, a.hdr->population);
+}
+
+// The queued pair events of the step: one thread each.  The last block to
+// finish resets the queue and the work-item ticket for the next step.
+__global__ __launch_bounds__(kStepThreads) void k_pairs(StepArgs a) {
+  const int rows_by_cell = (int)a.hdr->rows_by_cell;
+  const uint32_t t = a.t_from_device ? a.hdr->step : a.t;
+  const unsigned cnt = a.hdr->pair_count;
+  const unsigned n = cnt < a.pair_cap ? cnt : a.pair_cap;
+  unsigned long long pairs = 0, dropped = 0;
+  long long drop_signed = 0;
+  for (unsigned e = blockIdx.x * kStepThreads + threadIdx.x; e < n; e += gridDim.x * kStepThreads) {
+    const uint4 ev = a.pairs[e];
+    pair_children(a, rows_by_cell, ev.x, t, (int)ev.y, (int)ev.z, ev.w ? -1 : 1, pairs, dropped, drop_signed);
+  }
+  block_counters(a.hdr, pairs, 0ull, 0ll, dropped, drop_signed);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&a.hdr->pairs_done, 1u) == gridDim.x - 1u) {
+      a.hdr->pair_count = 0u;
+      a.hdr->item_ticket = 0u;
+      a.hdr->pairs_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+int step_grid(int n_M) {
+  static int cached_nM[8] = {0};
+  static int cached_grid[8] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = dev & 7;
+  if (cached_nM[slot] == n_M && cached_grid[slot] > 0) return cached_grid[slot];
+  int per_sm = 0;
+  const size_t sm = step_smem(n_M);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, kStepThreads, sm);
+  if (per_sm < 1) per_sm = 1;
+  int g = per_sm * num_sms();
+  if (g > kMaxStepBlocks) g = kMaxStepBlocks;
+  cached_nM[slot] = n_M;
+  cached_grid[slot] = g;
+  return g;
+}
+
+void prepare_step(const wmc_params& p) { (void)step_grid(p.n_M); }
+
+cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_in, uint32_t t, int t_from_device,
+                        int32_t* hist_out, cudaStream_t s) {
+  const Layout L = layout(p);
+  StepArgs a;
+  a.hist_in = hist_in;
+  a.hist_out = hist_out;
+  a.R = v.R;
+  a.items = v.items;
+  a.row_map = v.row_map;
+  a.VWh = v.VWh;
+  a.ccdf = v.ccdf;
+  a.scale = v.scale;
+  a.thr_cell = v.thr_cell;
+  a.xlo = v.xlo;
+  a.xhi = v.xhi;
+  a.pairs = v.pairs;
+  a.pair_cap = L.pair_cap;
+  a.hdr = v.hdr;
+  a.n_x = p.n_x;
+  a.n_M = p.n_M;
+  a.Q = p.Q;
+  a.r0 = ((-(p.n_M / 2)) % p.Q + p.Q) % p.Q;
+  a.child_wrap = p.child_wrap;
+  a.sim = p.sim;
+  a.k0 = (uint32_t)(p.seed & 0xffffffffu);
+  a.k1 = (uint32_t)(p.seed >> 32);
+  a.t = t;
+  a.t_from_device = t_from_device;
+  const int grid = step_grid(p.n_M);
+  cudaError_t e = step_timing_record(s, false);
+  if (e != cudaSuccess) return e;
+  k_step<<<grid, kStepThreads, step_smem(p.n_M), s>>>(a);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = step_timing_record(s, true);
+  if (e != cudaSuccess) return e;
+  k_pairs<<<4 * num_sms(), kStepThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
 
 // Loads the signed counts of cell i into s_n and their exclusive prefix of
 // |n| into s_pre[0..n_M] (s_pre[n_M] = survivors of the cell), block-wide.
@@ -79,300 +480,6 @@ __device__ __forceinline__ void load_row_prefix(const int32_t* __restrict__ hist
   if (tid == kStepThreads - 1) s_pre[n_M] = s_wsum[kStepThreads / 32 - 1];
 }
 
-__device__ __forceinline__ int sample_momentum(const StepArgs& a, int orow, unsigned long long U2) {
-  return sample_cdf_row(a.cdf + (size_t)orow * a.n_M, a.n_M, U2);
-}
-
-// A pair created by particle id (column k, sign sgn) that lands in cell c = i - 1 + d:
-// p' from the PICK draw, children into the block's private row d.
-__device__ __forceinline__ void create_pair(const StepArgs& a, uint32_t id, uint32_t t, int i, int d, int k,
-                                            int sgn, int* s_acc, unsigned long long& pairs,
-                                            unsigned long long& dropped, long long& drop_signed) {
-  const int n_M = a.n_M;
-  const int orow = a.rows_by_cell ? i - 1 + d : __ldg(a.row_map + i - 1 + d);
-  const uint4 wp = philox4x32_10(make_uint4(id, t, kPurposePick, a.sim), a.k0, a.k1);
-  const unsigned long long U2 = ((unsigned long long)(wp.x >> 5) << 26) | (unsigned long long)(wp.y >> 6);
-  const int kp = sample_momentum(a, orow, U2);
-  ++pairs;
-  const int Mp = kp - n_M / 2;
-  const int kc2[2] = {k + Mp, k - Mp};
-  const int sc2[2] = {sgn, -sgn};
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    int kc = kc2[q];
-    if (kc < 0 || kc >= n_M) {
-      if (!a.child_wrap) {
-        ++dropped;
-        drop_signed += sc2[q];
-        continue;
-      }
-      kc = ((kc % n_M) + n_M) % n_M;
-    }
-    atomicAdd(&s_acc[d * n_M + kc], sc2[q]);
-  }
-}
-
-// Descriptor of a work item, prepared by warp 0 one item ahead.
-struct ItemMeta {
-  unsigned long long thr_m, thr_0, thr_p;  // event thresholds of cells i-1, i, i+1
-  uint32_t base;                           // first id of cell i
-  int item, i, ch;
-};
-
-__global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
-  extern __shared__ int smem[];
-  a.rows_by_cell = (int)a.hdr->rows_by_cell;  // how the kernel stage laid out its CDF rows
-  const int n_M = a.n_M;
-  int* s_pre2 = smem;                    // 2 x (n_M + 1): prefix buffers
-  int* s_n2 = s_pre2 + 2 * (n_M + 1);    // 2 x n_M: signed count buffers
-  int* s_acc = s_n2 + 2 * n_M;           // 3 n_M: rows i-1, i, i+1
-  uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_acc + 3 * n_M);  // n_M
-  uint32_t* s_hi = s_lo + n_M;                                     // n_M
-  __shared__ ItemMeta s_meta[2];
-  __shared__ unsigned long long s_red[5][kStepThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t t = a.t_from_device ? a.hdr->step : a.t;
-  const int n_items = a.hdr->n_items;
-  for (int k = tid; k < n_M; k += kStepThreads) {
-    s_lo[k] = a.xlo[k];
-    s_hi[k] = a.xhi[k];
-  }
-  for (int q = tid; q < 3 * n_M; q += kStepThreads) s_acc[q] = 0;
-
-  // by warp 0: descriptor and row prefix of `item` into buffer `buf`
-  auto prepare = [&](int item, int buf) {
-    ItemMeta m;
-    m.item = item;
-    m.i = m.ch = 0;
-    m.base = 0u;
-    m.thr_m = m.thr_0 = m.thr_p = 0ull;
-    // the descriptor load goes out before the item count is known (any index
-    // below the capacity is readable; the count decides whether it is used)
-    int2 it = make_int2(0, 0);
-    if (item < a.max_items) it = __ldg(a.items + item);
-    if (item < n_items) {
-      m.i = it.x;
-      m.ch = it.y;
-      m.base = (uint32_t)__ldg(a.R + m.i);
-      m.thr_m = m.i > 0 ? __ldg(a.thr_cell + m.i - 1) : 0ull;
-      m.thr_0 = __ldg(a.thr_cell + m.i);
-      m.thr_p = m.i + 1 < a.n_x ? __ldg(a.thr_cell + m.i + 1) : 0ull;
-      warp_row_prefix(a.hist_in, m.i, n_M, s_n2 + buf * n_M, s_pre2 + buf * (n_M + 1), lane);
-    }
-    if (lane == 0) s_meta[buf] = m;
-  };
-  if (wid == 0) prepare(blockIdx.x, 0);
-
-  unsigned long long pairs = 0, absorbed = 0, dropped = 0;
-  long long abs_signed = 0, drop_signed = 0;
-
-  for (int round = 0;; ++round) {
-    __syncthreads();  // this item's buffer is ready; the previous item is flushed
-    const int buf = round & 1;
-    const ItemMeta m = s_meta[buf];
-    if (m.item >= n_items) break;
-    if (wid == 0) {
-      prepare(m.item + (int)gridDim.x, buf ^ 1);
-    } else {
-      const int* s_pre = s_pre2 + buf * (n_M + 1);
-      const int* s_n = s_n2 + buf * n_M;
-      const int i = m.i, ch = m.ch;
-      const uint32_t base = m.base;
-      const unsigned long long thr_m = m.thr_m, thr_0 = m.thr_0, thr_p = m.thr_p;
-      const int w = tid - 32;  // worker index
-      const uint32_t Ti = (uint32_t)s_pre[n_M];
-      // the item is [item0, item1) of the quad-aligned id range of the cell; its
-      // ids are spread over all workers in quad-aligned spans (a cell's last,
-      // partial item then keeps every worker busy too)
-      const unsigned long long A = base & ~3u;
-      const unsigned long long row_end = (unsigned long long)base + Ti;
-      const unsigned long long item0 = A + (unsigned long long)ch * kChunk;
-      const unsigned long long item1 = item0 + kChunk < row_end ? item0 + kChunk : row_end;
-      const unsigned long long len = item1 > item0 ? item1 - item0 : 0ull;
-      const unsigned long long span = ((len + 4ull * kStepWorkers - 1) / (4ull * kStepWorkers)) * 4ull;
-      const unsigned long long lo64 = item0 + (unsigned long long)w * span;
-      const unsigned long long g0_64 = lo64 > base ? lo64 : base;
-      const unsigned long long g1_64 = lo64 + span < item1 ? lo64 + span : item1;
-      // ids stay below 2^32 (the plan guarantees it); compare in 64 bits first
-      const uint32_t g0 = g0_64 < g1_64 ? (uint32_t)g0_64 : 0u;
-      const uint32_t g1 = g0_64 < g1_64 ? (uint32_t)g1_64 : 0u;
-      const bool need_gen = (thr_m | thr_0 | thr_p) != 0ull;
-
-      int k = 0, n_tot = 0, n_mov = 0, sgn = 1, dir = 0;
-      if (g0 < g1) {
-        k = bucket_of(s_pre, n_M, (int)(g0 - base));
-        uint32_t end_g = base + (uint32_t)s_pre[k + 1];
-        sgn = s_n[k] > 0 ? 1 : -1;
-        uint32_t lo = s_lo[k], hi = s_hi[k];
-        dir = drift_dir(lo, hi);
-        unsigned long long thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
-        for (uint32_t q = g0 >> 2; q <= (g1 - 1u) >> 2; ++q) {
-          const uint32_t qa = q << 2;
-          const uint4 wr = philox4x32_10(make_uint4(q, t - 1u, kPurposeRepos, a.sim), a.k0, a.k1);
-          uint4 wg = make_uint4(0u, 0u, 0u, 0u);
-          if (need_gen) wg = philox4x32_10(make_uint4(q, t, kPurposeGen, a.sim), a.k0, a.k1);
-          if (qa >= g0 && qa + 3u < g1 && qa + 3u < end_g) {
-            // four consecutive ids of bucket k
-            const int m0 = (wr.x > hi) | (wr.x < lo), m1 = (wr.y > hi) | (wr.y < lo);
-            const int m2 = (wr.z > hi) | (wr.z < lo), m3 = (wr.w > hi) | (wr.w < lo);
-            n_mov += m0 + m1 + m2 + m3;
-            n_tot += 4;
-            if (need_gen) {
-              const int mv[4] = {m0, m1, m2, m3};
-              const uint32_t u[4] = {wg.x, wg.y, wg.z, wg.w};
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                if ((unsigned long long)u[j] < (mv[j] ? thr_move : thr_0))
-                  create_pair(a, qa + (uint32_t)j, t, i, mv[j] ? dir + 1 : 1, k, sgn, s_acc, pairs, dropped,
-                              drop_signed);
-              }
-            }
-            continue;
-          }
-          const uint32_t w4[4] = {wr.x, wr.y, wr.z, wr.w};
-          const uint32_t u4[4] = {wg.x, wg.y, wg.z, wg.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint32_t id = qa + (uint32_t)j;
-            if (id < g0 || id >= g1) continue;
-            if (id >= end_g) {  // next non-empty bucket
-              const int stay = n_tot - n_mov;
-              if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
-              if (n_mov) {
-                if ((unsigned)(i + dir) < (unsigned)a.n_x) {
-                  atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * n_mov);
-                } else {
-                  absorbed += n_mov;
-                  abs_signed += sgn * n_mov;
-                }
-              }
-              n_tot = n_mov = 0;
-              do { ++k; } while (base + (uint32_t)s_pre[k + 1] <= id);
-              end_g = base + (uint32_t)s_pre[k + 1];
-              sgn = s_n[k] > 0 ? 1 : -1;
-              lo = s_lo[k];
-              hi = s_hi[k];
-              dir = drift_dir(lo, hi);
-              thr_move = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
-            }
-            const int mv = (w4[j] > hi) | (w4[j] < lo);
-            n_mov += mv;
-            ++n_tot;
-            if (need_gen && (unsigned long long)u4[j] < (mv ? thr_move : thr_0))
-              create_pair(a, id, t, i, mv ? dir + 1 : 1, k, sgn, s_acc, pairs, dropped, drop_signed);
-          }
-        }
-      }
-      // last bucket of each thread: lanes holding the same bucket combine first
-      const int key = n_tot ? k : -1;
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      const int stay = __reduce_add_sync(peers, n_tot - n_mov);
-      const int mov = __reduce_add_sync(peers, n_mov);
-      if (key >= 0 && lane == __ffs(peers) - 1) {
-        if (stay) atomicAdd(&s_acc[n_M + k], sgn * stay);
-        if (mov) {
-          if ((unsigned)(i + dir) < (unsigned)a.n_x) {
-            atomicAdd(&s_acc[(dir + 1) * n_M + k], sgn * mov);
-          } else {
-            absorbed += mov;
-            abs_signed += sgn * mov;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    // flush the private rows (and clear them for the next item)
-    for (int q = tid; q < 3 * n_M; q += kStepThreads) {
-      const int v = s_acc[q];
-      if (v) {
-        s_acc[q] = 0;
-        const int d = q / n_M, kc = q - d * n_M;
-        atomicAdd(a.hist_out + (size_t)(m.i - 1 + d) * n_M + kc, v);
-      }
-    }
-  }
-
-  // block totals of the counters, one atomic each
-  unsigned long long vals[5] = {pairs, absorbed, (unsigned long long)abs_signed, dropped,
-                                (unsigned long long)drop_signed};
-#pragma unroll
-  for (int j = 0; j < 5; ++j) {
-    unsigned long long v = vals[j];
-#pragma unroll
-    for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0) s_red[j][wid] = v;
-  }
-  __syncthreads();
-  if (tid < 5) {
-    unsigned long long v = 0;
-    for (int w = 0; w < kStepThreads / 32; ++w) v += s_red[tid][w];
-    if (v) {
-      unsigned long long* dst[5] = {&a.hdr->pairs, &a.hdr->absorbed,
-                                    reinterpret_cast<unsigned long long*>(&a.hdr->absorbed_signed), &a.hdr->dropped,
-                                    reinterpret_cast<unsigned long long*>(&a.hdr->dropped_signed)};
-      atomicAdd(dst[tid], v);
-    }
-  }
-  if (blockIdx.x == 0 && tid == 0 && n_items > 0) atomicAdd(&a.hdr->particle_steps, a.hdr->population);
-}
-
-static size_t step_smem(int n_M) {
-  return sizeof(int) * (size_t)(2 * (n_M + 1) + 2 * n_M + 3 * n_M) + 2 * sizeof(uint32_t) * n_M;
-}
-
-int step_grid(int n_M) {
-  static int cached_nM[8] = {0};
-  static int cached_grid[8] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const int slot = dev & 7;
-  if (cached_nM[slot] == n_M && cached_grid[slot] > 0) return cached_grid[slot];
-  int per_sm = 0;
-  const size_t sm = step_smem(n_M);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, kStepThreads, sm);
-  if (per_sm < 1) per_sm = 1;
-  int g = per_sm * num_sms();
-  if (g > kMaxStepBlocks) g = kMaxStepBlocks;
-  cached_nM[slot] = n_M;
-  cached_grid[slot] = g;
-  return g;
-}
-
-void prepare_step(const wmc_params& p) { (void)step_grid(p.n_M); }
-
-cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_in, uint32_t t, int t_from_device,
-                        int32_t* hist_out, cudaStream_t s) {
-  StepArgs a;
-  a.hist_in = hist_in;
-  a.hist_out = hist_out;
-  a.R = v.R;
-  a.items = v.items;
-  a.max_items = layout(p).max_items;
-  a.row_map = v.row_map;
-  a.cdf = v.cdf;
-  a.thr_cell = v.thr_cell;
-  a.xlo = v.xlo;
-  a.xhi = v.xhi;
-  a.hdr = v.hdr;
-  a.n_x = p.n_x;
-  a.n_M = p.n_M;
-  a.Q = p.Q;
-  a.child_wrap = p.child_wrap;
-  a.sim = p.sim;
-  a.k0 = (uint32_t)(p.seed & 0xffffffffu);
-  a.k1 = (uint32_t)(p.seed >> 32);
-  a.t = t;
-  a.t_from_device = t_from_device;
-  a.rows_by_cell = 0;
-  const int grid = step_grid(p.n_M);
-  cudaError_t e = step_timing_record(s, false);
-  if (e != cudaSuccess) return e;
-  k_step<<<grid, kStepThreads, step_smem(p.n_M), s>>>(a);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? step_timing_record(s, true) : e;
-}
-
 // ---------------------------------------------------------------- explicit survivors
 __global__ __launch_bounds__(kStepThreads) void k_materialize(const int32_t* __restrict__ hist,
                                                               const unsigned long long* __restrict__ R,
@@ -409,8 +516,9 @@ __global__ __launch_bounds__(kStepThreads) void k_materialize(const int32_t* __r
     __syncthreads();
     const int Ti = s_pre[n_M];
     const uint32_t base = (uint32_t)__ldg(R + i);
-    const int lo = chunk * kChunk + tid * kPerThread;  // ids [chunk kChunk, (chunk + 1) kChunk) of the row
-    const int hi = tid < kStepWorkers ? min(lo + kPerThread, Ti) : lo;
+    constexpr int kPer = kChunk / kStepThreads;
+    const int lo = chunk * kChunk + tid * kPer;  // ids [chunk kChunk, (chunk + 1) kChunk) of the row
+    const int hi = min(lo + kPer, Ti);
     if (lo < hi) {
       int k = bucket_of(s_pre, n_M, lo);
       for (int lid = lo; lid < hi; ++lid) {

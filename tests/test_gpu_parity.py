@@ -189,6 +189,15 @@ def test_steps_bit_exact_packet_on_barrier(wmc):
     assert st[oracle.ST_PAIRS] > 50000
 
 
+def test_steps_bit_exact_pair_queue_overflow(wmc):
+    """About 1.6e5 pair events per step in a 6400-bucket histogram: more than
+    the step's pair queue holds (2^16 entries at this size), so events are
+    completed both by the pair kernel and inside the step kernel."""
+    wl = wi.BARRIER_100.replace(packet=wi.Packet(50e-9, 4e-9, 0.1, 3_000_000))
+    _, c, st = _compare_steps(wmc, wl, wi.initial_histogram(wl), 1, 2)
+    assert st[oracle.ST_PAIRS] > 2 * 70_000
+
+
 def test_steps_bit_exact_wrap_and_clamp(wmc):
     wl = wi.BARRIER_100.replace(child_wrap=1, bc_potential=1, sim=7, seed=123456789012345,
                                 packet=wi.Packet(45e-9, 6e-9, 0.12, 50_000))
