@@ -62,6 +62,7 @@ Layout layout(const wmc_params& p) {
   L.pairs = o; o = align256(o + sizeof(uint4) * (size_t)L.pair_cap);
   L.B = o; o = align256(o + sizeof(float) * (size_t)L.Kp * (size_t)L.Np);
   L.tc = o; o = align256(o + tc_images_bytes(p));
+  L.plan = o; o = align256(o + sizeof(PlanStatus) * ((nx + kPlanCells - 1) / kPlanCells));
   L.total = o;
   return L;
 }
@@ -90,6 +91,7 @@ View view(const wmc_params& p, void* ws) {
   v.pairs = reinterpret_cast<uint4*>(b + L.pairs);
   v.B = reinterpret_cast<float*>(b + L.B);
   v.tc = b + L.tc;
+  v.plan = reinterpret_cast<PlanStatus*>(b + L.plan);
   return v;
 }
 

@@ -208,9 +208,61 @@ __device__ __forceinline__ int sample_cdf_row(const long long* __restrict__ c, i
 // CDF at the last column of lane block l (E columns each, E = ceil(n_M / 32))
 // and the block's own columns are re-quantised from the kernel row v (scale
 // s), so the result is the smallest k with C[k] > floor(U2 C[n_M - 1] / 2^53)
-// exactly as with the full CDF.  Column k has residue (r0 + k) mod Q.
+// exactly as with the full CDF.  Column k has residue (r0 + k) mod Q.  Loads
+// go out in small independent groups: the four segment ends of the 32 block
+// sums, the eight sums of one segment, then the block's columns eight at a
+// time.
 __device__ __forceinline__ int sample_coarse_row(const float* __restrict__ v, const long long* __restrict__ cc,
                                                  int s, int Q, int r0, int n_M, unsigned long long U2) {
+  const long long e0 = __ldg(cc + 7), e1 = __ldg(cc + 15), e2 = __ldg(cc + 23), e3 = __ldg(cc + 31);
+  const unsigned long long Qtot = (unsigned long long)e3;
+  const long long target = (long long)((__umul64hi(U2, Qtot) << 11) | ((U2 * Qtot) >> 53));
+  const int seg = (e0 <= target) + (e1 <= target) + (e2 <= target);  // e3 > target always
+  const longlong2* cs = reinterpret_cast<const longlong2*>(cc + 8 * seg);
+  long long c8[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const longlong2 pr = __ldg(cs + j);
+    c8[2 * j] = pr.x;
+    c8[2 * j + 1] = pr.y;
+  }
+  int blk = 8 * seg;
+  long long run = seg == 0 ? 0ll : (seg == 1 ? e0 : (seg == 2 ? e1 : e2));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool below = c8[j] <= target;
+    blk += below;
+    run = below ? c8[j] : run;  // the CDF before block blk
+  }
+  const int E = (n_M + kCdfBlocks - 1) / kCdfBlocks;
+  const int k0 = min(blk * E, n_M), k1 = min(k0 + E, n_M);
+  const int h = Q / 2;
+  int rr = (r0 + k0) % Q;
+  for (int kb = k0; kb < k1; kb += 8) {
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      int r = rr + e;
+      r = r >= Q ? r - Q : r;
+      float val = 0.f;
+      if (kb + e < k1 && r != 0 && r != h) val = r < h ? __ldg(v + r) : -__ldg(v + (Q - r));
+      x[e] = val > 0.f ? val : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      run += quantise(x[e], s);
+      if (kb + e < k1 && run > target) return kb + e;
+    }
+    rr += 8;
+    rr = rr >= Q ? rr - Q : rr;
+  }
+  return k1 - 1;  // not reached: block blk's sum exceeds the target
+}
+
+// The same draw with sequential loads and few registers (for the rare calls
+// from inside the particle-step kernel).
+__device__ __forceinline__ int sample_coarse_row_seq(const float* __restrict__ v, const long long* __restrict__ cc,
+                                                     int s, int Q, int r0, int n_M, unsigned long long U2) {
   const unsigned long long Qtot = (unsigned long long)__ldg(cc + kCdfBlocks - 1);
   const long long target = (long long)((__umul64hi(U2, Qtot) << 11) | ((U2 * Qtot) >> 53));
   int lo = 0, hi = kCdfBlocks - 1;
@@ -227,7 +279,7 @@ __device__ __forceinline__ int sample_coarse_row(const float* __restrict__ v, co
     if (run > target) return k;
     if (++rr == Q) rr = 0;
   }
-  return k1 - 1;  // not reached: block lo's sum exceeds the target
+  return k1 - 1;
 }
 
 // Smallest j in [0, 2^24] with fl32(j 2^-24 + d) >= edge (2^24 if none); the

@@ -48,6 +48,8 @@ constexpr long long kMaxItemsBase = 1ll << 20;   // item descriptors: 2^32 / kCh
 // Lane blocks of the coarse momentum CDF: a row's n_M columns are cut into 32
 // blocks of E = ceil(n_M / 32) consecutive columns (block l is [l E, (l+1) E)).
 constexpr int kCdfBlocks = 32;
+// Cells per block of the plan's scan.
+constexpr int kPlanCells = 1024;
 
 constexpr unsigned kMagic = 0x574d4331u;  // "WMC1": set by wmc_init
 
@@ -70,12 +72,32 @@ struct DevHeader {
   unsigned int rows_by_cell; // 1: the kernel stage wrote its rows at the cell index, 0: at the occupied-list index
   unsigned int pair_count;   // pair events queued by the particle-step kernel (reset by the pair kernel)
   unsigned int pairs_done;   // pair-kernel blocks finished (the last one resets the queue and the ticket)
+  unsigned int plan_epoch;   // launches of the plan so far (tags its blocks' published prefixes)
+  unsigned int plan_ticket;  // logical block index of the running plan launch (reset by its last block)
+};
+
+// Totals of a run of cells in the plan's scan: survivors (64 bits), work
+// items, needed cells, and whether a cell held 2^31 survivors or more.
+struct PlanSums {
+  unsigned long long T;
+  int I, N;
+  int big;
+  int pad;
+};
+
+// One block of the plan's scan publishes its own totals (agg) and then the
+// totals of every cell up to its last (inc); tag = epoch << 2 | state, state
+// 1 = agg valid, 2 = inc valid too, written after the values.
+struct PlanStatus {
+  PlanSums agg, inc;
+  unsigned int tag;
+  unsigned int pad[3];
 };
 
 // Byte offsets of the workspace regions (all 256-aligned).
 struct Layout {
   size_t header, T, R, IP, reach, occ, row_map, VWh, ccdf, scale, gamma, gthr, thr_cell, D, xlo, xhi, items, pairs, B,
-      tc, total;
+      tc, plan, total;
   long long max_items;
   unsigned pair_cap;  // entries of the pair queue
   int h;     // Q / 2
@@ -108,6 +130,7 @@ struct View {
   uint4* pairs;            // [pair_cap] pair events (id, cell, column, sign < 0) queued by the step
   float* B;                // [Kp][Np] sine matrix S[m][r], m = kk + 1
   void* tc;                // tensor-core operand images of S (BF16, FP16 hi, FP16 lo)
+  PlanStatus* plan;        // [ceil(n_x / kPlanCells)] published prefixes of the plan's blocks
 };
 View view(const wmc_params& p, void* ws);
 

@@ -149,14 +149,27 @@ __global__ __launch_bounds__(kCdfWarps * 32) void k_cdf(int n_M, int Q, int log2
                                                        unsigned long long* __restrict__ thr_cell,
                                                        unsigned int* __restrict__ flags, double dt,
                                                        DevHeader* __restrict__ hdr, long long* __restrict__ ccdf) {
+  extern __shared__ float s_cdf_rows[];  // one staged row (Q / 2 floats) per warp
   const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_host;
   if (hdr && blockIdx.x == 0 && threadIdx.x == 0) hdr->rows_by_cell = 0u;  // rows follow the occupied list
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * kCdfWarps + (threadIdx.x >> 5);
   if (row >= n_rows) return;
-  const float* v = VWh + (size_t)row * (Q / 2);
+  const int h = Q / 2;
+  // the row is staged in shared memory by coalesced loads: the CDF reads it
+  // in grid order (a permutation of the folded row), once per pass
+  // (padded: element r at r + r / 32, so that the lanes' contiguous column
+  // runs fall in distinct banks)
+  float* sv = s_cdf_rows + (threadIdx.x >> 5) * (h + h / 32 + 1);
+  const float* v = VWh + (size_t)row * h;
+  for (int r = lane; r < h; r += 32) sv[r + (r >> 5)] = __ldg(v + r);
+  __syncwarp();
   const int r0 = ((-(n_M / 2)) % Q + Q) % Q;   // r of column k = 0
-  auto xres = [&](int rr) { return positive_part(v, Q, rr); };
+  auto xres = [&](int rr) {
+    float x = 0.f;
+    if (rr != 0 && rr != h) x = rr < h ? sv[rr + (rr >> 5)] : -sv[(Q - rr) + ((Q - rr) >> 5)];
+    return x > 0.f ? x : 0.f;
+  };
   double g;
   int sc;
   long long tot;
@@ -540,7 +553,12 @@ cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_
       k_gamma_folded<0><<<blocks, kCdfWarps * 32, 0, s>>>(p.Q, lg, ca, cb, r0, VWh, n_rows_host, gamma, scale);
     return cudaGetLastError();
   }
-  k_cdf<<<(max_rows + kCdfWarps - 1) / kCdfWarps, kCdfWarps * 32, 0, s>>>(
+  const size_t sm = sizeof(float) * (size_t)kCdfWarps * (size_t)(p.Q / 2 + p.Q / 64 + 1);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_cdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_cdf<<<(max_rows + kCdfWarps - 1) / kCdfWarps, kCdfWarps * 32, sm, s>>>(
       p.n_M, p.Q, ceil_log2(p.n_M), VWh, n_rows_dev, n_rows_host, cdf, gamma, scale, gthr, occ, thr_cell, flags,
       p.dt_s, hdr, ccdf);
   return cudaGetLastError();

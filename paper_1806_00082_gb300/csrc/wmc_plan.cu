@@ -48,130 +48,199 @@ cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t 
   const Layout L = layout(p);
   const double d1 = ((kHbarJs * kPi) * p.dt_s) / ((p.mass_kg * (double)p.Q) * (p.dx_m * p.dx_m));
   k_init_tables<<<256, 256, 0, s>>>(p.n_M, p.Q, d1, v.D, v.xlo, v.xhi, v.B, L.Kp, L.Np, v.hdr);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // no stale publication may carry a tag of a coming plan launch
+  return cudaMemsetAsync(v.plan, 0, sizeof(PlanStatus) * (size_t)((p.n_x + kPlanCells - 1) / kPlanCells), s);
 }
 
 // ---------------------------------------------------------------- per-cell scan and plan
+// The plan: exclusive prefix sums over the cells of survivors (the first id
+// R[i] of each cell), work items (the first item IP[i]) and needed cells (the
+// occupied list and its row map), then the item descriptors; with clear_thr
+// the per-cell event thresholds are cleared (a kernel stage over the occupied
+// list then fills the occupied cells).  One thread per cell, kPlanCells cells
+// per block; the blocks chain their prefixes by a decoupled look-back: each
+// publishes its own totals at once and its inclusive prefix as soon as it
+// knows it, and a block sums its predecessors' totals back to the first
+// inclusive prefix it meets.  Blocks take their logical index from a ticket,
+// so every block waits only on blocks already running; every wait is bounded
+// and a timeout sets WMC_FLAG_TIMEOUT.  The last block writes the totals to
+// the header, resets the ticket and advances the epoch that tags the
+// publications.
+constexpr long long kPlanWaitCycles = 2000000000ll;
 
-// T and reach of every cell staged in shared memory by coalesced loads when
-// they fit, so the scan's per-thread runs read on-chip memory
-constexpr int kPlanStage = 4096;
+__device__ __forceinline__ PlanSums plan_add(const PlanSums& a, const PlanSums& b) {
+  PlanSums r;
+  r.T = a.T + b.T;
+  r.I = a.I + b.I;
+  r.N = a.N + b.N;
+  r.big = a.big | b.big;
+  r.pad = 0;
+  return r;
+}
 
-// The plan, by one block (blockDim.x threads, a multiple of 32 up to 1024):
-// exclusive prefix sums of survivors (ids), work items and needed cells, then
-// the occupied list, row map and work-item descriptors; with clear_thr the
-// per-cell event thresholds are cleared (a kernel stage over the occupied list
-// then fills the occupied cells; one over every cell writes them all itself).
-__device__ __forceinline__ void plan_block(int n_x, const unsigned long long* T_g, const unsigned char* reach_g,
-                           unsigned long long* __restrict__ R, int* __restrict__ IP, int* __restrict__ occ,
-                           int* __restrict__ row_map, int2* __restrict__ items, long long max_items,
-                           unsigned long long* __restrict__ thr_cell, DevHeader* hdr, int advance_step,
-                           int clear_thr) {
-  __shared__ unsigned long long wT[32];
-  __shared__ int wI[32], wN[32], wBig[32];
-  __shared__ unsigned long long s_T[kPlanStage];
-  __shared__ unsigned char s_reach[kPlanStage];
-  const int nt = blockDim.x, nw = nt >> 5;
+__device__ __forceinline__ PlanSums plan_load(const volatile PlanSums* p) {
+  PlanSums r;
+  r.T = p->T;
+  r.I = p->I;
+  r.N = p->N;
+  r.big = p->big;
+  r.pad = 0;
+  return r;
+}
+
+__device__ __forceinline__ void plan_store(volatile PlanSums* p, const PlanSums& v) {
+  p->T = v.T;
+  p->I = v.I;
+  p->N = v.N;
+  p->big = v.big;
+}
+
+__global__ __launch_bounds__(kPlanCells) void k_plan(int n_x, const unsigned long long* __restrict__ T,
+                                                     const unsigned char* __restrict__ reach,
+                                                     unsigned long long* __restrict__ R, int* __restrict__ IP,
+                                                     int* __restrict__ occ, int* __restrict__ row_map,
+                                                     int2* __restrict__ items, long long max_items,
+                                                     unsigned long long* __restrict__ thr_cell, DevHeader* hdr,
+                                                     PlanStatus* st, int advance_step, int clear_thr) {
+  __shared__ PlanSums w_s[kPlanCells / 32];
+  __shared__ PlanSums s_ex;
+  __shared__ int s_blk;
+  __shared__ unsigned int s_epoch;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const unsigned long long* T = T_g;
-  const unsigned char* reach = reach_g;
-  if (n_x <= kPlanStage) {
-    for (int i = tid; i < n_x; i += nt) {
-      s_T[i] = __ldg(T_g + i);
-      s_reach[i] = __ldg(reach_g + i);
-    }
-    __syncthreads();
-    T = s_T;
-    reach = s_reach;
+  if (tid == 0) {
+    s_blk = (int)atomicAdd(&hdr->plan_ticket, 1u);
+    s_epoch = *(volatile unsigned int*)&hdr->plan_epoch;
   }
-  const int per = (n_x + nt - 1) / nt;
-  const int lo = min(tid * per, n_x), hi = min(lo + per, n_x);
-  unsigned long long aT = 0;
-  int aI = 0, aN = 0, big = 0;
-  for (int i = lo; i < hi; ++i) {
-    const unsigned long long t = T[i];
-    aT += t;
-    aI += items_of_cell(t);
-    aN += cell_needs_kernel(reach, i, n_x);
-    big |= t > 0x7fffffffull;
-  }
-  // block-wide exclusive scan of (aT, aI, aN)
-  unsigned long long iT = aT;
-  int iI = aI, iN = aN;
+  __syncthreads();
+  const int blk = s_blk;
+  const unsigned int epoch = s_epoch;
+  const int i = blk * kPlanCells + tid;
+  const unsigned long long t = i < n_x ? __ldg(T + i) : 0ull;
+  PlanSums mine;
+  mine.T = t;
+  mine.I = items_of_cell(t);
+  mine.N = i < n_x ? cell_needs_kernel(reach, i, n_x) : 0;
+  mine.big = t > 0x7fffffffull;
+  mine.pad = 0;
+  // block-wide inclusive scan
+  PlanSums inc = mine;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    const unsigned long long uT = __shfl_up_sync(0xffffffffu, iT, off);
-    const int uI = __shfl_up_sync(0xffffffffu, iI, off);
-    const int uN = __shfl_up_sync(0xffffffffu, iN, off);
-    if (lane >= off) {
-      iT += uT;
-      iI += uI;
-      iN += uN;
-    }
+    PlanSums u;
+    u.T = __shfl_up_sync(0xffffffffu, inc.T, off);
+    u.I = __shfl_up_sync(0xffffffffu, inc.I, off);
+    u.N = __shfl_up_sync(0xffffffffu, inc.N, off);
+    u.big = __shfl_up_sync(0xffffffffu, inc.big, off);
+    if (lane >= off) inc = plan_add(inc, u);
   }
-  big = __any_sync(0xffffffffu, big);
-  if (lane == 31) {
-    wT[wid] = iT;
-    wI[wid] = iI;
-    wN[wid] = iN;
-    wBig[wid] = big;
-  }
+  if (lane == 31) w_s[wid] = inc;
   __syncthreads();
   if (wid == 0) {
-    unsigned long long sT = lane < nw ? wT[lane] : 0ull;
-    int sI = lane < nw ? wI[lane] : 0, sN = lane < nw ? wN[lane] : 0, sB = lane < nw ? wBig[lane] : 0;
+    PlanSums w = w_s[lane];
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const unsigned long long uT = __shfl_up_sync(0xffffffffu, sT, off);
-      const int uI = __shfl_up_sync(0xffffffffu, sI, off);
-      const int uN = __shfl_up_sync(0xffffffffu, sN, off);
-      if (lane >= off) {
-        sT += uT;
-        sI += uI;
-        sN += uN;
-      }
+      PlanSums u;
+      u.T = __shfl_up_sync(0xffffffffu, w.T, off);
+      u.I = __shfl_up_sync(0xffffffffu, w.I, off);
+      u.N = __shfl_up_sync(0xffffffffu, w.N, off);
+      u.big = __shfl_up_sync(0xffffffffu, w.big, off);
+      if (lane >= off) w = plan_add(w, u);
     }
-    sB = __any_sync(0xffffffffu, sB);
-    wT[lane] = sT;
-    wI[lane] = sI;
-    wN[lane] = sN;
-    wBig[lane] = sB;
+    w_s[lane] = w;
   }
   __syncthreads();
-  const unsigned long long baseT = (wid ? wT[wid - 1] : 0ull) + iT - aT;
-  int baseI = (wid ? wI[wid - 1] : 0) + iI - aI;
-  int baseN = (wid ? wN[wid - 1] : 0) + iN - aN;
-  const int ok = !wBig[31] && wT[31] < (1ull << 32) && (long long)wI[31] <= max_items;
-  unsigned long long r = baseT;
-  for (int i = lo; i < hi; ++i) {
-    const unsigned long long t = T[i];
-    if (ok) {
-      const int ni = items_of_cell(t);
-      for (int c = 0; c < ni; ++c) items[baseI + c] = make_int2(i, c);
+  if (wid) inc = plan_add(inc, w_s[wid - 1]);
+  const PlanSums agg = w_s[kPlanCells / 32 - 1];
+  // look-back by warp 0: lane l inspects predecessor blk - 1 - l - 32 w of
+  // window w, waiting (bounded) until it has published; the nearest inclusive
+  // prefix ends the walk, aggregates before it are added
+  if (wid == 0) {
+    volatile PlanStatus* me = st + blk;
+    if (lane == 0) {
+      plan_store(&me->agg, agg);
+      if (blk == 0) plan_store(&me->inc, agg);
+      __threadfence();
+      me->tag = (epoch << 2) | (blk == 0 ? 2u : 1u);
     }
-    if (clear_thr) thr_cell[i] = 0ull;
+    PlanSums ex = {0ull, 0, 0, 0, 0};
+    bool timed_out = false;
+    for (int top = blk - 1; top >= 0 && !timed_out; top -= 32) {
+      const int j = top - lane;
+      unsigned int tag = (epoch << 2) | 1u;
+      if (j >= 0) {
+        const volatile PlanStatus* o = st + j;
+        const long long t0 = clock64();
+        while (((tag = o->tag) >> 2) != (epoch & 0x3fffffffu) || (tag & 3u) == 0u) {
+          if (clock64() - t0 > kPlanWaitCycles) {
+            timed_out = true;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      timed_out = __any_sync(0xffffffffu, timed_out);
+      if (timed_out) break;
+      __threadfence();
+      const unsigned incl = __ballot_sync(0xffffffffu, j >= 0 && (tag & 3u) == 2u);
+      const int stop = incl ? __ffs(incl) - 1 : 32;   // nearest inclusive prefix in this window
+      PlanSums mineb = {0ull, 0, 0, 0, 0};
+      if (j >= 0 && lane <= stop) mineb = lane == stop ? plan_load(&st[j].inc) : plan_load(&st[j].agg);
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        PlanSums u;
+        u.T = __shfl_down_sync(0xffffffffu, mineb.T, off);
+        u.I = __shfl_down_sync(0xffffffffu, mineb.I, off);
+        u.N = __shfl_down_sync(0xffffffffu, mineb.N, off);
+        u.big = __shfl_down_sync(0xffffffffu, mineb.big, off);
+        mineb = plan_add(mineb, u);
+      }
+      ex = plan_add(ex, mineb);  // (lane 0 holds the window's sum)
+      if (incl) break;
+    }
+    if (lane == 0) {
+      if (timed_out) atomicOr(&hdr->flags, WMC_FLAG_TIMEOUT);
+      if (blk > 0) {
+        plan_store(&me->inc, plan_add(ex, agg));
+        __threadfence();
+        me->tag = (epoch << 2) | 2u;
+      }
+      s_ex = ex;
+    }
+  }
+  __syncthreads();
+  const PlanSums ex = s_ex;
+  const PlanSums tot = plan_add(ex, agg);  // through the block's last cell
+  if (i < n_x) {
+    const unsigned long long r = ex.T + inc.T - mine.T;
+    const int baseI = ex.I + inc.I - mine.I;
+    const int baseN = ex.N + inc.N - mine.N;
     R[i] = r;
     IP[i] = baseI;
-    if (cell_needs_kernel(reach, i, n_x)) {
+    for (int c = 0; c < mine.I; ++c)
+      if ((long long)baseI + c < max_items) items[baseI + c] = make_int2(i, c);
+    if (clear_thr) thr_cell[i] = 0ull;
+    if (mine.N) {
       occ[baseN] = i;
       row_map[i] = baseN;
-      ++baseN;
     } else {
       row_map[i] = -1;
     }
-    r += t;
-    baseI += items_of_cell(t);
   }
-  if (tid == nt - 1) {
-    const unsigned long long P = wT[31];
-    const int too_big = !ok;
-    R[n_x] = P;
-    IP[n_x] = wI[31];
-    hdr->population = P;
-    hdr->n_items = too_big ? 0 : wI[31];
-    hdr->n_occ = wN[31];
-    if (too_big) atomicOr(&hdr->flags, WMC_FLAG_CAPACITY);
+  if (blk == (int)gridDim.x - 1 && tid == 0) {
+    // totals of every cell
+    const bool ok = !tot.big && tot.T < (1ull << 32) && (long long)tot.I <= max_items;
+    R[n_x] = tot.T;
+    IP[n_x] = tot.I;
+    hdr->population = tot.T;
+    hdr->n_items = ok ? tot.I : 0;
+    hdr->n_occ = tot.N;
+    if (!ok) atomicOr(&hdr->flags, WMC_FLAG_CAPACITY);
     if (advance_step) hdr->step += 1u;
+    hdr->plan_ticket = 0u;
+    hdr->plan_epoch = (epoch + 1u) & 0x3fffffffu;
+    __threadfence();
   }
 }
 
@@ -237,20 +306,6 @@ __global__ __launch_bounds__(kRowsWarps * 32) void k_rows(const int32_t* __restr
   }
 }
 
-// The plan as its own single-block launch (n_x is at most a few 10^4 in the
-// workloads and this runs once per step).
-constexpr int kPlanThreads = 1024;
-
-__global__ __launch_bounds__(kPlanThreads) void k_plan(int n_x, const unsigned long long* __restrict__ T,
-                                                       const unsigned char* __restrict__ reach,
-                                                       unsigned long long* __restrict__ R, int* __restrict__ IP,
-                                                       int* __restrict__ occ, int* __restrict__ row_map,
-                                                       int2* __restrict__ items, long long max_items,
-                                                       unsigned long long* __restrict__ thr_cell, DevHeader* hdr,
-                                                       int advance_step, int clear_thr) {
-  plan_block(n_x, T, reach, R, IP, occ, row_map, items, max_items, thr_cell, hdr, advance_step, clear_thr);
-}
-
 cudaError_t launch_rows(const wmc_params& p, const View& v, const int32_t* hist, int64_t* rho, cudaStream_t s,
                         int32_t* zero_out) {
   const int blocks = (p.n_x + kRowsWarps - 1) / kRowsWarps;
@@ -260,8 +315,9 @@ cudaError_t launch_rows(const wmc_params& p, const View& v, const int32_t* hist,
 }
 
 cudaError_t launch_plan_scan(const wmc_params& p, const View& v, int advance_step, int clear_thr, cudaStream_t s) {
-  k_plan<<<1, kPlanThreads, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.items,
-                                    layout(p).max_items, v.thr_cell, v.hdr, advance_step, clear_thr);
+  const int blocks = (p.n_x + kPlanCells - 1) / kPlanCells;
+  k_plan<<<blocks, kPlanCells, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.items,
+                                       layout(p).max_items, v.thr_cell, v.hdr, v.plan, advance_step, clear_thr);
   return cudaGetLastError();
 }
 

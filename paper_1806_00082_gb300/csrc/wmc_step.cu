@@ -50,6 +50,7 @@ struct StepArgs {
 // p' of the pair created by particle id (column k, sign sgn) in cell c and the
 // children c (k + M', +sgn), (k - M', -sgn); rows follow the cell index or the
 // occupied list as the kernel stage laid them out.
+template <bool SEQ = false>
 __device__ __forceinline__ void pair_children(const StepArgs& a, int rows_by_cell, uint32_t id, uint32_t t, int c,
                                               int k, int sgn, unsigned long long& pairs, unsigned long long& dropped,
                                               long long& drop_signed) {
@@ -57,8 +58,11 @@ __device__ __forceinline__ void pair_children(const StepArgs& a, int rows_by_cel
   const int orow = rows_by_cell ? c : __ldg(a.row_map + c);
   const uint4 wp = philox4x32_10(make_uint4(id, t, kPurposePick, a.sim), a.k0, a.k1);
   const unsigned long long U2 = ((unsigned long long)(wp.x >> 5) << 26) | (unsigned long long)(wp.y >> 6);
-  const int kp = sample_coarse_row(a.VWh + (size_t)orow * h, a.ccdf + (size_t)orow * kCdfBlocks,
-                                   __ldg(a.scale + orow), a.Q, a.r0, n_M, U2);
+  const float* vrow = a.VWh + (size_t)orow * h;
+  const long long* crow = a.ccdf + (size_t)orow * kCdfBlocks;
+  const int sc = __ldg(a.scale + orow);
+  const int kp = SEQ ? sample_coarse_row_seq(vrow, crow, sc, a.Q, a.r0, n_M, U2)
+                     : sample_coarse_row(vrow, crow, sc, a.Q, a.r0, n_M, U2);
   ++pairs;
   const int Mp = kp - n_M / 2;
   const int kc2[2] = {k + Mp, k - Mp};
@@ -84,7 +88,7 @@ __device__ __forceinline__ void pair_children_direct(const StepArgs& a, int rows
                                                      int c, int k, int sgn) {
   unsigned long long pairs = 0, dropped = 0;
   long long drop_signed = 0;
-  pair_children(a, rows_by_cell, id, t, c, k, sgn, pairs, dropped, drop_signed);
+  pair_children<true>(a, rows_by_cell, id, t, c, k, sgn, pairs, dropped, drop_signed);
   atomicAdd(&a.hdr->pairs, pairs);
   if (dropped) {
     atomicAdd(&a.hdr->dropped, dropped);
@@ -119,30 +123,46 @@ __device__ __forceinline__ void block_counters(DevHeader* hdr, unsigned long lon
   }
 }
 
+// Lane blocks of the staged row prefix: E2 = the power of two >= ceil(n_M / 32)
+// columns per lane.
+__host__ __device__ __forceinline__ int step_lg_block(int n_M) {
+  int lg = 0;
+  while ((32 << lg) < n_M) ++lg;
+  return lg;
+}
+
 // Shared memory of a step block: the per-column move test (flip, threshold)
 // of the block, then per warp the row prefix in a padded layout (column k at
-// k + floor(k / E), E = ceil(n_M / 32), so that lane l's block of E columns
-// is contiguous and bank-conflict free), the sign bits and the event queue.
+// k + (k >> lg), so that lane l's block of E2 = 2^lg columns is contiguous and
+// bank-conflict free), the sign bits, the non-empty bits, the next non-empty
+// column after each column (16 bits) and the event queue.
 __host__ __device__ __forceinline__ int step_warp_words(int n_M) {
-  const int E = (n_M + 31) >> 5;
-  return 32 * (E + 1) + 1 + E + kPairQ;
+  const int E2 = 1 << step_lg_block(n_M);
+  return 32 * (E2 + 1) + 1 + 2 * ((n_M + 31) / 32) + (n_M + 1) / 2 + kPairQ;
 }
 
 static size_t step_smem(int n_M) {
   return sizeof(uint32_t) * (2 * (size_t)n_M + (size_t)kStepWarps * step_warp_words(n_M));
 }
 
-__global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
+// 4-bit mask of the elements j of a quad with j < d (d may be <= 0 or >= 4).
+__device__ __forceinline__ uint32_t first_mask(int d) { return d >= 4 ? 0xfu : (d <= 0 ? 0u : (1u << d) - 1u); }
+
+__global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
   extern __shared__ __align__(16) uint32_t smem_step[];
   __shared__ int s_qn[kStepWarps];
+  __shared__ unsigned long long s_thr[kStepWarps][3];  // event thresholds of cells i - 1, i, i + 1
   const int n_M = a.n_M;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int E = (n_M + 31) >> 5;
+  const int lg = step_lg_block(n_M), E2 = 1 << lg;
   uint2* s_xm = reinterpret_cast<uint2*>(smem_step);
   uint32_t* wsm = smem_step + 2 * n_M + wid * step_warp_words(n_M);
-  int* s_pp = reinterpret_cast<int*>(wsm);        // padded row prefix, 32 (E + 1) + 1 ints
-  uint32_t* s_sg = wsm + 32 * (E + 1) + 1;         // sign bits (1: positive), E words
-  uint32_t* s_q = s_sg + E;                        // event queue
+  int* s_pp = reinterpret_cast<int*>(wsm);             // padded row prefix
+  const int NW = (n_M + 31) / 32;
+  uint32_t* s_sg = wsm + 32 * (E2 + 1) + 1;             // sign bits (1: negative)
+  uint32_t* s_nz = s_sg + NW;                            // non-empty bits
+  uint16_t* s_nx = reinterpret_cast<uint16_t*>(s_nz + NW);  // next non-empty column
+  uint32_t* s_q = s_nz + NW + (n_M + 1) / 2;              // event queue
   const int rows_by_cell = (int)a.hdr->rows_by_cell;
   const uint32_t t = a.t_from_device ? a.hdr->step : a.t;
   const int n_items = a.hdr->n_items;
@@ -154,12 +174,12 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
   }
   if (lane == 0) s_qn[wid] = 0;
   __syncthreads();
-  const uint32_t magicE = (uint32_t)((0x100000000ull + (unsigned)E - 1ull) / (unsigned)E);  // ceil(2^32 / E)
-  auto pidx = [&](int k) { return k + (int)__umulhi((uint32_t)k, magicE); };
+  auto P = [&](int k) { return s_pp[k + (k >> lg)]; };
 
   int cur_i = -1;
   uint32_t base = 0u;
-  unsigned long long thr_m = 0, thr_0 = 0, thr_p = 0;
+  bool need_gen = false, any_full = false;
+  uint32_t rej = 0u;
 
   int item = 0;
   if (lane == 0) item = (int)atomicAdd(&a.hdr->item_ticket, 1u);
@@ -171,18 +191,34 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
     const int i = it.x, ch = it.y;
     if (i != cur_i) {
       // stage the row: |n| into the padded buffer, sign bits, then the
-      // exclusive prefix in place (lane l over its block of E columns)
+      // exclusive prefix in place (lane l over its block of E2 columns)
       const int32_t* row = a.hist_in + (size_t)i * n_M;
       for (int k0 = 0; k0 < n_M; k0 += 32) {
         const int k = k0 + lane;
         const int n = k < n_M ? __ldg(row + k) : 0;
-        if (k < n_M) s_pp[pidx(k)] = n < 0 ? -n : n;
-        const uint32_t b = __ballot_sync(0xffffffffu, n > 0);
-        if (lane == 0) s_sg[k0 >> 5] = b;
+        if (k < n_M) s_pp[k + (k >> lg)] = n < 0 ? -n : n;
+        const uint32_t b = __ballot_sync(0xffffffffu, n < 0);
+        const uint32_t z = __ballot_sync(0xffffffffu, n != 0);
+        if (lane == 0) {
+          s_sg[k0 >> 5] = b;
+          s_nz[k0 >> 5] = z;
+        }
       }
       __syncwarp();
-      const int kb0 = min(lane * E, n_M), kb1 = min(kb0 + E, n_M);
-      int* blk = s_pp + lane * (E + 1);
+      // next non-empty column after each column (n_M if none), word by word
+      // from the last, carrying the first non-empty column of later words
+      {
+        int carry = n_M;
+        for (int c = NW - 1; c >= 0; --c) {
+          const uint32_t z = s_nz[c];
+          const uint32_t above = z & ~((2u << lane) - 1u);  // (2 << 31 wraps to 0: no bits above lane 31)
+          const int kk = (c << 5) + lane;
+          if (kk < n_M) s_nx[kk] = (uint16_t)(above ? (c << 5) + __ffs(above) - 1 : carry);
+          if (z) carry = (c << 5) + __ffs(z) - 1;
+        }
+      }
+      const int kb0 = min(lane << lg, n_M), kb1 = min(kb0 + E2, n_M);
+      int* blk = s_pp + lane * (E2 + 1);
       int local = 0;
       for (int j = 0; j < kb1 - kb0; ++j) local += blk[j];
       int incl = local;
@@ -198,16 +234,28 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
         run += v;
       }
       __syncwarp();
-      if (lane == 31) s_pp[pidx(n_M)] = incl;
+      if (lane == 31) s_pp[n_M + (n_M >> lg)] = incl;
       base = (uint32_t)__ldg(a.R + i);
-      thr_m = i > 0 ? __ldg(a.thr_cell + i - 1) : 0ull;
-      thr_0 = __ldg(a.thr_cell + i);
-      thr_p = i + 1 < a.n_x ? __ldg(a.thr_cell + i + 1) : 0ull;
+      const unsigned long long thr_m = i > 0 ? __ldg(a.thr_cell + i - 1) : 0ull;
+      const unsigned long long thr_0 = __ldg(a.thr_cell + i);
+      const unsigned long long thr_p = i + 1 < a.n_x ? __ldg(a.thr_cell + i + 1) : 0ull;
+      if (lane == 0) {
+        s_thr[wid][0] = thr_m;
+        s_thr[wid][1] = thr_0;
+        s_thr[wid][2] = thr_p;
+      }
+      need_gen = (thr_m | thr_0 | thr_p) != 0ull;
+      // events: a stayer tests thr(i), a mover thr(i +- 1) (0 outside the
+      // domain: absorbed particles create no pair); rej = the largest of them
+      // as a quick rejection of a whole quad (exact unless a threshold is 2^32)
+      const unsigned long long tmax =
+          thr_0 > thr_m ? (thr_0 > thr_p ? thr_0 : thr_p) : (thr_m > thr_p ? thr_m : thr_p);
+      any_full = tmax >> 32 != 0ull;
+      rej = any_full ? 0xffffffffu : (uint32_t)tmax;
       cur_i = i;
       __syncwarp();
     }
-    const bool need_gen = (thr_m | thr_0 | thr_p) != 0ull;
-    const uint32_t Ti = (uint32_t)s_pp[pidx(n_M)];
+    const uint32_t Ti = (uint32_t)P(n_M);
     // the item is [item0, item1) of the quad-aligned id range of the cell; each
     // lane takes a quad-aligned span of it
     const unsigned long long A = base & ~3u;
@@ -222,44 +270,41 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
     const bool has = g0_64 < g1_64;
     const uint32_t g0 = has ? (uint32_t)g0_64 : 0u, g1 = has ? (uint32_t)g1_64 : 0u;
     const uint32_t i0 = (uint32_t)item0;
+    int32_t* const out_i = a.hist_out + (size_t)i * n_M;
 
     // bucket state
-    int k = 0, sgn = 1, dir = 0, tgt = i;
-    uint32_t end = 0u, flip = 0u, mthr = 0xffffffffu, rej = 0u;
-    unsigned long long e_st = 0ull, e_mv = 0ull;
-    bool full = false;
+    int k = 0, sgn = 1, dir = 0;
+    uint32_t end = 0u, flip = 0u, mthr = 0xffffffffu;
     int n_st = 0, n_mv = 0;
     auto load_bucket = [&]() {
-      end = base + (uint32_t)s_pp[pidx(k + 1)];
-      sgn = ((s_sg[k >> 5] >> (k & 31)) & 1u) ? 1 : -1;
+      end = base + (uint32_t)P(k + 1);
+      sgn = ((s_sg[k >> 5] >> (k & 31)) & 1u) ? -1 : 1;
       const uint2 xm = s_xm[k];
       flip = xm.x;
       mthr = xm.y;
       dir = flip ? -1 : (mthr != 0xffffffffu ? 1 : 0);
-      tgt = i + dir;
-      e_st = thr_0;
-      e_mv = dir > 0 ? thr_p : (dir < 0 ? thr_m : 0ull);
-      const unsigned long long emax = e_st > e_mv ? e_st : e_mv;
-      full = emax >> 32 != 0ull;
-      rej = full ? 0xffffffffu : (uint32_t)emax;
     };
     auto flush_bucket = [&]() {
-      if (n_st) atomicAdd(a.hist_out + (size_t)i * n_M + k, sgn * n_st);
+      if (n_st) atomicAdd(out_i + k, sgn > 0 ? n_st : -n_st);
       if (n_mv) {
-        if ((unsigned)tgt < (unsigned)a.n_x) {
-          atomicAdd(a.hist_out + (size_t)tgt * n_M + k, sgn * n_mv);
+        const int c = sgn > 0 ? n_mv : -n_mv;
+        if ((unsigned)(i + dir) < (unsigned)a.n_x) {
+          atomicAdd(out_i + (dir > 0 ? n_M : -n_M) + k, c);
         } else {  // left the domain (edge cells only): counted at once
           atomicAdd(&a.hdr->absorbed, (unsigned long long)n_mv);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->absorbed_signed),
-                    (unsigned long long)(long long)(sgn * n_mv));
+          atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->absorbed_signed), (unsigned long long)(long long)c);
         }
       }
       n_st = n_mv = 0;
     };
-    auto push = [&](uint32_t id, int mv) {
-      const int pos = atomicAdd(&s_qn[wid], 1);
-      if (pos < kPairQ)  // always (the queue is drained whenever it could fill within one quad iteration)
-        s_q[pos] = (id - i0) | ((uint32_t)k << 12) | ((uint32_t)(mv ? dir + 1 : 1) << 24) | (sgn < 0 ? 1u << 26 : 0u);
+    // pair event of particle id (mover or not) of the current bucket
+    auto test_event = [&](uint32_t id, uint32_t u, int mv) {
+      const unsigned long long thr = s_thr[wid][mv ? dir + 1 : 1];
+      if ((unsigned long long)u < thr) {
+        const int pos = atomicAdd(&s_qn[wid], 1);
+        if (pos < kPairQ)  // always (the queue is drained whenever it could fill within one quad iteration)
+          s_q[pos] = (id - i0) | ((uint32_t)k << 12) | ((uint32_t)(mv ? dir + 1 : 1) << 24) | (sgn < 0 ? 1u << 26 : 0u);
+      }
     };
     // queued events of this item to the global queue (warp-collective)
     auto flush_queue = [&]() {
@@ -292,7 +337,7 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
       int lo = 0, hi = n_M;
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (s_pp[pidx(mid)] <= lid) lo = mid; else hi = mid;
+        if (P(mid) <= lid) lo = mid; else hi = mid;
       }
       k = lo;
       load_bucket();
@@ -308,38 +353,25 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
         uint4 wg = make_uint4(q, t, kPurposeGen, a.sim);
         if (need_gen) philox4x32_10_x2(wr, wg, a.k0, a.k1);
         else wr = philox4x32_10(wr, a.k0, a.k1);
-        if (qa >= g0 && qa + 4u <= g1 && qa + 4u <= end) {
-          // four consecutive ids of bucket k
-          const int m0 = (wr.x ^ flip) > mthr, m1 = (wr.y ^ flip) > mthr;
-          const int m2 = (wr.z ^ flip) > mthr, m3 = (wr.w ^ flip) > mthr;
-          const int nm = m0 + m1 + m2 + m3;
-          n_mv += nm;
-          n_st += 4 - nm;
-          if (need_gen) {
-            const uint32_t umin = min(min(wg.x, wg.y), min(wg.z, wg.w));
-            if (umin < rej || full) {
-              if ((unsigned long long)wg.x < (m0 ? e_mv : e_st)) push(qa, m0);
-              if ((unsigned long long)wg.y < (m1 ? e_mv : e_st)) push(qa + 1u, m1);
-              if ((unsigned long long)wg.z < (m2 ? e_mv : e_st)) push(qa + 2u, m2);
-              if ((unsigned long long)wg.w < (m3 ? e_mv : e_st)) push(qa + 3u, m3);
-            }
-          }
-        } else {
-          const uint32_t w4[4] = {wr.x, wr.y, wr.z, wr.w};
-          const uint32_t u4[4] = {wg.x, wg.y, wg.z, wg.w};
+        const bool ev_possible = need_gen && (min(min(wg.x, wg.y), min(wg.z, wg.w)) < rej || any_full);
+        // the ids of the quad in [g0, g1), each in its bucket: a bucket ends
+        // exactly where the next non-empty one starts
+        const uint32_t vmask = first_mask((int)(g1 - qa)) & ~first_mask((int)(g0 - qa));
+        const uint32_t w4[4] = {wr.x, wr.y, wr.z, wr.w};
+        const uint32_t u4[4] = {wg.x, wg.y, wg.z, wg.w};
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 4; ++j) {
+          if ((vmask >> j) & 1u) {
             const uint32_t id = qa + (uint32_t)j;
-            if (id < g0 || id >= g1) continue;
-            if (id >= end) {  // next non-empty bucket
+            if (id >= end) {
               flush_bucket();
-              do { ++k; } while (k < n_M - 1 && base + (uint32_t)s_pp[pidx(k + 1)] <= id);
+              k = s_nx[k];
               load_bucket();
             }
             const int mv = (w4[j] ^ flip) > mthr;
             n_mv += mv;
             n_st += 1 - mv;
-            if (need_gen && (unsigned long long)u4[j] < (mv ? e_mv : e_st)) push(id, mv);
+            if (ev_possible) test_event(id, u4[j], mv);
           }
         }
       }
@@ -435,7 +467,9 @@ cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_
   e = cudaGetLastError();
   if (e == cudaSuccess) e = step_timing_record(s, true);
   if (e != cudaSuccess) return e;
-  k_pairs<<<4 * num_sms(), kStepThreads, 0, s>>>(a);
+  // one thread per queued event (the count is on the device: surplus blocks exit)
+  const unsigned pair_blocks = (L.pair_cap + kStepThreads - 1) / kStepThreads;
+  k_pairs<<<pair_blocks < 8u * (unsigned)num_sms() ? pair_blocks : 8u * (unsigned)num_sms(), kStepThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
