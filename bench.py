@@ -35,6 +35,11 @@ METRIC = "particle-steps/s; kernel cell·M evals/s at stated err vs FP64 (TC vs 
 UNIT = "particle-steps/s"
 L2_BYTES = 129 * 2 ** 20
 
+# DRAM bytes (read + write) of one particle-step kernel launch from the ncu
+# capture named below; None until the current kernel has been captured.
+K_STEP_DRAM_BYTES = None
+K_STEP_TRAFFIC_SOURCE = "no ncu capture of the current particle-step kernel yet"
+
 
 def _env_int(k, d):
     try:
@@ -185,7 +190,8 @@ def native_arm(args, w):
     wl = w.replace(sim=rank)          # independent replica per rank
     p = wmc.Params.of(wl)
     V = torch.from_numpy(wi.potential(wl)).to(dev)
-    h0 = torch.from_numpy(wi.initial_histogram(wl)).to(dev)
+    h0_host = wi.initial_histogram(wl)
+    h0 = torch.from_numpy(h0_host).to(dev)
     ws = wmc.workspace(p, dev)
     a = h0.clone()
     b = torch.empty_like(a)
@@ -207,7 +213,7 @@ def native_arm(args, w):
         torch.cuda.synchronize()
         with Clocks(local) as clk:
             for q in range(n_iter):
-                flush.zero_()                    # inputs are L2-resident: flush between iterations
+                flush.zero_()                    # L2 flushed between timed iterations
                 ev[q][0].record(stream)
                 wmc.run(p, V, a, b, t, 2, ws)
                 ev[q][1].record(stream)
@@ -218,16 +224,17 @@ def native_arm(args, w):
             torch.distributed.barrier()
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
         c = wmc.get_counters(p, ws)
+        err = wmc.get_error(p, ws)
     ms_max, ps_total = reduce_over_ranks(ms, float(c["particle_steps"]), dev)
     value = ps_total / (ms_max * 1e-3)
 
     # ---- dominant kernel: the particle step inside the same step graphs
-    roof = step_roofline(wmc, torch, p, V, a, b, ws, stream, t, flush, min(n_iter, 50))
-    t += 2 * min(n_iter, 50)
+    roof = step_roofline(wmc, torch, p, V, a, b, ws, stream, t, flush, min(n_iter, 20), local)
+    t += 2 * min(n_iter, 20)
     # ---- end to end through the C ABI with host buffers
-    e2e = end_to_end(wmc, torch, p, V, ws, stream, h0, t + 4 * n_iter, n=20)
-    # ---- kernel evaluation throughput, all cells of the 16384-cell double barrier
-    kev = kernel_eval_rate(wmc, torch, dev, stream, flush) if rank == 0 else None
+    e2e = end_to_end(wmc, torch, p, V, ws, stream, h0_host, a, t + 4, n=12)
+    kev = kernel_eval_rate(wmc, torch, dev, stream, flush) if rank == 0 and not args.no_batched else None
+    drift = drift_only_rate(wmc, torch, dev, stream, flush) if rank == 0 and not args.no_batched else None
     bat = batched_rate(wmc, torch, dev, stream) if rank == 0 and not args.no_batched else None
     adjo = adjoint_rate(wmc, torch, dev, stream) if rank == 0 and not args.no_batched else None
 
@@ -239,7 +246,8 @@ def native_arm(args, w):
     if world == 1 and not args.no_cpu_baseline:
         rate, ps_cpu, st_cpu, secs = oracle_rate(w, 10.0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{w.name} full N0={w.packet.n0}, first {st_cpu} steps ({secs:.1f} s, single thread)"}
+               "sample": f"{w.name} full N0={w.packet.n0}, first {st_cpu} step(s) ({secs:.1f} s, single thread; "
+                         f"the FP64 kernel on every occupied cell and the particle loop)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak",
@@ -248,15 +256,18 @@ def native_arm(args, w):
                    "dt_fs": w.dt_s / 1e-15, "kernel": "fp32 (compensated)",
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed iterations (2 steps each)"},
         "clocks": clk.summary(),
-        # per step: k_rows, k_plan, k_kernel_rows_small, k_step; per wmc_run call: k_set_step
-        "gpu_launches": 4 * steps + n_iter,
+        # per step: k_rows, k_plan, kernel stage (contraction + CDF, or the fused
+        # small-window kernel), k_step, k_pairs; per wmc_run call: k_set_step
+        "gpu_launches": (6 if w.Q // 2 > 128 else 5) * steps + n_iter,
         "e2e": e2e,
         "roofline": roof,
         "cpu_baseline": cpu,
         "kernel_eval": kev,
+        "drift_only": drift,
         "batched": bat,
         "adjoint": adjo,
-        "counters": {k: c[k] for k in ("pairs", "absorbed", "dropped", "n_occ", "flags")},
+        "counters": {k: c[k] for k in ("pairs", "absorbed", "dropped", "n_occ", "population", "flags")},
+        "device_status": {"code": err[0], "message": err[1]},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -283,88 +294,122 @@ def reach_cells(wmc, torch, p, V, ws, stream):
 def philox_calls(c0, c1, r0, r1):
     """Philox4x32-10 calls of the particle-step kernel per step over one
     two-step launch: one offset draw per four survivors (the particle-step
-    counter, exact), one creation draw per four survivors of reach cells (exact
-    for the first step, the launch's output state standing in for the second
-    step's input) and one draw per created pair (exact)."""
+    counter, exact) and one pair-creation draw per four survivors of reach
+    cells (exact for the first step, the launch's output state standing in for
+    the second step's input).  The pair draws run in the pair kernel."""
     ps = c1["particle_steps"] - c0["particle_steps"]
-    pairs = c1["pairs"] - c0["pairs"]
-    return (ps / 4.0 + (r0 + r1) / 4.0 + pairs) / 2.0
+    return (ps / 4.0 + (r0 + r1) / 4.0) / 2.0
 
 
-# DRAM bytes (read + write) of one k_step launch on barrier-2000, from an ncu
-# capture of the current kernel (407.3 KB read, 0 written): the particle step
-# reads the histogram rows and CDFs and keeps its output in L2.
-K_STEP_DRAM_BYTES = 407_296
+def philox_peak(wmc, torch, dev, stream, reps=5):
+    """Calls per second of the generator alone (wmc_philox_throughput: two
+    calls at a time under one key schedule, every SM busy), timed with events;
+    the ceiling of the particle step's arithmetic."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = torch.empty(sms * 8 * 256, dtype=torch.int32, device=dev)
+    pairs = 128
+    best = None
+    with torch.cuda.stream(stream):
+        wmc.philox_throughput(out, pairs)
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wmc.philox_throughput(out, pairs)
+            e1.record(stream)
+            stream.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            best = sec if best is None else min(best, sec)
+    calls = 2.0 * pairs * out.numel()
+    return calls / best, {"threads": out.numel(), "calls_per_launch": calls, "seconds": best, "sms": sms}
 
 
-def step_roofline(wmc, torch, p, V, a, b, ws, stream, t, flush, n):
+# 14 bytes per particle-step: the algorithmic traffic of a stored-particle
+# design (7-byte SoA record read and rewritten per step)
+BYTES_PER_PARTICLE_STEP = 14
+
+
+def step_roofline(wmc, torch, p, V, a, b, ws, stream, t, flush, n, gpu_index):
     """The particle-step kernel as it runs in the timed step graphs: n more
     launches of the same two-step graph, L2 flushed before each, recaptured
     with the library's CUDA events around the kernel (event-record nodes on the
-    launching stream; they cost a few microseconds of graph latency each, so
-    the timed region above runs without them).  Duration = the second step's
-    kernel of each launch; work in Philox4x32-10 calls (philox_calls)."""
+    launching stream).  Duration = the second step's kernel of each launch;
+    work in Philox4x32-10 calls (philox_calls), against the measured calls/s
+    of the generator alone; clocks sampled meanwhile."""
+    peaks, src = _peaks()
     reach = reach_cells(wmc, torch, p, V, ws, stream)
-    k_ms, k_calls = [], []
-    with torch.cuda.stream(stream):
-        wmc.step_timing(True)
-        try:
-            c0 = wmc.get_counters(p, ws)
-            r0 = float(a.abs()[reach].sum())
-            for _ in range(n):
-                # keep the stream busy while the host enqueues after its wait
-                torch.cuda._sleep(200_000)
-                flush.zero_()
-                wmc.run(p, V, a, b, t, 2, ws)
-                t += 2
-                k_ms.append(wmc.step_timing_read())
-                c1 = wmc.get_counters(p, ws)
-                r1 = float(a.abs()[reach].sum())
-                k_calls.append(philox_calls(c0, c1, r0, r1))
-                c0, r0 = c1, r1
-        finally:
-            wmc.step_timing(False)
+    k_ms, k_calls, k_ps = [], [], []
+    with Clocks(gpu_index) as clk:
+        peak_calls, peak_info = philox_peak(wmc, torch, a.device, stream)
+        with torch.cuda.stream(stream):
+            wmc.step_timing(True)
+            try:
+                c0 = wmc.get_counters(p, ws)
+                r0 = float(a.abs()[reach].sum())
+                for _ in range(n):
+                    torch.cuda._sleep(200_000)   # keep the stream busy while the host enqueues after its wait
+                    flush.zero_()
+                    wmc.run(p, V, a, b, t, 2, ws)
+                    t += 2
+                    k_ms.append(wmc.step_timing_read())
+                    c1 = wmc.get_counters(p, ws)
+                    r1 = float(a.abs()[reach].sum())
+                    k_calls.append(philox_calls(c0, c1, r0, r1))
+                    k_ps.append((c1["particle_steps"] - c0["particle_steps"]) / 2.0)
+                    c0, r0 = c1, r1
+            finally:
+                wmc.step_timing(False)
     sec = float(np.mean(k_ms)) * 1e-3
     per_launch = float(np.mean(k_calls))
-    sm_mhz = 2070.0
-    # ALU peak: a Philox4x32-10 call is 20 32x32->64-bit products, i.e. 40
-    # operations of the integer-multiply pipe (64 lanes/clk/SM), 152 SMs.
-    peak_calls = 152 * 64 * sm_mhz * 1e6 / 40
+    ps_launch = float(np.mean(k_ps))
     achieved = per_launch / sec
+    hbm = BYTES_PER_PARTICLE_STEP * ps_launch / sec / 1e9
     return {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": peak_calls,
             "unit": "Philox4x32-10 calls/s", "frac": achieved / peak_calls, "traffic": K_STEP_DRAM_BYTES,
-            "traffic_source": "ncu --set full capture of k_step on barrier-2000: dram read + write per launch",
-            "per_launch": {"philox_calls": per_launch, "seconds": sec, "launches_timed": len(k_ms)},
-            "peak_source": f"derived: 152 SMs x 64 integer-multiply lanes x {sm_mhz:.0f} MHz / 40 per call"}
+            "traffic_source": K_STEP_TRAFFIC_SOURCE,
+            "per_launch": {"philox_calls": per_launch, "particle_steps": ps_launch, "seconds": sec,
+                           "launches_timed": len(k_ms)},
+            "peak_source": "measured in this run: wmc_philox_throughput (the generator alone on every SM, two "
+                           f"calls per key schedule), {peak_info['threads']} threads, events; clocks {clk.summary()}",
+            "hbm_equivalent": {"bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "achieved_GBs": hbm,
+                               "peak_GBs": peaks["hbm_gbs"], "frac": hbm / peaks["hbm_gbs"],
+                               "note": f"{src} copy bandwidth; the design stores no particles, so this is the "
+                                       "throughput a stored-particle step would need"}}
 
 
-def end_to_end(wmc, torch, p, V, ws, stream, h0, t0, n=10):
+def end_to_end(wmc, torch, p, V, ws, stream, h0_host, a_dev, t0, n=12):
     """Per step: H2D of a state from pinned memory, one wmc_run step, D2H of the
-    new state, for a stream of n independent states.  The steps run in order on
-    the compute stream (they share the workspace); the copies run on their own
-    streams into two buffer sets, so that the upload of the next state and the
-    download of the previous result overlap the current step.  Timed with
+    new state, for a sequence of n states (three distinct ones in turn: the
+    initial state and two later states of the same run).  The steps run in order
+    on the compute stream (they share the workspace); the copies run on their
+    own streams into two buffer sets, so that the upload of the next state and
+    the download of the previous result overlap the current step.  Timed with
     events from the first upload to the last download (all of it enqueued
-    behind a sleep kernel first, so that host enqueue time is not timed)."""
-    host_in = h0.cpu().pin_memory()
-    host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
-    bufs = [(torch.empty_like(h0), torch.empty_like(h0)) for _ in range(2)]
-    up, down = torch.cuda.Stream(device=h0.device), torch.cuda.Stream(device=h0.device)
+    behind a sleep kernel, so that host enqueue time is not timed).  Each
+    state and its output (2 x 64 MB at 16384 x 1024) exceed L2 together."""
+    states = [torch.from_numpy(h0_host).pin_memory(), a_dev.cpu().pin_memory()]
+    with torch.cuda.stream(stream):
+        tmp_a, tmp_b = a_dev.clone(), torch.empty_like(a_dev)
+        wmc.run(p, V, tmp_a, tmp_b, t0, 2, ws)
+        stream.synchronize()
+    states.append(tmp_a.cpu().pin_memory())
+    del tmp_a, tmp_b
+    host_out = [torch.empty_like(states[0]).pin_memory() for _ in range(2)]
+    bufs = [(torch.empty_like(a_dev), torch.empty_like(a_dev)) for _ in range(2)]
+    up, down = torch.cuda.Stream(device=a_dev.device), torch.cuda.Stream(device=a_dev.device)
     ev = lambda: torch.cuda.Event()
+    t0 += 2
     with torch.cuda.stream(stream):
         # warm-up calls: build the cached one-step graphs of both buffer sets
         # outside the timed region
         for a, b in bufs:
-            a.copy_(host_in, non_blocking=True)
+            a.copy_(states[0], non_blocking=True)
             wmc.run(p, V, a, b, t0, 1, ws)
         wmc.reset_counters(p, ws)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        # hold the stream while the host enqueues the whole sequence, so that the
-        # events time the copies and steps, not this loop's Python
         torch.cuda._sleep(4_000_000)
         e0.record(stream)
-        free = [None, None]      # set k may be overwritten once its download is done
+        free = [None, None]
         done = []
         for q in range(n):
             k = q & 1
@@ -373,7 +418,7 @@ def end_to_end(wmc, torch, p, V, ws, stream, h0, t0, n=10):
             if free[k] is not None:
                 up.wait_event(free[k])
             with torch.cuda.stream(up):
-                a.copy_(host_in, non_blocking=True)
+                a.copy_(states[q % len(states)], non_blocking=True)
                 loaded = ev(); loaded.record(up)
             stream.wait_event(loaded)
             wmc.run(p, V, a, b, t0 + q, 1, ws)
@@ -389,16 +434,51 @@ def end_to_end(wmc, torch, p, V, ws, stream, h0, t0, n=10):
         stream.synchronize()
         c = wmc.get_counters(p, ws)
     secs = e0.elapsed_time(e1) * 1e-3
-    nbytes = h0.numel() * 4
+    nbytes = states[0].numel() * 4
     return {"value": c["particle_steps"] / secs, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "steps": n, "overlap": "copies on two streams, two buffer sets"}
+            "d2h_bytes_per_step": nbytes, "steps": n, "states": len(states),
+            "overlap": "copies on two streams, two buffer sets"}
+
+
+def _oracle_rows_worker(args):
+    """One process of the oracle kernel timing: FP64 rows of the given cells."""
+    import oracle as orc
+    wname, rows = args
+    w = wi.WORKLOADS[wname]
+    V = wi.potential(w)
+    t0 = time.perf_counter()
+    orc.kernel_rows(orc.params(w.replace(n_M=w.Q)), V, rows)
+    return time.perf_counter() - t0
+
+
+def oracle_kernel_rate(w, rows_single=512, rows_per_proc=256):
+    """The FP64 oracle kernel (Eq. wigner-1d-discrete, the direct window sum) in
+    cell x M evaluations per second: one thread, then one process per host core
+    (spawned) on their own rows."""
+    import multiprocessing as mp
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, w.n_x, rows_single)
+    t1 = _oracle_rows_worker((w.name, rows))
+    single = rows_single * w.Q / t1
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_rows_worker, [(w.name, rows[:8])] * cores)   # import and build in every worker
+        t0 = time.perf_counter()
+        pool.map(_oracle_rows_worker, [(w.name, rng.integers(0, w.n_x, rows_per_proc)) for _ in range(cores)])
+        tall = time.perf_counter() - t0
+    return {"single_thread": {"cellM_per_s": single, "rows": rows_single, "seconds": t1},
+            "all_cores": {"cellM_per_s": cores * rows_per_proc * w.Q / tall, "cores": cores,
+                          "rows": cores * rows_per_proc, "seconds": tall},
+            "note": "FP64 direct window sum, n_M = Q columns per row (one period)"}
 
 
 def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
     """The contraction on all 16384 cells of the double barrier (Q = n_M = 1024)
     in each precision form, timed alone with events (L2 flushed before each
     launch).  Algorithmic work: 2 (h-1)^2 flop per cell (distinct columns); the
-    split form issues three products per output (pipe work 3x)."""
+    split forms issue three products per output (pipe work 3x).  The FP64
+    oracle kernel is timed beside it on the host cores."""
     peaks, src = _peaks()
     w = wi.DOUBLE_BARRIER_16384
     p = wmc.Params.of(w)
@@ -443,7 +523,42 @@ def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
                                  "unit": "TFLOP/s", "frac": issued / sec / peak, "traffic": None,
                                  "peak_source": psrc}
             res[form] = r
-    return {"workload": f"{w.name}, all {w.n_x} cells, n_M = {w.n_M}", "forms": res}
+    try:
+        orc = oracle_kernel_rate(w)
+    except Exception as e:  # the timing is context; the GPU numbers stand without it
+        orc = {"unavailable": str(e)[:200]}
+    return {"workload": f"{w.name}, all {w.n_x} cells, n_M = {w.n_M}", "forms": res, "oracle_fp64": orc}
+
+
+def drift_only_rate(wmc, torch, dev, stream, flush, steps=20, warmup=4):
+    """Secondary leg, labelled drift-only: the 2000-cell barrier with 1e7
+    particles, whose packet starts farther than L_C / 2 from the barrier, so
+    its first steps create no pairs (drift, absorption and the histogram only)."""
+    w = wi.BARRIER_2000
+    p = wmc.Params.of(w)
+    V = torch.from_numpy(wi.potential(w)).to(dev)
+    a = torch.from_numpy(wi.initial_histogram(w)).to(dev)
+    b = torch.empty_like(a)
+    ws = wmc.workspace(p, dev)
+    tot = 0.0
+    with torch.cuda.stream(stream):
+        wmc.init(p, ws)
+        wmc.run(p, V, a, b, 1, warmup, ws)
+        wmc.reset_counters(p, ws)
+        t = 1 + warmup
+        for _ in range(steps // 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wmc.run(p, V, a, b, t, 2, ws)
+            e1.record(stream)
+            stream.synchronize()
+            tot += e0.elapsed_time(e1) * 1e-3
+            t += 2
+        c = wmc.get_counters(p, ws)
+    return {"workload": f"{w.name} (drift-only: no pairs in these steps)", "value": c["particle_steps"] / tot,
+            "unit": UNIT, "steps": 2 * (steps // 2), "ms_per_step": 1e3 * tot / (2 * (steps // 2)),
+            "pairs": c["pairs"]}
 
 
 def batched_rate(wmc, torch, dev, stream, n_sims=512, steps=20, warmup=2):
@@ -522,6 +637,8 @@ def single_leg(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     if args.leg == "kernel":
         out = kernel_eval_rate(wmc, torch, dev, stream, flush, reps=max(1, args.steps))
+    elif args.leg == "drift":
+        out = drift_only_rate(wmc, torch, dev, stream, flush)
     elif args.leg == "batched":
         out = batched_rate(wmc, torch, dev, stream, steps=max(2, args.steps), warmup=1)
     else:
@@ -538,8 +655,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="double-barrier-16384", choices=sorted(wi.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--leg", default="all", choices=["all", "kernel", "batched", "adjoint"],
+    ap.add_argument("--no-batched", action="store_true", help="skip the secondary legs (kernel, drift-only, "
+                    "batched, adjoint)")
+    ap.add_argument("--leg", default="all", choices=["all", "kernel", "drift", "batched", "adjoint"],
                     help="run one secondary leg alone (for profiling); 'all' is the benchmark")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

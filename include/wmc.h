@@ -163,6 +163,16 @@ wmc_status wmc_step_timing_read(float* ms);
 /* Reads the counters (synchronises the stream).  out [host]. */
 wmc_status wmc_get_counters(const wmc_params* p, const void* ws, wmc_counters* out, wmc_stream_t stream);
 
+/* The device conditions of the workspace as a status: synchronises the stream,
+ * reads the flags and writes to *device_status [host] WMC_ERR_TIMEOUT,
+ * WMC_ERR_CAPACITY or WMC_ERR_RATE (in that order of precedence) if the
+ * corresponding flag is set, else WMC_OK, and a NUL-terminated description
+ * into msg [host] of len bytes (may be NULL).  The flags stay set until
+ * wmc_reset_counters.  Returns WMC_ERR_ARG for bad arguments, WMC_ERR_CUDA if
+ * the read fails. */
+wmc_status wmc_get_error(const wmc_params* p, const void* ws, wmc_stream_t stream, wmc_status* device_status,
+                         char* msg, size_t len);
+
 /* ---------------------------------------------------------------------------
  * Kernel evaluation on given cells -- Eq. (wigner-1d-discrete) as the N = 1
  * analytic network of Sec. 2.2 (hidden units V(l) sin(theta_l), output weight
@@ -350,6 +360,17 @@ wmc_status wmc_materialize(const wmc_params* p, const int32_t* hist, uint32_t t,
  * out [dev] uint32[n][4].  The generator the step uses, exposed for checks. */
 wmc_status wmc_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int64_t n, uint32_t* out,
                              wmc_stream_t stream);
+
+/* Throughput probe of the generator (a measurement aid; the paper has no
+ * counterpart): n_threads threads (a multiple of 256) each evaluate
+ * 2 pairs_per_thread Philox4x32-10 calls, two at a time under one key
+ * schedule as the particle step does, on distinct counters (pairs_per_thread
+ * n_threads < 2^32), and write the XOR of all their words to out [dev]
+ * uint32[n_threads].  Timing it with events gives the calls per second the
+ * GPU sustains on the generator alone, the ceiling of the particle step's
+ * arithmetic.  Stream-ordered. */
+wmc_status wmc_philox_throughput(uint32_t key0, uint32_t key1, int32_t pairs_per_thread, uint32_t* out,
+                                 int64_t n_threads, wmc_stream_t stream);
 
 #ifdef __cplusplus
 }

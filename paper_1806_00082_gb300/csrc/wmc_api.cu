@@ -555,6 +555,42 @@ wmc_status wmc_materialize(const wmc_params* p, const int32_t* hist, uint32_t t,
   return cuda_status(launch_materialize(*p, v, hist, t, cell, f, M, sign, capacity, (cudaStream_t)stream));
 }
 
+wmc_status wmc_philox_throughput(uint32_t key0, uint32_t key1, int32_t pairs_per_thread, uint32_t* out,
+                                 int64_t n_threads, wmc_stream_t stream) {
+  if (!out || pairs_per_thread < 1 || n_threads < 256 || (n_threads % 256) != 0 || n_threads / 256 > 0x7fffffff)
+    return WMC_ERR_ARG;
+  if ((long long)pairs_per_thread * n_threads >= (1ll << 32)) return WMC_ERR_ARG;  // counters stay distinct
+  return cuda_status(launch_philox_throughput(key0, key1, pairs_per_thread, out, n_threads, (cudaStream_t)stream));
+}
+
+wmc_status wmc_get_error(const wmc_params* p, const void* ws, wmc_stream_t stream, wmc_status* device_status,
+                         char* msg, size_t len) {
+  if (!params_ok(p) || !ws || !device_status) return WMC_ERR_ARG;
+  wmc_counters c;
+  const wmc_status st = wmc_get_counters(p, ws, &c, stream);
+  if (st != WMC_OK) return st;
+  wmc_status d = WMC_OK;
+  const char* text = "no device condition";
+  if (c.flags & WMC_FLAG_TIMEOUT) {
+    d = WMC_ERR_TIMEOUT;
+    text = "a bounded device wait gave up (WMC_FLAG_TIMEOUT)";
+  } else if (c.flags & WMC_FLAG_CAPACITY) {
+    d = WMC_ERR_CAPACITY;
+    text = "population >= 2^32, work items or an output capacity exceeded (WMC_FLAG_CAPACITY)";
+  } else if (c.flags & WMC_FLAG_RATE) {
+    d = WMC_ERR_RATE;
+    text = "gamma dt >= 1 in an evaluated cell (WMC_FLAG_RATE)";
+  }
+  *device_status = d;
+  if (msg && len) {
+    size_t n = strlen(text);
+    if (n >= len) n = len - 1;
+    memcpy(msg, text, n);
+    msg[n] = '\0';
+  }
+  return WMC_OK;
+}
+
 wmc_status wmc_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int64_t n, uint32_t* out,
                              wmc_stream_t stream) {
   if (n < 0 || (n > 0 && (!ctr || !out))) return WMC_ERR_ARG;

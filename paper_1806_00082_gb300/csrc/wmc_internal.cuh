@@ -216,6 +216,8 @@ cudaError_t launch_materialize(const wmc_params& p, const View& v, const int32_t
 cudaError_t launch_density(const wmc_params& p, const int32_t* hist, int64_t* rho, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, long long n, uint32_t* out,
                           cudaStream_t s);
+cudaError_t launch_philox_throughput(uint32_t k0, uint32_t k1, int pairs_per_thread, uint32_t* out, long long n_threads,
+                                     cudaStream_t s);
 
 int num_sms();
 // Optional CUDA events around the particle-step kernel (wmc_step_timing): records

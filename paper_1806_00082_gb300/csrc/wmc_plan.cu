@@ -353,6 +353,29 @@ __global__ void k_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1
     out[q] = philox4x32_10(ctr[q], k0, k1);
 }
 
+// Throughput of the generator as the particle step uses it: each thread
+// evaluates calls in pairs under one key schedule (counters (q, 1, 2, 0) and
+// (q, 2, 1, 0) for distinct q) and folds every word into one XOR, written
+// out so that no evaluation can be dropped.
+__global__ __launch_bounds__(256) void k_philox_throughput(uint32_t k0, uint32_t k1, int pairs_per_thread,
+                                                           uint32_t* __restrict__ out) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  uint32_t acc = 0u;
+  for (int j = 0; j < pairs_per_thread; ++j) {
+    const uint32_t q = g + (uint32_t)j * gs;
+    uint4 a = make_uint4(q, 1u, 2u, 0u), b = make_uint4(q, 2u, 1u, 0u);
+    philox4x32_10_x2(a, b, k0, k1);
+    acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+  }
+  out[g] = acc;
+}
+
+cudaError_t launch_philox_throughput(uint32_t k0, uint32_t k1, int pairs_per_thread, uint32_t* out, long long n_threads,
+                                     cudaStream_t s) {
+  k_philox_throughput<<<(unsigned)(n_threads / 256), 256, 0, s>>>(k0, k1, pairs_per_thread, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, long long n, uint32_t* out,
                           cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

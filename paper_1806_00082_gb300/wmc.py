@@ -32,6 +32,7 @@ EXPORTS = (
     "wmc_kernel_eval_noalloc", "wmc_batch_workspace_size", "wmc_batch_layout", "wmc_batch_init", "wmc_batch_run",
     "wmc_batch_autotune", "wmc_batch_get_counters", "wmc_potential_tanh", "wmc_potential_tanh_vjp",
     "wmc_kernel_eval_rows", "wmc_kernel_vjp", "wmc_check_wait", "wmc_step_timing", "wmc_step_timing_read",
+    "wmc_get_error", "wmc_philox_throughput",
 )
 
 
@@ -137,6 +138,8 @@ def load(path: str | None = None):
             "wmc_potential_tanh_vjp": ([pp, vp, i32, i32, i32, ctypes.c_float, vp, vp, vp], i32),
             "wmc_kernel_eval_rows": ([pp, vp, i32, i32, vp, vp, vp], i32),
             "wmc_kernel_vjp": ([pp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
+            "wmc_get_error": ([pp, vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_char_p, ctypes.c_size_t], i32),
+            "wmc_philox_throughput": ([u32, u32, i32, vp, i64, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -213,6 +216,22 @@ def get_counters(p: Params, ws: torch.Tensor) -> dict:
     c = Counters()
     _check("wmc_get_counters", load().wmc_get_counters(ctypes.byref(p), _ptr(ws), ctypes.byref(c), _stream()))
     return c.as_dict()
+
+
+def get_error(p: Params, ws: torch.Tensor) -> tuple:
+    """(status code, message) of the workspace's device conditions; synchronises."""
+    st = ctypes.c_int32(0)
+    buf = ctypes.create_string_buffer(160)
+    _check("wmc_get_error", load().wmc_get_error(ctypes.byref(p), _ptr(ws), _stream(), ctypes.byref(st), buf,
+                                                   ctypes.sizeof(buf)))
+    return int(st.value), buf.value.decode()
+
+
+def philox_throughput(out: torch.Tensor, pairs_per_thread: int, key0: int = 1, key1: int = 2) -> None:
+    """Generator throughput probe: out.numel() threads (a multiple of 256), 2 pairs_per_thread calls each."""
+    _check("wmc_philox_throughput", load().wmc_philox_throughput(key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF,
+                                                                   int(pairs_per_thread), _ptr(out), out.numel(),
+                                                                   _stream()))
 
 
 def kernel_eval(p: Params, V: torch.Tensor, occ: torch.Tensor, ws: torch.Tensor, prec: int = FP32,

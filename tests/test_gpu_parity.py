@@ -465,3 +465,44 @@ def test_rate_flag(wmc):
     h0 = wi.initial_histogram(wl.replace(packet=wi.Packet(50e-9, 3e-9, 0.1, 1000)))
     _, c = gpu_run(wmc, torch, p, V, h0, 1, 1)
     assert c["flags"] & wmc.FLAG_RATE
+
+
+def test_get_error_maps_device_flags(wmc):
+    """wmc_get_error: no condition after a clean run, the rate condition after
+    gamma dt >= 1, the timeout condition after a bounded wait gives up (the
+    timeout takes precedence), and nothing after a counter reset."""
+    wl = wi.BARRIER_100.replace(dt_s=2e-15)
+    p = wmc.Params.of(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    code, msg = wmc.get_error(p, ws)
+    assert code == 0 and msg
+    V = torch.from_numpy(wi.potential(wl) * 50).cuda()
+    a = torch.from_numpy(wi.initial_histogram(wl.replace(packet=wi.Packet(50e-9, 3e-9, 0.1, 1000)))).cuda()
+    b = torch.empty_like(a)
+    wmc.run(p, V, a, b, 1, 1, ws, wmc.FP32, False)
+    code, msg = wmc.get_error(p, ws)
+    assert code == 3 and "gamma" in msg          # WMC_ERR_RATE
+    sig = torch.zeros(1, dtype=torch.int32, device="cuda")
+    wmc.check_wait(p, sig, 1_000_000, ws)
+    code, _ = wmc.get_error(p, ws)
+    assert code == 5                              # WMC_ERR_TIMEOUT
+    wmc.reset_counters(p, ws)
+    assert wmc.get_error(p, ws)[0] == 0
+
+
+def test_philox_throughput_probe_folds_the_generator(wmc):
+    """The throughput probe evaluates exactly the calls it claims: thread g
+    folds the words of counters (q, 1, 2, 0) and (q, 2, 1, 0), q = g + j G."""
+    out = torch.empty(512, dtype=torch.int32, device="cuda")
+    wmc.philox_throughput(out, 3, key0=0x1234, key1=0xabcdef)
+    got = out.cpu().numpy().view(np.uint32)
+    G = out.numel()
+    for g in (0, 1, 257, 511):
+        acc = 0
+        for j in range(3):
+            q = g + j * G
+            for ctr in ((q, 1, 2, 0), (q, 2, 1, 0)):
+                for wv in oracle.philox(ctr, (0x1234, 0xabcdef)):
+                    acc ^= int(wv)
+        assert int(got[g]) == acc

@@ -49,11 +49,12 @@ def test_single_process_reduction_is_identity():
 
 def test_step_work_count_per_step():
     """The particle-step kernel's Philox calls per step over one two-step
-    launch: a quarter call per survivor-step, a quarter per survivor of a reach
-    cell (first step exact, the launch's output for the second), one per pair."""
+    launch: a quarter call per survivor-step (offsets) and a quarter per
+    survivor of a reach cell (pair-creation words); the pair draws belong to
+    the pair kernel."""
     import bench
     c0 = {"particle_steps": 1000, "pairs": 10}
     c1 = {"particle_steps": 1000 + 2 * 400, "pairs": 10 + 6}
     got = bench.philox_calls(c0, c1, 40.0, 48.0)
-    assert got == (800 / 4 + (40 + 48) / 4 + 6) / 2
+    assert got == (800 / 4 + (40 + 48) / 4) / 2
     assert bench.philox_calls(c0, c0, 0.0, 0.0) == 0.0
