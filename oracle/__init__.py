@@ -9,6 +9,8 @@ Functions and the passages they follow:
 
 - :func:`kernel_rows` -- Eq. (wigner-1d-discrete): the finite-window discrete
   Wigner kernel, summed over m = -h..h (h = L_C / (2 dx)) in FP64.
+- :func:`kernel_rows_n2` -- Eq. (kernel_ML) with N = 2 and the barycentric
+  weights of Sec. 2.3: consecutive cells grouped in pairs, FP64.
 - :func:`cdf_row` -- Eq. (momentum_integral): gamma as the sum of V_W^+ over M
   and the CDF for drawing p' ~ V_W^+ / gamma, as exact sums of V_W^+ quantised
   to 62-bit fixed point relative to the row maximum.
@@ -97,6 +99,7 @@ def _load():
         lib.wmco_kernel_value.argtypes = [pp, f64p, ctypes.c_int32, ctypes.c_int32]
         lib.wmco_kernel_value.restype = ctypes.c_double
         lib.wmco_kernel_rows.argtypes = [pp, f64p, ctypes.c_int32, i32p, f64p]
+        lib.wmco_kernel_rows_n2.argtypes = [pp, f64p, ctypes.c_int32, i32p, f64p]
         lib.wmco_cdf_row.argtypes = [ctypes.c_int32, f64p, i64p, i32p]
         lib.wmco_cdf_row.restype = ctypes.c_double
         lib.wmco_sample_row.argtypes = [ctypes.c_int32, i64p, ctypes.c_uint64]
@@ -159,6 +162,17 @@ def kernel_rows(p: Params, V: np.ndarray, rows) -> np.ndarray:
     out = np.zeros((r.size, p.n_M), dtype=np.float64)
     _load().wmco_kernel_rows(ctypes.byref(p), _ptr(V64, ctypes.c_double), r.size, _ptr(r, ctypes.c_int32),
                              _ptr(out, ctypes.c_double))
+    return out
+
+
+def kernel_rows_n2(p: Params, V: np.ndarray, rows) -> np.ndarray:
+    """The N = 2 barycentric network of Eq. (kernel_ML) (Sec. 2.3):
+    V_W2(rows[r]; k - n_M/2) for k in [0, n_M), array [len(rows), n_M] in 1/s."""
+    V64 = np.ascontiguousarray(V, dtype=np.float64)
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.zeros((r.size, p.n_M), dtype=np.float64)
+    _load().wmco_kernel_rows_n2(ctypes.byref(p), _ptr(V64, ctypes.c_double), r.size, _ptr(r, ctypes.c_int32),
+                                _ptr(out, ctypes.c_double))
     return out
 
 

@@ -178,6 +178,42 @@ void wmco_kernel_rows(const wmco_params* p, const double* V, int32_t n_rows, con
   free(dV);
 }
 
+/* The N = 2 network of Eq. (kernel_ML) with the barycentric weights of Sec. 2.3
+ * (omega^V = (1, 1), omega^theta = (1/2, 1/2), W_l = w_l = -2 dx / (hbar L_C),
+ * one cosine factor since N = 2^1): the terms V(l) sin(theta_l(i, j)) of the
+ * N = 1 network are grouped by consecutive cells (2q, 2q + 1), V is replaced by
+ * the pair's average and sin a + sin b = 2 sin((a + b)/2) cos((a - b)/2), so
+ *   V_W2(i; M) = -(2 / (hbar Q)) cos(pi M / Q)
+ *                sum_{q: i-h <= 2q, 2q+1 <= i+h} [V(2q) + V(2q+1)] sin(pi (4q + 1 - 2i) M / Q),
+ * theta_l(i, j) = (l - i) 2 pi M / Q.  The pairs lie inside the window
+ * [i - h, i + h]; the one cell of the window left out has a zero sine.
+ * Sines of the period-2Q integer phases sin(2 pi t / (2Q)), t exact mod 2Q. */
+void wmco_kernel_rows_n2(const wmco_params* p, const double* V, int32_t n_rows, const int32_t* rows,
+                         double* out) {
+  const int32_t Q = p->Q, h = Q / 2, Q2 = 2 * Q;
+  double* S2 = (double*)malloc(sizeof(double) * (size_t)Q2);
+  for (int32_t t = 0; t < Q2; ++t) S2[t] = wmco_sine(Q2, t);
+  for (int32_t r = 0; r < n_rows; ++r) {
+    const int64_t i = rows[r];
+    /* first pair: the smallest even 2q >= i - h */
+    int64_t q0 = i - h;
+    if (q0 % 2 != 0) q0 += 1;            /* (works for negative q0 as well: |q0 % 2| = 1) */
+    for (int32_t k = 0; k < p->n_M; ++k) {
+      const int64_t M = k - p->n_M / 2;
+      double acc = 0.0;
+      for (int64_t l = q0; l + 1 <= i + h; l += 2) {
+        int64_t t = ((2 * (l - i) + 1) * M) % Q2;
+        if (t < 0) t += Q2;
+        acc += (pot(p, V, l) + pot(p, V, l + 1)) * S2[t];
+      }
+      int64_t tc = (M + h) % Q2;          /* cos(pi M / Q) = sin(2 pi (M + Q/2) / (2Q)) */
+      if (tc < 0) tc += Q2;
+      out[(int64_t)r * p->n_M + k] = -(2.0 / (WMCO_HBAR_EVS * (double)Q)) * S2[tc] * acc;
+    }
+  }
+  free(S2);
+}
+
 /* Smallest L with 2^L >= n. */
 static int32_t ceil_log2(int32_t n) {
   int32_t L = 0;

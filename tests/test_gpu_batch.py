@@ -94,3 +94,39 @@ def test_batch_matches_oracle_where_kernel_is_zero(wmc):
     for s, w in enumerate(wls):
         ref, _ = oracle.simulate(oracle.params(w), wi.initial_histogram(w), 1, 4, V=wi.potential(w))
         np.testing.assert_array_equal(got[ho[s]:ho[s + 1]].reshape(w.n_x, w.n_M), ref)
+
+
+def test_batch_with_pairs_matches_oracle_bit_exact(wmc):
+    """A batch whose simulations create pairs (n_M 128 and 256, packets next to
+    their barriers), every simulation compared bit for bit with the CPU oracle
+    fed the FP32 kernel values of that simulation (wmc_kernel_eval, the values
+    the solo and batched steps use) and the same Philox streams; the batch's
+    counters equal the sums of the oracle's."""
+    from tests._util import full_from_half
+    wls = wi.batch_workloads(8, seed=21, n_x_range=(150, 600), n0_range=(20_000, 80_000))
+    for s in range(len(wls)):
+        w = wls[s]
+        side = -1 if s % 2 else 1
+        wls[s] = w.replace(packet=wi.Packet(w.length_m / 2 + side * 9e-9, 4e-9, 0.05 + 0.02 * (s % 3),
+                                            w.packet.n0))
+    assert {w.n_M for w in wls} == {128, 256}
+    ps, co, ho, V, H = _batch(wmc, wls)
+    steps = 6
+    got, c = _run_batch(wmc, ps, V, H, 1, steps)
+    tot = {"pairs": 0, "absorbed": 0, "dropped": 0, "particle_steps": 0}
+    for s, w in enumerate(wls):
+        p = wmc.Params.of(w)
+        ws = wmc.workspace(p)
+        wmc.init(p, ws)
+        occ = torch.arange(w.n_x, dtype=torch.int32, device="cuda")
+        half = wmc.kernel_eval(p, torch.from_numpy(wi.potential(w)).cuda(), occ, ws).cpu().numpy()
+        ref, st = oracle.simulate(oracle.params(w), wi.initial_histogram(w), 1, steps,
+                                  table=full_from_half(half, w.Q, w.n_M))
+        np.testing.assert_array_equal(got[ho[s]:ho[s + 1]].reshape(w.n_x, w.n_M), ref)
+        tot["pairs"] += int(st[oracle.ST_PAIRS])
+        tot["absorbed"] += int(st[oracle.ST_ABSORBED])
+        tot["dropped"] += int(st[oracle.ST_DROPPED])
+        tot["particle_steps"] += int(st[oracle.ST_PARTICLE_STEPS])
+    for k, v in tot.items():
+        assert c[k] == v, k
+    assert tot["pairs"] > 1000
