@@ -523,11 +523,33 @@ def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
                                  "unit": "TFLOP/s", "frac": issued / sec / peak, "traffic": None,
                                  "peak_source": psrc}
             res[form] = r
+    # the N = 2 barycentric network (Sec. 2.3) on the same cells
+    n2 = {}
+    with torch.cuda.stream(stream):
+        for form in ("fp32", "bf16", "fp16", "fp16_split"):
+            prec = wmc.PRECISIONS[form]
+            for _ in range(3):
+                wmc.kernel_eval_n2(p, V, occ, ws, prec=prec, out=out)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                wmc.kernel_eval_n2(p, V, occ, ws, prec=prec, out=out)
+                e1.record(stream)
+                stream.synchronize()
+                tot += e0.elapsed_time(e1) * 1e-3
+            sec = tot / reps
+            n2[form] = {"seconds": sec, "cellM_per_s": w.n_x * w.n_M / sec,
+                        "vs_n1_same_form": res[form]["seconds"] / sec, "err_bound_normwise_vs_fp64_n2": bounds[form]}
     try:
         orc = oracle_kernel_rate(w)
     except Exception as e:  # the timing is context; the GPU numbers stand without it
         orc = {"unavailable": str(e)[:200]}
-    return {"workload": f"{w.name}, all {w.n_x} cells, n_M = {w.n_M}", "forms": res, "oracle_fp64": orc}
+    return {"workload": f"{w.name}, all {w.n_x} cells, n_M = {w.n_M}", "forms": res, "oracle_fp64": orc,
+            "n2_network": {"note": "N = 2 barycentric network of Sec. 2.3 (h pair terms against the N = 1 form's "
+                                   "h - 1 folded differences); errors against the FP64 N = 2 oracle",
+                           "forms": n2}}
 
 
 def drift_only_rate(wmc, torch, dev, stream, flush, steps=20, warmup=4):

@@ -206,6 +206,27 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
 wmc_status wmc_kernel_eval_noalloc(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
                                    float* VWh, wmc_stream_t stream);
 
+/* The N = 2 network of Sec. 2.3 -- Eq. (kernel_ML) with N = 2 and the
+ * barycentric weights (omega^V = (1, 1), omega^theta = (1/2, 1/2),
+ * W_l = w_l = -2 dx / (hbar L_C), one cosine factor): the terms V(l) sin(theta_l)
+ * of the N = 1 network are grouped by consecutive cells (2q, 2q + 1), the
+ * potential of a pair replaced by its average, so that
+ *   V_W2(i; M) = -(2 / (hbar Q)) cos(pi M / Q)
+ *                sum_{pairs (2q, 2q+1) in [i - h, i + h]} [V(2q) + V(2q+1)] sin(pi (4q + 1 - 2i) M / Q),
+ * half as many sines as the N = 1 network's 2h + 1 terms.  It is odd and
+ * Q-periodic in M and zero at M = 0 and M = h, so rows use the same
+ * half-period layout; it equals wmc_kernel_eval where V is constant on every
+ * pair of cells and approaches it to first order in dx for a smooth V.
+ * Evaluated as a contraction of the signed pair sums A(i, u) (u = 0 .. h - 1:
+ * V(i+u) + V(i+u+1) if i + u is even, else -(V(i-u-1) + V(i-u))) with
+ * cos(pi r / Q) sin(pi (2u + 1) r / Q).
+ *   V, occ, n_occ, VWh, ws as for wmc_kernel_eval.
+ *   prec WMC_FP32, WMC_BF16, WMC_FP16 or WMC_FP16_SPLIT (WMC_TF32X3 and
+ *        windows whose operands do not fit return WMC_ERR_UNSUPPORTED).
+ * The rows can drive the simulation through wmc_kernel_table_occupied. */
+wmc_status wmc_kernel_eval_n2(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
+                              wmc_precision prec, float* VWh, void* ws, wmc_stream_t stream);
+
 /* gamma and the momentum CDF of kernel rows -- Eq. (momentum_integral) and the
  * postulate's draw of p' with probability V_W^+ / gamma.  The positive parts
  * x_k = max(V_W(k), 0) of a row are quantised relative to the row maximum:

@@ -34,6 +34,7 @@ Layout layout(const wmc_params& p) {
   L.Kp = ((L.h - 1 + 31) / 32) * 32;
   if (L.Kp == 0) L.Kp = 32;
   L.Np = ((L.h + 63) / 64) * 64;
+  L.Kp2 = ((L.h + 31) / 32) * 32;
   size_t o = 0;
   L.header = o; o = align256(o + sizeof(DevHeader));
   L.T = o; o = align256(o + sizeof(unsigned long long) * nx);
@@ -61,6 +62,7 @@ Layout layout(const wmc_params& p) {
   }
   L.pairs = o; o = align256(o + sizeof(uint4) * (size_t)L.pair_cap);
   L.B = o; o = align256(o + sizeof(float) * (size_t)L.Kp * (size_t)L.Np);
+  L.B2 = o; o = align256(o + sizeof(float) * (size_t)L.Kp2 * (size_t)L.Np);
   L.tc = o; o = align256(o + tc_images_bytes(p));
   L.plan = o; o = align256(o + sizeof(PlanStatus) * ((nx + kPlanCells - 1) / kPlanCells));
   L.total = o;
@@ -90,6 +92,7 @@ View view(const wmc_params& p, void* ws) {
   v.items = reinterpret_cast<int2*>(b + L.items);
   v.pairs = reinterpret_cast<uint4*>(b + L.pairs);
   v.B = reinterpret_cast<float*>(b + L.B);
+  v.B2 = reinterpret_cast<float*>(b + L.B2);
   v.tc = b + L.tc;
   v.plan = reinterpret_cast<PlanStatus*>(b + L.plan);
   return v;
@@ -451,6 +454,27 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
     return cuda_status(launch_kernel_rows_small(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, nullptr, nullptr,
                                                 nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream));
   return cuda_status(launch_kernel_eval(*p, V, occ, nullptr, n_occ, n_occ, v.B, VWh, (cudaStream_t)stream));
+}
+
+wmc_status wmc_kernel_eval_n2(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
+                              wmc_precision prec, float* VWh, void* ws, wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_kernel_eval_n2");
+  if (!params_ok(p) || !V || !ws || n_occ < 0 || (n_occ > 0 && (!occ || !VWh))) return WMC_ERR_ARG;
+  if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
+  if (prec == WMC_TF32X3) return WMC_ERR_UNSUPPORTED;
+  if (n_occ == 0) return WMC_OK;
+  const View v = view(*p, ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (prec != WMC_FP32)
+    e = launch_kernel_eval_tc(*p, (int)prec, V, occ, nullptr, n_occ, n_occ, v.tc, VWh, &v.hdr->flags, s, 2);
+  else if (small_window(*p))
+    e = launch_kernel_rows_small(*p, V, occ, nullptr, n_occ, n_occ, v.B2, VWh, nullptr, nullptr, nullptr, nullptr,
+                                 nullptr, nullptr, s, nullptr, nullptr, 2);
+  else
+    e = launch_kernel_eval(*p, V, occ, nullptr, n_occ, n_occ, v.B2, VWh, s, 2);
+  if (e == cudaErrorNotSupported) return WMC_ERR_UNSUPPORTED;
+  return cuda_status(e);
 }
 
 wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows, int64_t* cdf, double* gamma,

@@ -186,13 +186,7 @@ __global__ void k_b_init(const SimDesc* __restrict__ d, int n, long long n_cells
   for (long long e = tid; e < sine_elems; e += nt) {
     const SimDesc& s = d[owner(d, n, e, 2)];
     const long long q = e - s.sine_off;
-    const int kk = (int)(q / s.Np), r = (int)(q % s.Np);
-    float v = 0.f;
-    if (kk < s.h - 1 && r < s.h) {
-      const long long t = ((long long)(kk + 1) * r) % s.Q;
-      v = __double2float_rn(sinpi(2.0 * (double)t / (double)s.Q));
-    }
-    sine[e] = v;
+    sine[e] = sine_entry_n1(s.Q, (int)(q / s.Np), (int)(q % s.Np));
   }
 }
 

@@ -7,10 +7,50 @@
 
 namespace wmc {
 
+// Entry (kk, r) of the sine matrix of the N = 1 network (the folded window sum
+// of Eq. wigner-1d-discrete): sin(2 pi ((kk+1) r mod Q) / Q) for kk < h-1,
+// r < h (term m = kk + 1, half-period column r), zero elsewhere.  Every
+// kernel and operand image takes its sine values from here.
+__device__ __forceinline__ float sine_entry_n1(int Q, int kk, int r) {
+  const int h = Q / 2;
+  if (kk >= h - 1 || r >= h) return 0.f;
+  const long long t = ((long long)(kk + 1) * r) % Q;
+  return __double2float_rn(sinpi(2.0 * (double)t / (double)Q));
+}
+
+// Entry (u, r) of the matrix of the N = 2 barycentric network in its folded
+// form (Eq. kernel_ML with N = 2): cos(pi r / Q) sin(pi ((2u+1) r mod 2Q) / Q)
+// for u < h, r < h (pair offset u, half-period column r), zero elsewhere; the
+// product is formed in FP64 and rounded once.
+__device__ __forceinline__ float sine_entry_n2(int Q, int u, int r) {
+  const int h = Q / 2;
+  if (u >= h || r >= h) return 0.f;
+  const long long t = ((long long)(2 * u + 1) * r) % (2ll * Q);
+  return __double2float_rn(cospi((double)r / (double)Q) * sinpi((double)t / (double)Q));
+}
+
 __device__ __forceinline__ float pot(const float* __restrict__ V, int n_x, int bc, long long l) {
   if (l >= 0 && l < n_x) return __ldg(V + l);
   if (!bc) return 0.f;
   return __ldg(V + (l < 0 ? 0 : n_x - 1));
+}
+
+// Term idx of the contraction's A operand for cell i of potential V: the N = 1
+// network's difference V(i + m) - V(i - m), m = idx + 1 (zero from idx = h - 1
+// on), or the N = 2 network's signed pair sum at offset u = idx:
+// V(i+u) + V(i+u+1) if i + u is even, else -(V(i-u-1) + V(i-u)) (zero from
+// idx = h on); the pair at u and its mirror at -u-1 have opposite sines and
+// exactly one of them starts at an even cell.
+template <int NET>
+__device__ __forceinline__ float a_term(const float* __restrict__ V, int n_x, int bc, int h, long long i, int idx) {
+  if (NET == 1) {
+    const int m = idx + 1;
+    return m <= h - 1 ? __fsub_rn(pot(V, n_x, bc, i + m), pot(V, n_x, bc, i - m)) : 0.f;
+  }
+  const int u = idx;
+  if (u > h - 1) return 0.f;
+  return ((i + u) & 1) == 0 ? __fadd_rn(pot(V, n_x, bc, i + u), pot(V, n_x, bc, i + u + 1))
+                            : -__fadd_rn(pot(V, n_x, bc, i - u - 1), pot(V, n_x, bc, i - u));
 }
 
 // Error-free transformation of a + b (Knuth's TwoSum): s + e == a + b exactly.

@@ -97,12 +97,13 @@ struct PlanStatus {
 // Byte offsets of the workspace regions (all 256-aligned).
 struct Layout {
   size_t header, T, R, IP, reach, occ, row_map, VWh, ccdf, scale, gamma, gthr, thr_cell, D, xlo, xhi, items, pairs, B,
-      tc, plan, total;
+      B2, tc, plan, total;
   long long max_items;
   unsigned pair_cap;  // entries of the pair queue
   int h;     // Q / 2
   int Kp;    // contraction length h - 1 padded to a multiple of 32
   int Np;    // output columns h padded to a multiple of 64
+  int Kp2;   // contraction length h of the N = 2 network padded to a multiple of 32
 };
 
 bool params_ok(const wmc_params* p);
@@ -129,6 +130,7 @@ struct View {
   int2* items;             // [max_items] work items (cell, chunk)
   uint4* pairs;            // [pair_cap] pair events (id, cell, column, sign < 0) queued by the step
   float* B;                // [Kp][Np] sine matrix S[m][r], m = kk + 1
+  float* B2;               // [Kp2][Np] folded matrix of the N = 2 network, pair offset u
   void* tc;                // tensor-core operand images of S (BF16, FP16 hi, FP16 lo)
   PlanStatus* plan;        // [ceil(n_x / kPlanCells)] published prefixes of the plan's blocks
 };
@@ -185,8 +187,11 @@ cudaError_t launch_rows(const wmc_params& p, const View& v, const int32_t* hist,
                         int32_t* zero_out);
 cudaError_t launch_plan_scan(const wmc_params& p, const View& v, int advance_step, int clear_thr, cudaStream_t s);
 int step_grid(int n_M);
+// (net 1: the N = 1 network with B = the sine matrix; net 2: the N = 2
+// network with B = its folded matrix B2)
 cudaError_t launch_kernel_eval(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
-                               int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s);
+                               int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s,
+                               int net = 1);
 // Fused kernel row + fixed-point CDF for small windows (Q/2 <= 128); the CDF
 // outputs may all be null (kernel rows only).
 bool small_window(const wmc_params& p);
@@ -194,7 +199,7 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
                                      int n_occ_host, int max_rows, const float* B, float* VWh, long long* ccdf,
                                      int* scale, double* gamma, unsigned long long* gthr,
                                      unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s,
-                                     const unsigned char* reach = nullptr, DevHeader* hdr = nullptr);
+                                     const unsigned char* reach = nullptr, DevHeader* hdr = nullptr, int net = 1);
 cudaError_t launch_gather_table(const wmc_params& p, const float* table, const int* occ, const int* n_occ_dev,
                                 int max_rows, float* VWh, cudaStream_t s);
 // Tensor-core contraction (BF16, FP16, FP16 hi/lo split).
@@ -202,7 +207,7 @@ size_t tc_images_bytes(const wmc_params& p);
 cudaError_t launch_init_tc_images(const wmc_params& p, void* images, cudaStream_t s);
 cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V, const int* occ, const int* n_occ_dev,
                                   int n_occ_host, int max_rows, const void* images, float* VWh, unsigned int* flags,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int net = 1);
 // CDF of rows: row-major cdf[row][n_M] and/or the coarse form ccdf[row][kCdfBlocks];
 // cdf/ccdf/scale/gthr/thr_cell/flags may be null.
 cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_dev, int n_rows_host,

@@ -19,6 +19,7 @@ namespace wmc {
 // level of one 32-term chunk instead of growing with the window length.
 constexpr int BM = 64, BN = 64, BK = 32;
 
+template <int NET>
 __global__ __launch_bounds__(256) void k_kernel_eval_fp32(const float* __restrict__ V, int n_x, int bc, int Q,
                                                           const int* __restrict__ occ,
                                                           const int* __restrict__ n_occ_dev, int n_occ_host,
@@ -50,9 +51,7 @@ __global__ __launch_bounds__(256) void k_kernel_eval_fp32(const float* __restric
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int kk = (tid >> 6) + 4 * q;
-      const int m = k0 + kk + 1;
-      float v = 0.f;
-      if (m <= h - 1) v = __fsub_rn(pot(Va, n_x, bc, (long long)a_cell + m), pot(Va, n_x, bc, (long long)a_cell - m));
+      const float v = a_term<NET>(Va, n_x, bc, h, a_cell, k0 + kk);
       As[kk][ar] = v;
     }
 #pragma unroll
@@ -100,13 +99,17 @@ __global__ __launch_bounds__(256) void k_kernel_eval_fp32(const float* __restric
 }
 
 cudaError_t launch_kernel_eval(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
-                               int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s) {
+                               int n_occ_host, int max_rows, const float* B, float* VWh, cudaStream_t s, int net) {
   if (max_rows <= 0) return cudaSuccess;
   const Layout L = layout(p);
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   dim3 grid((max_rows + BM - 1) / BM, (L.h + BN - 1) / BN);
-  k_kernel_eval_fp32<<<grid, 256, 0, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host, B, L.Kp, L.Np,
-                                          c, VWh);
+  if (net == 2)
+    k_kernel_eval_fp32<2><<<grid, 256, 0, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host, B, L.Kp2,
+                                               L.Np, c, VWh);
+  else
+    k_kernel_eval_fp32<1><<<grid, 256, 0, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host, B, L.Kp,
+                                               L.Np, c, VWh);
   return cudaGetLastError();
 }
 
@@ -302,7 +305,7 @@ constexpr int kRowMaxH = 128;
 
 // A warp accumulates R rows together, sharing each sine load among them (R = 4
 // when there are rows enough to fill the GPU that way, else 1).
-template <int C, int R>  // output columns per lane: h <= 32 C
+template <int C, int R, int NET>  // output columns per lane: h <= 32 C; NET 1 or 2
 __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
     const float* __restrict__ V, int n_x, int bc, int Q, int n_M, int log2_nM, const int* __restrict__ occ,
     const int* __restrict__ n_occ_dev, int n_occ_host, const float* __restrict__ B, int Np, float c,
@@ -314,10 +317,11 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
   // and a zero event threshold
   extern __shared__ float s_mem[];
   const int h = Q / 2;
+  const int Kt = NET == 1 ? h - 1 : h;  // terms of the contraction
   if (hdr && blockIdx.x == 0 && threadIdx.x == 0) hdr->rows_by_cell = reach ? 1u : 0u;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* s_B = s_mem;                                             // (h - 1) x h, row m - 1
-  float* s_row = s_mem + (h - 1) * h + wid * (R + 1) * 32 * C;    // kernel row (h floats)
+  float* s_B = s_mem;                                             // Kt x h, row = term
+  float* s_row = s_mem + Kt * h + wid * (R + 1) * 32 * C;         // kernel row (h floats)
   float* s_dv = s_row + 32 * C;                                   // row g: dV(m) at s_dv[g 32 C + m - 1]
   const int n_rows = n_occ_dev ? *n_occ_dev : n_occ_host;
   if ((int)(blockIdx.x * kRowWarps * R) >= n_rows) return;
@@ -335,12 +339,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
       const int rw = (int)((blockIdx.x * kRowWarps + wid) * R) + g;
       if (rw < n_rows && cell_needs_kernel(reach, rw, n_x)) row_ok |= 1u << g;
 #pragma unroll
-      for (int q = 0; q < C; ++q) {
-        const int m = lane + 1 + 32 * q;
-        dv[g][q] = (rw < n_rows && m <= h - 1)
-                       ? __fsub_rn(pot(V, n_x, bc, (long long)rw + m), pot(V, n_x, bc, (long long)rw - m))
-                       : 0.f;
-      }
+      for (int q = 0; q < C; ++q) dv[g][q] = rw < n_rows ? a_term<NET>(V, n_x, bc, h, rw, lane + 32 * q) : 0.f;
     }
 #pragma unroll
     for (int g = 0; g < R; ++g) {
@@ -374,7 +373,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
   }
   if (stage_B) {
     // stage the sine rows with eight loads in flight per thread
-    const int nB = (h - 1) * h;
+    const int nB = Kt * h;
     for (int q0 = threadIdx.x; q0 < nB; q0 += 8 * kRowWarps * 32) {
       float tmp[8];
 #pragma unroll
@@ -400,12 +399,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
       const int i = ok ? (occ ? __ldg(occ + row) : row % n_x) : 0;
       const float* Vr = (occ || !ok) ? V : V + (size_t)(row / n_x) * n_x;
 #pragma unroll
-      for (int q = 0; q < C; ++q) {
-        const int m = lane + 1 + 32 * q;
-        s_dv[g * 32 * C + m - 1] =
-            (ok && m <= h - 1) ? __fsub_rn(pot(Vr, n_x, bc, (long long)i + m), pot(Vr, n_x, bc, (long long)i - m))
-                               : 0.f;
-      }
+      for (int q = 0; q < C; ++q) s_dv[g * 32 * C + lane + 32 * q] = ok ? a_term<NET>(Vr, n_x, bc, h, i, lane + 32 * q) : 0.f;
     }
     bool nz = false;  // rows over a flat potential are exactly zero: skip the sums
 #pragma unroll
@@ -419,15 +413,15 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
     for (int g = 0; g < R; ++g)
 #pragma unroll
       for (int cc = 0; cc < C; ++cc) sacc[g][cc] = eacc[g][cc] = 0.f;
-    for (int m0 = 1; nz && m0 <= h - 1; m0 += 32) {   // chunks of 32 window terms
+    for (int j0 = 0; nz && j0 < Kt; j0 += 32) {   // chunks of 32 window terms
       float part[R][C];
 #pragma unroll
       for (int g = 0; g < R; ++g)
 #pragma unroll
         for (int cc = 0; cc < C; ++cc) part[g][cc] = 0.f;
-      const int m1 = min(m0 + 32, h);
-      for (int m = m0; m < m1; ++m) {
-        const float* brow = s_B + (m - 1) * h;
+      const int j1 = min(j0 + 32, Kt);
+      for (int j = j0; j < j1; ++j) {
+        const float* brow = s_B + j * h;
         float b[C];
 #pragma unroll
         for (int cc = 0; cc < C; ++cc) {
@@ -436,7 +430,7 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
         }
 #pragma unroll
         for (int g = 0; g < R; ++g) {
-          const float d = s_dv[g * 32 * C + m - 1];
+          const float d = s_dv[g * 32 * C + j];
 #pragma unroll
           for (int cc = 0; cc < C; ++cc) part[g][cc] = fmaf(d, b[cc], part[g][cc]);
         }
@@ -491,33 +485,38 @@ __global__ __launch_bounds__(kRowWarps * 32) void k_kernel_rows_small(
 
 bool small_window(const wmc_params& p) { return p.Q / 2 <= kRowMaxH; }
 
-static size_t rows_small_smem(int h, int R) {
+static size_t rows_small_smem(int h, int R, int net) {
   const int C = h <= 32 ? 1 : (h <= 64 ? 2 : 4);
-  return sizeof(float) * ((size_t)(h - 1) * h + (size_t)kRowWarps * (R + 1) * 32 * C);
+  const int Kt = net == 2 ? h : h - 1;
+  return sizeof(float) * ((size_t)Kt * h + (size_t)kRowWarps * (R + 1) * 32 * C);
 }
 
 cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const int* occ, const int* n_occ_dev,
                                      int n_occ_host, int max_rows, const float* B, float* VWh, long long* ccdf,
                                      int* scale, double* gamma, unsigned long long* gthr,
                                      unsigned long long* thr_cell, unsigned int* flags, cudaStream_t s,
-                                     const unsigned char* reach, DevHeader* hdr) {
+                                     const unsigned char* reach, DevHeader* hdr, int net) {
   if (max_rows <= 0) return cudaSuccess;
   const Layout L = layout(p);
   const int h = L.h;
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   const int R = (long long)max_rows >= 2ll * num_sms() * kRowWarps * 4 ? 4 : 1;
-  const size_t sm = rows_small_smem(h, R);
+  const size_t sm = rows_small_smem(h, R, net);
   int blocks = (max_rows + kRowWarps * R - 1) / (kRowWarps * R);
   if (blocks > 2 * num_sms()) blocks = 2 * num_sms();
   const int lg = ceil_log2(p.n_M);
-#define WMC_LAUNCH_ROWS(CC, RR)                                                                                   \
+#define WMC_LAUNCH_ROWS_NET(CC, RR, NN)                                                                           \
   do {                                                                                                            \
     if (sm > 48 * 1024)                                                                                           \
-      cudaFuncSetAttribute(k_kernel_rows_small<CC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);    \
-    k_kernel_rows_small<CC, RR><<<blocks, kRowWarps * 32, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, p.n_M, lg, occ, \
-                                                                   n_occ_dev, n_occ_host, B, L.Np, c, VWh, ccdf,  \
-                                                                   scale, gamma, gthr, thr_cell, flags, p.dt_s,   \
-                                                                   reach, hdr);                                   \
+      cudaFuncSetAttribute(k_kernel_rows_small<CC, RR, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);\
+    k_kernel_rows_small<CC, RR, NN><<<blocks, kRowWarps * 32, sm, s>>>(                                           \
+        V, p.n_x, p.bc_potential, p.Q, p.n_M, lg, occ, n_occ_dev, n_occ_host, B, L.Np, c, VWh, ccdf, scale,       \
+        gamma, gthr, thr_cell, flags, p.dt_s, reach, hdr);                                                        \
+  } while (0)
+#define WMC_LAUNCH_ROWS(CC, RR)                     \
+  do {                                              \
+    if (net == 2) WMC_LAUNCH_ROWS_NET(CC, RR, 2);   \
+    else WMC_LAUNCH_ROWS_NET(CC, RR, 1);            \
   } while (0)
   if (R == 4) {
     if (h <= 32) WMC_LAUNCH_ROWS(1, 4);
@@ -529,6 +528,7 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
     else WMC_LAUNCH_ROWS(4, 1);
   }
 #undef WMC_LAUNCH_ROWS
+#undef WMC_LAUNCH_ROWS_NET
   return cudaGetLastError();
 }
 

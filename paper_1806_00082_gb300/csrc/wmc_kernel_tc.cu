@@ -31,7 +31,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
-#include "wmc_internal.cuh"
+#include "wmc_device.cuh"
 
 namespace wmc {
 
@@ -194,6 +194,22 @@ __device__ __forceinline__ float potential_at(const float* __restrict__ V, int n
   return __ldg(V + (l < 0 ? 0 : n_x - 1));
 }
 
+// Entry (row, kk) of the A operand: the N = 1 network's potential difference
+// V(i + m) - V(i - m), m = kk + 1 (zero beyond m = h - 1), or the N = 2
+// network's signed pair sum at offset u = kk: V(i+u) + V(i+u+1) if i + u is
+// even, else -(V(i-u-1) + V(i-u)) (zero beyond u = h - 1).  From a staged
+// window w (w[h + j] = V(i + j)) or from the potential itself.
+template <int NET>
+__device__ __forceinline__ float a_entry_window(const float* w, int h, int i, int kk) {
+  if (NET == 1) {
+    const int m = kk + 1;
+    return m <= h - 1 ? __fsub_rn(w[h + m], w[h - m]) : 0.f;
+  }
+  const int u = kk;
+  if (u > h - 1) return 0.f;
+  return ((i + u) & 1) == 0 ? __fadd_rn(w[h + u], w[h + u + 1]) : -__fadd_rn(w[h - u - 1], w[h - u]);
+}
+
 // Byte offset of element (row, k) of a 128 x 64 K-major operand block in the
 // 128-byte swizzled layout (row r at 128 r, chunk k / 8 stored at chunk
 // (k / 8) ^ (r % 8)); blocks of consecutive rows concatenate.
@@ -218,8 +234,7 @@ __device__ __forceinline__ float from_bits(uint16_t b, int prec) {
 // (zero outside m < h, r < h), rounded to BF16 (img_bf16), FP16 (img_hi) and the
 // FP16 residual scaled by 2^11 (img_lo).
 __global__ void k_init_tc_images(int Q, int KB, int NT, uint16_t* __restrict__ img_bf16,
-                                 uint16_t* __restrict__ img_hi, uint16_t* __restrict__ img_lo) {
-  const int h = Q / 2;
+                                 uint16_t* __restrict__ img_hi, uint16_t* __restrict__ img_lo, int net) {
   const long long total = (long long)NT * KB * TN * TK;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
@@ -227,12 +242,8 @@ __global__ void k_init_tc_images(int Q, int KB, int NT, uint16_t* __restrict__ i
     const int e = (int)(q % (TN * TK));
     const int n = e / TK, k = e % TK;
     const int nt = blk / KB, kb = blk % KB;
-    const int m = kb * TK + k + 1, r = nt * TN + n;
-    float v = 0.f;
-    if (m <= h - 1 && r < h) {
-      const long long t = ((long long)m * r) % Q;
-      v = __double2float_rn(sinpi(2.0 * (double)t / (double)Q));
-    }
+    const int kk = kb * TK + k, r = nt * TN + n;
+    const float v = net == 2 ? sine_entry_n2(Q, kk, r) : sine_entry_n1(Q, kk, r);
     const size_t off = (size_t)blk * (kTileBytes / 2) + core_offset(n, k) / 2;
     img_bf16[off] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
     const __half hi = __float2half_rn(v);
@@ -245,7 +256,6 @@ __global__ void k_init_tc_images(int Q, int KB, int NT, uint16_t* __restrict__ i
 // in 128 x 32 blocks of the swizzled layout (four 4-byte values per chunk).
 __global__ void k_init_tc_images32(int Q, int KB32, int NT, uint32_t* __restrict__ img_hi,
                                    uint32_t* __restrict__ img_lo) {
-  const int h = Q / 2;
   const long long total = (long long)NT * KB32 * TN * 32;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
@@ -253,12 +263,7 @@ __global__ void k_init_tc_images32(int Q, int KB32, int NT, uint32_t* __restrict
     const int e = (int)(q % (TN * 32));
     const int n = e / 32, k = e % 32;
     const int nt = blk / KB32, kb = blk % KB32;
-    const int m = kb * 32 + k + 1, r = nt * TN + n;
-    float v = 0.f;
-    if (m <= h - 1 && r < h) {
-      const long long t = ((long long)m * r) % Q;
-      v = __double2float_rn(sinpi(2.0 * (double)t / (double)Q));
-    }
+    const float v = sine_entry_n1(Q, kb * 32 + k, nt * TN + n);
     // chunk k / 4 of row n, value k % 4 in it
     const size_t off = (size_t)blk * (kTileBytes / 4) + (core_offset(n, (k >> 2) * 8) >> 2) + (k & 3);
     const uint32_t hi = to_tf32(v);
@@ -530,7 +535,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
-template <int PREC, int TNW>
+template <int PREC, int TNW, int NET>
 __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float* __restrict__ V, int n_x, int bc,
                                                                      int Q, const int* __restrict__ occ,
                                                                      const int* __restrict__ n_occ_dev, int n_occ_host,
@@ -700,7 +705,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
       uint8_t* blk = sA + (size_t)kb * kTileBytes;
       const int m0 = kb * TK + k8 * 8 + 1;
       float dv[4][8];
-      if (fast && m0 + 7 <= h - 1) {
+      if (NET == 1 && fast && m0 + 7 <= h - 1) {
         // P[j] = V at offset m0 - 1 + j right of row 4 rg, N[j] = V at offset m0 + 7 - j left of it
         float P[12], N[12];
         const float* pp = sV + 4 * rg + h + m0 - 1;
@@ -721,14 +726,10 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
         for (int d = 0; d < 4; ++d)
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const int m = m0 + e;
+            const int kk = m0 - 1 + e;
             dv[d][e] = 0.f;
-            if (m <= h - 1) {
-              if (contig) dv[d][e] = __fsub_rn(sV[4 * rg + d + h + m], sV[4 * rg + d + h - m]);
-              else if (valid_d[d])
-                dv[d][e] = __fsub_rn(potential_at(V_d[d], n_x, bc, (long long)cell_d[d] + m),
-                                     potential_at(V_d[d], n_x, bc, (long long)cell_d[d] - m));
-            }
+            if (contig) dv[d][e] = a_entry_window<NET>(sV + 4 * rg + d, h, cell0 + 4 * rg + d, kk);
+            else if (valid_d[d]) dv[d][e] = a_term<NET>(V_d[d], n_x, bc, h, cell_d[d], kk);
           }
       }
       uint4 w[4];
@@ -850,7 +851,7 @@ __host__ __device__ constexpr size_t ws_split_smem_bytes(int KB, int h, bool tf3
                                       : (kWsBuilders / 32) * kWsStageFloats);
 }
 
-template <bool TF32>
+template <bool TF32, int NET>
 __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
     const float* __restrict__ V, int n_x, int bc, int Q, const int* __restrict__ occ,
     const int* __restrict__ n_occ_dev, int n_occ_host, const void* __restrict__ img_hi_v,
@@ -1024,7 +1025,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
         const int kb = kb0 + kbl;
         const int m0 = kb * KBLK + k8 * EPC + 1;
         float dv[4][EPC];
-        if (fast && m0 + EPC - 1 <= h - 1) {
+        if (NET == 1 && fast && m0 + EPC - 1 <= h - 1) {
           // P[j] = V at offset m0 - 1 + j right of row 4 rg, N[j] = V at offset m0 + EPC - 1 - j left of it
           constexpr int NW = EPC + 4;
           float P[NW], N[NW];
@@ -1046,14 +1047,10 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
           for (int d = 0; d < 4; ++d)
 #pragma unroll
             for (int e = 0; e < EPC; ++e) {
-              const int m = m0 + e;
+              const int kk = m0 - 1 + e;
               dv[d][e] = 0.f;
-              if (m <= h - 1) {
-                if (contig) dv[d][e] = __fsub_rn(sV[4 * rg + d + h + m], sV[4 * rg + d + h - m]);
-                else if (valid_d[d])
-                  dv[d][e] = __fsub_rn(potential_at(V_d[d], n_x, bc, (long long)cell_d[d] + m),
-                                       potential_at(V_d[d], n_x, bc, (long long)cell_d[d] - m));
-              }
+              if (contig) dv[d][e] = a_entry_window<NET>(sV + 4 * rg + d, h, cell0 + 4 * rg + d, kk);
+              else if (valid_d[d]) dv[d][e] = a_term<NET>(V_d[d], n_x, bc, h, cell_d[d], kk);
             }
         }
         uint4 wh[4], wl[4];
@@ -1154,9 +1151,10 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
 
 // ---------------------------------------------------------------- host side
 struct TcImages {
-  int KB, NT, KB32;          // 16-bit K blocks (64 values), column tiles, TF32 K blocks (32 values)
+  int KB, NT, KB32, KB2;     // 16-bit K blocks (64 values), column tiles, TF32 K blocks (32 values), N = 2 K blocks
   size_t bytes_per_image;    // NT * KB * kTileBytes (BF16, FP16 hi, FP16 lo)
   size_t bytes_per_image32;  // NT * KB32 * kTileBytes (TF32 hi, TF32 lo)
+  size_t bytes_per_image2;   // NT * KB2 * kTileBytes (N = 2 network: BF16, FP16 hi, FP16 lo)
 };
 
 static int g_h(const wmc_params& p) { return p.Q / 2; }
@@ -1169,39 +1167,98 @@ static TcImages tc_geometry(const wmc_params& p) {
   g.NT = (h + TN - 1) / TN;
   g.KB32 = (h - 1 + 31) / 32;
   if (g.KB32 < 1) g.KB32 = 1;
+  g.KB2 = (h + TK - 1) / TK;  // the N = 2 network's K = h pair offsets
   g.bytes_per_image = (size_t)g.NT * g.KB * kTileBytes;
   g.bytes_per_image32 = (size_t)g.NT * g.KB32 * kTileBytes;
+  g.bytes_per_image2 = (size_t)g.NT * g.KB2 * kTileBytes;
   return g;
 }
 
 size_t tc_images_bytes(const wmc_params& p) {
   const TcImages g = tc_geometry(p);
-  return 3 * g.bytes_per_image + 2 * g.bytes_per_image32;
+  return 3 * g.bytes_per_image + 2 * g.bytes_per_image32 + 3 * g.bytes_per_image2;
 }
 
 cudaError_t launch_init_tc_images(const wmc_params& p, void* images, cudaStream_t s) {
   const TcImages g = tc_geometry(p);
   uint16_t* base = static_cast<uint16_t*>(images);
   const size_t n16 = g.bytes_per_image / 2;
-  k_init_tc_images<<<256, 256, 0, s>>>(p.Q, g.KB, g.NT, base, base + n16, base + 2 * n16);
+  k_init_tc_images<<<256, 256, 0, s>>>(p.Q, g.KB, g.NT, base, base + n16, base + 2 * n16, 1);
   uint32_t* b32 = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(images) + 3 * g.bytes_per_image);
   k_init_tc_images32<<<256, 256, 0, s>>>(p.Q, g.KB32, g.NT, b32, b32 + g.bytes_per_image32 / 4);
+  uint16_t* b2 = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(images) + 3 * g.bytes_per_image +
+                                             2 * g.bytes_per_image32);
+  const size_t n2 = g.bytes_per_image2 / 2;
+  k_init_tc_images<<<256, 256, 0, s>>>(p.Q, g.KB2, g.NT, b2, b2 + n2, b2 + 2 * n2, 2);
   return cudaGetLastError();
 }
 
+// The N = 2 network (net = 2) runs on the warp-specialised BF16 / FP16 and
+// FP16-split kernels with its own operand images and A builder; other forms
+// return cudaErrorNotSupported for it.
+template <int NET>
+static cudaError_t launch_tc_net(const wmc_params& p, int prec, const float* V, const int* occ, const int* n_occ_dev,
+                                 int n_occ_host, int max_rows, const uint16_t* base, int KB, const TcImages& g,
+                                 float* VWh, unsigned int* flags, cudaStream_t s);
+
 cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V, const int* occ, const int* n_occ_dev,
                                   int n_occ_host, int max_rows, const void* images, float* VWh, unsigned int* flags,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int net) {
   if (max_rows <= 0) return cudaSuccess;
   const TcImages g = tc_geometry(p);
+  if (net == 2) {
+    const uint16_t* b2 = reinterpret_cast<const uint16_t*>(static_cast<const uint8_t*>(images) +
+                                                           3 * g.bytes_per_image + 2 * g.bytes_per_image32);
+    return launch_tc_net<2>(p, prec, V, occ, n_occ_dev, n_occ_host, max_rows, b2, g.KB2, g, VWh, flags, s);
+  }
   const uint16_t* base = static_cast<const uint16_t*>(images);
+  if (prec == WMC_BF16 || prec == WMC_FP16 || prec == WMC_FP16_SPLIT) {
+    const cudaError_t e = launch_tc_net<1>(p, prec, V, occ, n_occ_dev, n_occ_host, max_rows, base, g.KB, g, VWh,
+                                           flags, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   const size_t n16 = g.bytes_per_image / 2;
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   dim3 grid((max_rows + TM - 1) / TM, g.NT);
+  if (prec == WMC_BF16) {
+    const size_t sm = tc_smem_bytes(false, g_h(p));
+    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_kernel_eval_tc<WMC_BF16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
+                                                     base, nullptr, g.KB, c, VWh, flags);
+  } else if (prec == WMC_FP16) {
+    const size_t sm = tc_smem_bytes(false, g_h(p));
+    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_kernel_eval_tc<WMC_FP16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
+                                                     base + n16, nullptr, g.KB, c, VWh, flags);
+  } else if (prec == WMC_TF32X3 && ws_split_smem_bytes(g.KB32, g_h(p), true) <= 226 * 1024) {
+    const size_t sm = ws_split_smem_bytes(g.KB32, g_h(p), true);
+    const uint8_t* b32 = reinterpret_cast<const uint8_t*>(images) + 3 * g.bytes_per_image;
+    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_kernel_eval_tc_ws_split<true, 1><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                                 n_occ_host, b32, b32 + g.bytes_per_image32,
+                                                                 g.KB32, c, VWh, flags);
+  } else if (prec == WMC_FP16_SPLIT) {
+    const size_t sm = tc_smem_bytes(true, g_h(p));
+    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_kernel_eval_tc<WMC_FP16_SPLIT><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                           n_occ_host, base + n16, base + 2 * n16, g.KB, c, VWh,
+                                                           flags);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int NET>
+static cudaError_t launch_tc_net(const wmc_params& p, int prec, const float* V, const int* occ, const int* n_occ_dev,
+                                 int n_occ_host, int max_rows, const uint16_t* base, int KB, const TcImages& g,
+                                 float* VWh, unsigned int* flags, cudaStream_t s) {
+  const size_t n16 = (size_t)g.NT * KB * kTileBytes / 2;
+  const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   const int row_tiles = (max_rows + TM - 1) / TM;
   const int tnw = g_h(p) > TN ? 256 : 128;
-  const size_t ws_sm = ws_smem_bytes(g.KB, g_h(p), tnw);
-  if ((prec == WMC_BF16 || prec == WMC_FP16) && g.KB <= kWsMaxKB && ws_sm <= 226 * 1024) {
+  const size_t ws_sm = ws_smem_bytes(KB, g_h(p), tnw);
+  if ((prec == WMC_BF16 || prec == WMC_FP16) && KB <= kWsMaxKB && ws_sm <= 226 * 1024) {
     // warp-specialised form.  The column tiles are split over grid.y by the
     // factor that minimises waves x per-CTA work, with the fixed part of a CTA
     // (set-up and building A) counted as three 128-column tiles.
@@ -1219,12 +1276,13 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
       }
     }
     const dim3 ws_grid(row_tiles, n_split);
-#define WMC_LAUNCH_WS(PR, TW)                                                                                      \
-  do {                                                                                                             \
-    cudaFuncSetAttribute(k_kernel_eval_tc_ws<PR, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_sm);    \
-    k_kernel_eval_tc_ws<PR, TW><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,  \
-                                                                   n_occ_host, img, g.KB, g.NT, n_split, c, VWh,   \
-                                                                   flags);                                         \
+#define WMC_LAUNCH_WS(PR, TW)                                                                                    \
+  do {                                                                                                           \
+    cudaFuncSetAttribute(k_kernel_eval_tc_ws<PR, TW, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                         (int)ws_sm);                                                                            \
+    k_kernel_eval_tc_ws<PR, TW, NET><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ,      \
+                                                                        n_occ_dev, n_occ_host, img, KB, g.NT,    \
+                                                                        n_split, c, VWh, flags);                 \
   } while (0)
     if (prec == WMC_BF16) {
       if (tnw == 256) WMC_LAUNCH_WS(WMC_BF16, 256);
@@ -1236,39 +1294,16 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
 #undef WMC_LAUNCH_WS
     return cudaGetLastError();
   }
-  if (prec == WMC_BF16) {
-    const size_t sm = tc_smem_bytes(false, g_h(p));
-    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_kernel_eval_tc<WMC_BF16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
-                                                     base, nullptr, g.KB, c, VWh, flags);
-  } else if (prec == WMC_FP16) {
-    const size_t sm = tc_smem_bytes(false, g_h(p));
-    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_kernel_eval_tc<WMC_FP16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
-                                                     base + n16, nullptr, g.KB, c, VWh, flags);
-  } else if (prec == WMC_FP16_SPLIT && ws_split_smem_bytes(g.KB, g_h(p)) <= 226 * 1024) {
-    const size_t sm = ws_split_smem_bytes(g.KB, g_h(p));
-    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_kernel_eval_tc_ws_split<false><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
-                                                                  n_occ_host, base + n16, base + 2 * n16, g.KB, c,
-                                                                  VWh, flags);
-  } else if (prec == WMC_TF32X3 && ws_split_smem_bytes(g.KB32, g_h(p), true) <= 226 * 1024) {
-    const size_t sm = ws_split_smem_bytes(g.KB32, g_h(p), true);
-    const uint8_t* b32 = reinterpret_cast<const uint8_t*>(images) + 3 * g.bytes_per_image;
-    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_kernel_eval_tc_ws_split<true><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
-                                                                 n_occ_host, b32, b32 + g.bytes_per_image32,
-                                                                 g.KB32, c, VWh, flags);
-  } else if (prec == WMC_FP16_SPLIT) {
-    const size_t sm = tc_smem_bytes(true, g_h(p));
-    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_kernel_eval_tc<WMC_FP16_SPLIT><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
-                                                           n_occ_host, base + n16, base + 2 * n16, g.KB, c, VWh,
-                                                           flags);
-  } else {
-    return cudaErrorInvalidValue;
+  if (prec == WMC_FP16_SPLIT && ws_split_smem_bytes(KB, g_h(p)) <= 226 * 1024) {
+    const size_t sm = ws_split_smem_bytes(KB, g_h(p));
+    const dim3 grid(row_tiles, g.NT);
+    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<false, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_kernel_eval_tc_ws_split<false, NET><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ,
+                                                                       n_occ_dev, n_occ_host, base + n16,
+                                                                       base + 2 * n16, KB, c, VWh, flags);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  return cudaErrorNotSupported;
 }
 
 }  // namespace wmc

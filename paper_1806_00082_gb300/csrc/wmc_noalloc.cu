@@ -21,7 +21,7 @@
 // caller.
 #include <mutex>
 
-#include "wmc_internal.cuh"
+#include "wmc_device.cuh"
 
 namespace wmc {
 namespace {
@@ -37,17 +37,9 @@ float* g_scratch_ptr[64] = {};
 
 // B[kk][r] = sin(2 pi ((kk+1) r mod Q) / Q) for kk < h-1, r < h, zero elsewhere.
 __global__ void k_fill_sine_scratch(float* __restrict__ B, int Q, int Kp, int Np) {
-  const int h = Q / 2;
   const long long n = (long long)Kp * Np;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const int kk = (int)(q / Np), r = (int)(q % Np);
-    float v = 0.f;
-    if (kk < h - 1 && r < h) {
-      const long long t = ((long long)(kk + 1) * r) % Q;
-      v = __double2float_rn(sinpi(2.0 * (double)t / (double)Q));
-    }
-    B[q] = v;
-  }
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    B[q] = sine_entry_n1(Q, (int)(q / Np), (int)(q % Np));
 }
 
 // Device address of the scratch array on the current device.  In host code the

@@ -13,10 +13,10 @@ namespace wmc {
 // fl32(f + D) >= 1 iff w > xhi[k], left iff fl32(f + D) < 0 iff w < xlo[k].
 // B[kk][r] = sin(2 pi ((kk+1) r mod Q) / Q) for kk < h-1, r < h (zero padding
 // elsewhere): the integer-indexed sine matrix of the network's hidden layer
-// (Sec. 2.2).
+// (Sec. 2.2); B2[u][r] the folded matrix of the N = 2 network (Sec. 2.3).
 __global__ void k_init_tables(int n_M, int Q, double d1, float* __restrict__ D, uint32_t* __restrict__ xlo,
-                              uint32_t* __restrict__ xhi, float* __restrict__ B, int Kp, int Np, DevHeader* hdr) {
-  const int h = Q / 2;
+                              uint32_t* __restrict__ xhi, float* __restrict__ B, int Kp, int Np,
+                              float* __restrict__ B2, int Kp2, DevHeader* hdr) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
   if (tid == 0) {
@@ -33,21 +33,14 @@ __global__ void k_init_tables(int n_M, int Q, double d1, float* __restrict__ D, 
     xlo[k] = lo;
     xhi[k] = hi;
   }
-  for (long long q = tid; q < (long long)Kp * Np; q += nthreads) {
-    const int kk = (int)(q / Np), r = (int)(q % Np);
-    float v = 0.f;
-    if (kk < h - 1 && r < h) {
-      const long long t = ((long long)(kk + 1) * r) % Q;
-      v = __double2float_rn(sinpi(2.0 * (double)t / (double)Q));
-    }
-    B[q] = v;
-  }
+  for (long long q = tid; q < (long long)Kp * Np; q += nthreads) B[q] = sine_entry_n1(Q, (int)(q / Np), (int)(q % Np));
+  for (long long q = tid; q < (long long)Kp2 * Np; q += nthreads) B2[q] = sine_entry_n2(Q, (int)(q / Np), (int)(q % Np));
 }
 
 cudaError_t launch_init_tables(const wmc_params& p, const View& v, cudaStream_t s) {
   const Layout L = layout(p);
   const double d1 = ((kHbarJs * kPi) * p.dt_s) / ((p.mass_kg * (double)p.Q) * (p.dx_m * p.dx_m));
-  k_init_tables<<<256, 256, 0, s>>>(p.n_M, p.Q, d1, v.D, v.xlo, v.xhi, v.B, L.Kp, L.Np, v.hdr);
+  k_init_tables<<<256, 256, 0, s>>>(p.n_M, p.Q, d1, v.D, v.xlo, v.xhi, v.B, L.Kp, L.Np, v.B2, L.Kp2, v.hdr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // no stale publication may carry a tag of a coming plan launch

@@ -32,7 +32,7 @@ EXPORTS = (
     "wmc_kernel_eval_noalloc", "wmc_batch_workspace_size", "wmc_batch_layout", "wmc_batch_init", "wmc_batch_run",
     "wmc_batch_autotune", "wmc_batch_get_counters", "wmc_potential_tanh", "wmc_potential_tanh_vjp",
     "wmc_kernel_eval_rows", "wmc_kernel_vjp", "wmc_check_wait", "wmc_step_timing", "wmc_step_timing_read",
-    "wmc_get_error", "wmc_philox_throughput",
+    "wmc_get_error", "wmc_philox_throughput", "wmc_kernel_eval_n2",
 )
 
 
@@ -138,6 +138,7 @@ def load(path: str | None = None):
             "wmc_potential_tanh_vjp": ([pp, vp, i32, i32, i32, ctypes.c_float, vp, vp, vp], i32),
             "wmc_kernel_eval_rows": ([pp, vp, i32, i32, vp, vp, vp], i32),
             "wmc_kernel_vjp": ([pp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
+            "wmc_kernel_eval_n2": ([pp, vp, vp, i32, i32, vp, vp, vp], i32),
             "wmc_get_error": ([pp, vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_char_p, ctypes.c_size_t], i32),
             "wmc_philox_throughput": ([u32, u32, i32, vp, i64, vp], i32),
         }
@@ -241,6 +242,17 @@ def kernel_eval(p: Params, V: torch.Tensor, occ: torch.Tensor, ws: torch.Tensor,
         out = torch.empty((n, p.h), dtype=torch.float32, device=V.device)
     _check("wmc_kernel_eval", load().wmc_kernel_eval(ctypes.byref(p), _ptr(V), _ptr(occ), n, prec, _ptr(out),
                                                      _ptr(ws), _stream()))
+    return out
+
+
+def kernel_eval_n2(p: Params, V: torch.Tensor, occ: torch.Tensor, ws: torch.Tensor, prec: int = FP32,
+                   out: torch.Tensor | None = None) -> torch.Tensor:
+    """wmc_kernel_eval_n2: half-period rows of the N = 2 barycentric network."""
+    n = occ.numel()
+    if out is None:
+        out = torch.empty((n, p.h), dtype=torch.float32, device=V.device)
+    _check("wmc_kernel_eval_n2", load().wmc_kernel_eval_n2(ctypes.byref(p), _ptr(V), _ptr(occ), n, prec, _ptr(out),
+                                                           _ptr(ws), _stream()))
     return out
 
 
