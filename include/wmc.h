@@ -132,6 +132,18 @@ wmc_status wmc_init(const wmc_params* p, void* ws, size_t ws_bytes, wmc_stream_t
 /* Zeroes the counters and flags of an initialised workspace. */
 wmc_status wmc_reset_counters(const wmc_params* p, void* ws, wmc_stream_t stream);
 
+/* Numbering of a sub-domain's particles (domain decomposition over cell
+ * ranges): the survivors enumerated by wmc_annihilate and the steps of wmc_run
+ * are numbered from id_base (0 after wmc_init) instead of 0, so a rank that
+ * owns a range of cells, its histogram zero outside the range, draws the
+ * Philox words of the global numbering when id_base is the number of
+ * particles in the cells before its range.  Particles that drift out of the
+ * range land in the neighbouring rows of the output, for the owning rank to
+ * add.  id_base + the population must stay below 2^32 (else WMC_FLAG_CAPACITY);
+ * wmc_materialize writes survivor id at place id - id_base.  Stream-ordered;
+ * WMC_ERR_ARG for id_base >= 2^32. */
+wmc_status wmc_set_id_base(const wmc_params* p, void* ws, uint64_t id_base, wmc_stream_t stream);
+
 /* Failure-detection check of the device wait pattern the tensor-core kernels
  * use: one device thread waits until the 32-bit word *signal [dev] is non-zero
  * or max_cycles SM clock cycles have passed; if it gives up it sets

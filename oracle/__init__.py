@@ -17,7 +17,9 @@ Functions and the passages they follow:
 - :func:`philox` -- Philox4x32-10 from Salmon et al., SC'11.
 - :func:`materialize` -- rule 2 survivors re-emitted in (cell, M) order.
 - :func:`simulate` -- the postulate of Sec. 2.1 (free drift, pair creation with
-  probability gamma dt, momenta p +- p') with rules 1 and 2, step by step.
+  probability gamma dt, momenta p +- p') with rules 1 and 2, step by step;
+  :func:`simulate_subdomain` one step of a range of cells whose particles are
+  numbered after those of the cells before it.
 - :func:`density` -- rule 1: signed counts summed over M.
 """
 from __future__ import annotations
@@ -114,6 +116,8 @@ def _load():
         lib.wmco_density.argtypes = [pp, i32p, i64p]
         lib.wmco_simulate.argtypes = [pp, f64p, f32p, i32p, ctypes.c_uint32, ctypes.c_int32, i32p, i64p]
         lib.wmco_simulate.restype = ctypes.c_int32
+        lib.wmco_simulate_subdomain.argtypes = [pp, f64p, f32p, i32p, ctypes.c_uint32, ctypes.c_uint64, i32p, i64p]
+        lib.wmco_simulate_subdomain.restype = ctypes.c_int32
         _lib = lib
     return _lib
 
@@ -252,4 +256,27 @@ def simulate(p: Params, hist0: np.ndarray, t_first: int, n_steps: int, V=None, t
                             n_steps, _ptr(out, ctypes.c_int32), _ptr(stats, ctypes.c_int64))
     if err:
         raise RuntimeError(f"oracle simulate failed with code {err}")
+    return out.reshape(p.n_x, p.n_M), stats
+
+
+def simulate_subdomain(p: Params, hist: np.ndarray, t: int, id_base: int, V=None, table=None):
+    """One step t of a sub-domain (its particles only in hist, full [n_x, n_M]
+    layout) whose particles are numbered from id_base; particles leaving it
+    land in the neighbouring rows of the result.  Returns (hist, stats)."""
+    lib = _load()
+    h0 = np.ascontiguousarray(hist, dtype=np.int32).reshape(-1)
+    out = np.zeros_like(h0)
+    stats = np.zeros(ST_N, np.int64)
+    if table is not None:
+        tab = np.ascontiguousarray(table, dtype=np.float32).reshape(-1)
+        vptr = ctypes.POINTER(ctypes.c_double)()
+        tptr = _ptr(tab, ctypes.c_float)
+    else:
+        V64 = np.ascontiguousarray(V, dtype=np.float64)
+        vptr = _ptr(V64, ctypes.c_double)
+        tptr = ctypes.POINTER(ctypes.c_float)()
+    err = lib.wmco_simulate_subdomain(ctypes.byref(p), vptr, tptr, _ptr(h0, ctypes.c_int32), t & 0xFFFFFFFF,
+                                      int(id_base), _ptr(out, ctypes.c_int32), _ptr(stats, ctypes.c_int64))
+    if err:
+        raise RuntimeError(f"oracle subdomain step failed with code {err}")
     return out.reshape(p.n_x, p.n_M), stats

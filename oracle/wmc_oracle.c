@@ -298,21 +298,25 @@ int64_t wmco_population(const wmco_params* p, const int32_t* hist) {
 }
 
 /* Survivors of a net signed histogram, in row-major (cell, M) order, each
- * with a fresh offset f = u24(word id mod 4 of Philox(id / 4, step, REPOS, sim)).
- * Returns the count written, or -1 if it exceeds capacity or 2^32. */
-int64_t wmco_materialize(const wmco_params* p, const int32_t* hist, uint32_t step, int64_t capacity,
-                         int32_t* cell, float* f, int16_t* M, int8_t* s) {
+ * with a fresh offset f = u24(word id mod 4 of Philox(id / 4, step, REPOS, sim)),
+ * where the particle's number id is id_base plus its place in this histogram
+ * (id_base = 0 for a whole domain; a sub-domain of cells numbers its particles
+ * after those of the cells before it).  Outputs are indexed by the place.
+ * Returns the count written, or -1 if it exceeds capacity or the ids 2^32. */
+static int64_t materialize_from(const wmco_params* p, const int32_t* hist, uint32_t step, int64_t capacity,
+                                uint64_t id_base, int32_t* cell, float* f, int16_t* M, int8_t* s) {
   int64_t id = 0;
   for (int32_t i = 0; i < p->n_x; ++i) {
     for (int32_t k = 0; k < p->n_M; ++k) {
       int32_t n = hist[(int64_t)i * p->n_M + k];
       int32_t a = n < 0 ? -n : n;
       for (int32_t c = 0; c < a; ++c) {
-        if (id >= capacity || id >= ((int64_t)1 << 32)) return -1;
+        const uint64_t gid = id_base + (uint64_t)id;
+        if (id >= capacity || gid >= ((uint64_t)1 << 32)) return -1;
         uint32_t w[4];
-        draw(p, (uint32_t)(id >> 2), step, WMCO_PURPOSE_REPOS, w);
+        draw(p, (uint32_t)(gid >> 2), step, WMCO_PURPOSE_REPOS, w);
         cell[id] = i;
-        f[id] = wmco_u24(w[id & 3]);
+        f[id] = wmco_u24(w[gid & 3]);
         M[id] = (int16_t)(k - p->n_M / 2);
         s[id] = (int8_t)(n > 0 ? 1 : -1);
         ++id;
@@ -320,6 +324,11 @@ int64_t wmco_materialize(const wmco_params* p, const int32_t* hist, uint32_t ste
     }
   }
   return id;
+}
+
+int64_t wmco_materialize(const wmco_params* p, const int32_t* hist, uint32_t step, int64_t capacity,
+                         int32_t* cell, float* f, int16_t* M, int8_t* s) {
+  return materialize_from(p, hist, step, capacity, 0u, cell, f, M, s);
 }
 
 /* Rule 1: rho(i) = sum over M of the signed counts. */
@@ -354,8 +363,28 @@ enum {
  * that two implementations can be fed the same kernel values).
  * V: potential [n_x] in eV (ignored if table is given).
  * stats: int64[ST_N], accumulated. Returns 0 or an ST_ERR code. */
+static int32_t simulate_from(const wmco_params* p, const double* V, const float* table, const int32_t* hist,
+                             uint32_t t_first, int32_t n_steps, uint64_t id_base, int32_t* hist_out,
+                             int64_t* stats);
+
 int32_t wmco_simulate(const wmco_params* p, const double* V, const float* table, const int32_t* hist,
                       uint32_t t_first, int32_t n_steps, int32_t* hist_out, int64_t* stats) {
+  return simulate_from(p, V, table, hist, t_first, n_steps, 0u, hist_out, stats);
+}
+
+/* One step of a sub-domain of cells (its particles only in hist; every other
+ * row zero), its particles numbered from id_base: the particles of the cells
+ * before it in a domain decomposition come first.  Particles that drift out of
+ * the sub-domain land in the neighbouring rows of hist_out (to be passed to
+ * the rank that owns them); only leaving [0, n_x) absorbs. */
+int32_t wmco_simulate_subdomain(const wmco_params* p, const double* V, const float* table, const int32_t* hist,
+                                uint32_t t, uint64_t id_base, int32_t* hist_out, int64_t* stats) {
+  return simulate_from(p, V, table, hist, t, 1, id_base, hist_out, stats);
+}
+
+static int32_t simulate_from(const wmco_params* p, const double* V, const float* table, const int32_t* hist,
+                             uint32_t t_first, int32_t n_steps, uint64_t id_base, int32_t* hist_out,
+                             int64_t* stats) {
   const int64_t nx = p->n_x, nM = p->n_M, G = nx * nM;
   float* D = (float*)malloc(sizeof(float) * nM);
   wmco_drift_table(p, D);
@@ -380,7 +409,7 @@ int32_t wmco_simulate(const wmco_params* p, const double* V, const float* table,
     e.f = (float*)malloc(sizeof(float) * (P ? P : 1));
     e.M = (int16_t*)malloc(sizeof(int16_t) * (P ? P : 1));
     e.s = (int8_t*)malloc(P ? P : 1);
-    e.n = wmco_materialize(p, cur, t - 1u, P, e.cell, e.f, e.M, e.s);
+    e.n = materialize_from(p, cur, t - 1u, P, id_base, e.cell, e.f, e.M, e.s);
     if (e.n < 0) { err = 1; ens_free(&e); break; }
     stats[ST_PARTICLE_STEPS] += e.n;
 
@@ -412,10 +441,11 @@ int32_t wmco_simulate(const wmco_params* p, const double* V, const float* table,
       }
       /* pair creation with probability gamma dt */
       uint32_t w[4];
-      draw(p, (uint32_t)(id >> 2), t, WMCO_PURPOSE_GEN, w);
-      double u1 = wmco_u32(w[id & 3]);
+      const uint64_t gid = id_base + (uint64_t)id;
+      draw(p, (uint32_t)(gid >> 2), t, WMCO_PURPOSE_GEN, w);
+      double u1 = wmco_u32(w[gid & 3]);
       if (u1 < gam[c] * p->dt_s) {
-        draw(p, (uint32_t)id, t, WMCO_PURPOSE_PICK, w);
+        draw(p, (uint32_t)gid, t, WMCO_PURPOSE_PICK, w);
         int32_t kp = wmco_sample_row(p->n_M, crow, wmco_u53_bits(w[0], w[1]));
         int32_t Mp = kp - p->n_M / 2;
         int32_t Mc[2] = {e.M[id] + Mp, e.M[id] - Mp};

@@ -113,6 +113,8 @@ int num_sms() {
 
 __global__ void k_set_step(DevHeader* hdr, uint32_t step) { hdr->step = step; }
 
+__global__ void k_set_id_base(DevHeader* hdr, unsigned long long base) { hdr->id_base = base; }
+
 __global__ void k_reset_counters(DevHeader* hdr) {
   hdr->particle_steps = 0;
   hdr->pairs = 0;
@@ -395,6 +397,13 @@ wmc_status wmc_check_wait(const wmc_params* p, const uint32_t* signal, uint64_t 
   if (!params_ok(p) || !signal || !ws || max_cycles > (1ull << 34)) return WMC_ERR_ARG;
   const View v = view(*p, ws);
   k_check_wait<<<1, 1, 0, (cudaStream_t)stream>>>(signal, (long long)max_cycles, v.hdr);
+  return cuda_status(cudaGetLastError());
+}
+
+wmc_status wmc_set_id_base(const wmc_params* p, void* ws, uint64_t id_base, wmc_stream_t stream) {
+  if (!params_ok(p) || !ws || id_base >= (1ull << 32)) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  k_set_id_base<<<1, 1, 0, (cudaStream_t)stream>>>(v.hdr, (unsigned long long)id_base);
   return cuda_status(cudaGetLastError());
 }
 

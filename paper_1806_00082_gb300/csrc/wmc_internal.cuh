@@ -74,6 +74,8 @@ struct DevHeader {
   unsigned int pairs_done;   // pair-kernel blocks finished (the last one resets the queue and the ticket)
   unsigned int plan_epoch;   // launches of the plan so far (tags its blocks' published prefixes)
   unsigned int plan_ticket;  // logical block index of the running plan launch (reset by its last block)
+  unsigned int pad0;
+  unsigned long long id_base;  // number of the first survivor (a sub-domain numbers after the cells before it)
 };
 
 // Totals of a run of cells in the plan's scan: survivors (64 bits), work

@@ -205,8 +205,9 @@ __global__ __launch_bounds__(kPlanCells) void k_plan(int n_x, const unsigned lon
   __syncthreads();
   const PlanSums ex = s_ex;
   const PlanSums tot = plan_add(ex, agg);  // through the block's last cell
+  const unsigned long long id_base = hdr->id_base;
   if (i < n_x) {
-    const unsigned long long r = ex.T + inc.T - mine.T;
+    const unsigned long long r = id_base + ex.T + inc.T - mine.T;
     const int baseI = ex.I + inc.I - mine.I;
     const int baseN = ex.N + inc.N - mine.N;
     R[i] = r;
@@ -223,8 +224,8 @@ __global__ __launch_bounds__(kPlanCells) void k_plan(int n_x, const unsigned lon
   }
   if (blk == (int)gridDim.x - 1 && tid == 0) {
     // totals of every cell
-    const bool ok = !tot.big && tot.T < (1ull << 32) && (long long)tot.I <= max_items;
-    R[n_x] = tot.T;
+    const bool ok = !tot.big && id_base + tot.T < (1ull << 32) && (long long)tot.I <= max_items;
+    R[n_x] = id_base + tot.T;
     IP[n_x] = tot.I;
     hdr->population = tot.T;
     hdr->n_items = ok ? tot.I : 0;

@@ -533,6 +533,7 @@ __global__ __launch_bounds__(kStepThreads) void k_materialize(const int32_t* __r
     return;
   }
   const int n_items = hdr->n_items;
+  const unsigned long long id_base = hdr->id_base;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     __syncthreads();
     if (tid == 0) {
@@ -560,10 +561,11 @@ __global__ __launch_bounds__(kStepThreads) void k_materialize(const int32_t* __r
         const uint32_t id = base + (uint32_t)lid;
         const uint4 w = philox4x32_10(make_uint4(id >> 2, t, kPurposeRepos, sim), k0, k1);
         const uint32_t wj = (id & 3u) == 0u ? w.x : ((id & 3u) == 1u ? w.y : ((id & 3u) == 2u ? w.z : w.w));
-        cell[id] = i;
-        f[id] = (float)(wj >> 8) * 0x1p-24f;
-        M[id] = (int16_t)(k - n_M / 2);
-        sign[id] = (int8_t)(s_n[k] > 0 ? 1 : -1);
+        const uint32_t o = id - (uint32_t)id_base;  // place in this histogram
+        cell[o] = i;
+        f[o] = (float)(wj >> 8) * 0x1p-24f;
+        M[o] = (int16_t)(k - n_M / 2);
+        sign[o] = (int8_t)(s_n[k] > 0 ? 1 : -1);
       }
     }
   }

@@ -32,7 +32,7 @@ EXPORTS = (
     "wmc_kernel_eval_noalloc", "wmc_batch_workspace_size", "wmc_batch_layout", "wmc_batch_init", "wmc_batch_run",
     "wmc_batch_autotune", "wmc_batch_get_counters", "wmc_potential_tanh", "wmc_potential_tanh_vjp",
     "wmc_kernel_eval_rows", "wmc_kernel_vjp", "wmc_check_wait", "wmc_step_timing", "wmc_step_timing_read",
-    "wmc_get_error", "wmc_philox_throughput", "wmc_kernel_eval_n2",
+    "wmc_get_error", "wmc_philox_throughput", "wmc_kernel_eval_n2", "wmc_set_id_base",
 )
 
 
@@ -139,6 +139,7 @@ def load(path: str | None = None):
             "wmc_kernel_eval_rows": ([pp, vp, i32, i32, vp, vp, vp], i32),
             "wmc_kernel_vjp": ([pp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
             "wmc_kernel_eval_n2": ([pp, vp, vp, i32, i32, vp, vp, vp], i32),
+            "wmc_set_id_base": ([pp, vp, ctypes.c_uint64, vp], i32),
             "wmc_get_error": ([pp, vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_char_p, ctypes.c_size_t], i32),
             "wmc_philox_throughput": ([u32, u32, i32, vp, i64, vp], i32),
         }
@@ -217,6 +218,10 @@ def get_counters(p: Params, ws: torch.Tensor) -> dict:
     c = Counters()
     _check("wmc_get_counters", load().wmc_get_counters(ctypes.byref(p), _ptr(ws), ctypes.byref(c), _stream()))
     return c.as_dict()
+
+
+def set_id_base(p: Params, ws: torch.Tensor, id_base: int) -> None:
+    _check("wmc_set_id_base", load().wmc_set_id_base(ctypes.byref(p), _ptr(ws), int(id_base), _stream()))
 
 
 def get_error(p: Params, ws: torch.Tensor) -> tuple:
