@@ -9,6 +9,8 @@ Functions and the passages they follow:
 
 - :func:`kernel_rows` -- Eq. (wigner-1d-discrete): the finite-window discrete
   Wigner kernel, summed over m = -h..h (h = L_C / (2 dx)) in FP64.
+- :func:`kernel_all_dft` -- the same sum for every cell by a sliding window
+  over exp(i 2 pi l M / Q)-weighted potentials, O(n_x n_M), FP64.
 - :func:`kernel_rows_n2` -- Eq. (kernel_ML) with N = 2 and the barycentric
   weights of Sec. 2.3: consecutive cells grouped in pairs, FP64.
 - :func:`cdf_row` -- Eq. (momentum_integral): gamma as the sum of V_W^+ over M
@@ -102,6 +104,7 @@ def _load():
         lib.wmco_kernel_value.restype = ctypes.c_double
         lib.wmco_kernel_rows.argtypes = [pp, f64p, ctypes.c_int32, i32p, f64p]
         lib.wmco_kernel_rows_n2.argtypes = [pp, f64p, ctypes.c_int32, i32p, f64p]
+        lib.wmco_kernel_all_dft.argtypes = [pp, f64p, f64p]
         lib.wmco_cdf_row.argtypes = [ctypes.c_int32, f64p, i64p, i32p]
         lib.wmco_cdf_row.restype = ctypes.c_double
         lib.wmco_sample_row.argtypes = [ctypes.c_int32, i64p, ctypes.c_uint64]
@@ -166,6 +169,15 @@ def kernel_rows(p: Params, V: np.ndarray, rows) -> np.ndarray:
     out = np.zeros((r.size, p.n_M), dtype=np.float64)
     _load().wmco_kernel_rows(ctypes.byref(p), _ptr(V64, ctypes.c_double), r.size, _ptr(r, ctypes.c_int32),
                              _ptr(out, ctypes.c_double))
+    return out
+
+
+def kernel_all_dft(p: Params, V: np.ndarray) -> np.ndarray:
+    """Eq. (wigner-1d-discrete) on every cell by the sliding window of
+    exp(i 2 pi l M / Q)-weighted potentials: [n_x, n_M] in 1/s, FP64."""
+    V64 = np.ascontiguousarray(V, dtype=np.float64)
+    out = np.zeros((p.n_x, p.n_M), dtype=np.float64)
+    _load().wmco_kernel_all_dft(ctypes.byref(p), _ptr(V64, ctypes.c_double), _ptr(out, ctypes.c_double))
     return out
 
 

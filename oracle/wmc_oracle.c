@@ -178,6 +178,49 @@ void wmco_kernel_rows(const wmco_params* p, const double* V, int32_t n_rows, con
   free(dV);
 }
 
+/* Eq. (wigner-1d-discrete) by a sliding window instead of a sum per cell:
+ * with E_M(l) = exp(i 2 pi l M / Q) the window sum is
+ *   W_M(i) = sum_{l=i-h}^{i+h} V(l) E_M(l),   V_W(i; M) = -(2 / (hbar Q)) Im[ E_M(-i) W_M(i) ]
+ * (the unfolded sum of the N = 1 network, sum_l V(l) sin((l - i) 2 pi M / Q)),
+ * and W_M(i + 1) = W_M(i) + V(i + h + 1) E_M(i + h + 1) - V(i - h) E_M(i - h), so a
+ * column costs O(n_x) instead of O(n_x h).  FP64 throughout, exact integer
+ * phases (l M mod Q); V outside the domain follows bc_potential.  All cells:
+ * out[i][k] = V_W(i; k - n_M/2), i = 0 .. n_x - 1.  An independent
+ * arrangement of the same sum, to cross-check wmco_kernel_rows. */
+void wmco_kernel_all_dft(const wmco_params* p, const double* V, double* out) {
+  const int32_t Q = p->Q, h = Q / 2;
+  const int64_t nx = p->n_x;
+  double* C = (double*)malloc(sizeof(double) * (size_t)Q);
+  double* S = (double*)malloc(sizeof(double) * (size_t)Q);
+  /* sin(2 pi t / Q), and cos(2 pi t / Q) = sin(2 pi (4t + Q) / (4Q)) */
+  for (int32_t t = 0; t < Q; ++t) {
+    S[t] = wmco_sine(Q, t);
+    C[t] = wmco_sine(4 * Q, 4 * (int64_t)t + Q);
+  }
+  for (int32_t k = 0; k < p->n_M; ++k) {
+    const int64_t M = k - p->n_M / 2;
+    const int64_t Mq = ((M % Q) + Q) % Q;
+    double wr = 0.0, wi = 0.0;                   /* W_M(0) */
+    for (int64_t l = -h; l <= h; ++l) {
+      const int64_t t = ((l * Mq) % Q + Q) % Q;
+      const double v = pot(p, V, l);
+      wr += v * C[t];
+      wi += v * S[t];
+    }
+    for (int64_t i = 0; i < nx; ++i) {
+      const int64_t ti = ((i * Mq) % Q + Q) % Q;  /* E_M(-i) = C[ti] - i S[ti] */
+      out[i * p->n_M + k] = -(2.0 / (WMCO_HBAR_EVS * (double)Q)) * (C[ti] * wi - S[ti] * wr);
+      const int64_t la = i + h + 1, lb = i - h;
+      const int64_t ta = ((la * Mq) % Q + Q) % Q, tb = ((lb * Mq) % Q + Q) % Q;
+      const double va = pot(p, V, la), vb = pot(p, V, lb);
+      wr += va * C[ta] - vb * C[tb];
+      wi += va * S[ta] - vb * S[tb];
+    }
+  }
+  free(C);
+  free(S);
+}
+
 /* The N = 2 network of Eq. (kernel_ML) with the barycentric weights of Sec. 2.3
  * (omega^V = (1, 1), omega^theta = (1/2, 1/2), W_l = w_l = -2 dx / (hbar L_C),
  * one cosine factor since N = 2^1): the terms V(l) sin(theta_l(i, j)) of the
