@@ -218,6 +218,18 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
 wmc_status wmc_kernel_eval_noalloc(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
                                    float* VWh, wmc_stream_t stream);
 
+/* Eq. (wigner-1d-discrete) on every cell by a sliding window, in FP64: for
+ * each half-period column r, W(i) = sum_{l=i-h}^{i+h} V(l) exp(i 2 pi l r / Q)
+ * moves by one term in and one out per cell and VWh[i][r] =
+ * -(2 / (hbar Q)) Im[exp(-i 2 pi i r / Q) W(i)], so all n_x rows cost O(n_x h)
+ * FP64 operations (the window sum started afresh every 256 cells) instead of
+ * O(n_x h^2); exact integer phases.  An independent arrangement of the sum,
+ * accurate to the FP32 rounding of the output, for cross-checking the other
+ * forms on every cell.  V [dev] float[n_x] in eV; VWh [dev] float[n_x][Q/2]
+ * (row = cell), written; ws as for wmc_kernel_eval (its 2Q-double phase table
+ * is overwritten). */
+wmc_status wmc_kernel_eval_dft(const wmc_params* p, const float* V, float* VWh, void* ws, wmc_stream_t stream);
+
 /* The N = 2 network of Sec. 2.3 -- Eq. (kernel_ML) with N = 2 and the
  * barycentric weights (omega^V = (1, 1), omega^theta = (1/2, 1/2),
  * W_l = w_l = -2 dx / (hbar L_C), one cosine factor): the terms V(l) sin(theta_l)

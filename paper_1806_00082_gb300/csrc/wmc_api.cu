@@ -65,6 +65,7 @@ Layout layout(const wmc_params& p) {
   L.B2 = o; o = align256(o + sizeof(float) * (size_t)L.Kp2 * (size_t)L.Np);
   L.tc = o; o = align256(o + tc_images_bytes(p));
   L.plan = o; o = align256(o + sizeof(PlanStatus) * ((nx + kPlanCells - 1) / kPlanCells));
+  L.dft = o; o = align256(o + sizeof(double) * 2 * (size_t)p.Q);
   L.total = o;
   return L;
 }
@@ -95,6 +96,7 @@ View view(const wmc_params& p, void* ws) {
   v.B2 = reinterpret_cast<float*>(b + L.B2);
   v.tc = b + L.tc;
   v.plan = reinterpret_cast<PlanStatus*>(b + L.plan);
+  v.dft = reinterpret_cast<double*>(b + L.dft);
   return v;
 }
 
@@ -484,6 +486,13 @@ wmc_status wmc_kernel_eval_n2(const wmc_params* p, const float* V, const int32_t
     e = launch_kernel_eval(*p, V, occ, nullptr, n_occ, n_occ, v.B2, VWh, s, 2);
   if (e == cudaErrorNotSupported) return WMC_ERR_UNSUPPORTED;
   return cuda_status(e);
+}
+
+wmc_status wmc_kernel_eval_dft(const wmc_params* p, const float* V, float* VWh, void* ws, wmc_stream_t stream) {
+  NvtxRange nvtx("wmc_kernel_eval_dft");
+  if (!params_ok(p) || !V || !VWh || !ws) return WMC_ERR_ARG;
+  const View v = view(*p, ws);
+  return cuda_status(launch_kernel_dft(*p, V, v.dft, VWh, (cudaStream_t)stream));
 }
 
 wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows, int64_t* cdf, double* gamma,

@@ -99,7 +99,7 @@ struct PlanStatus {
 // Byte offsets of the workspace regions (all 256-aligned).
 struct Layout {
   size_t header, T, R, IP, reach, occ, row_map, VWh, ccdf, scale, gamma, gthr, thr_cell, D, xlo, xhi, items, pairs, B,
-      B2, tc, plan, total;
+      B2, tc, plan, dft, total;
   long long max_items;
   unsigned pair_cap;  // entries of the pair queue
   int h;     // Q / 2
@@ -135,6 +135,7 @@ struct View {
   float* B2;               // [Kp2][Np] folded matrix of the N = 2 network, pair offset u
   void* tc;                // tensor-core operand images of S (BF16, FP16 hi, FP16 lo)
   PlanStatus* plan;        // [ceil(n_x / kPlanCells)] published prefixes of the plan's blocks
+  double* dft;             // [2 Q] cos and sin of the Q phases (sliding-window evaluation)
 };
 View view(const wmc_params& p, void* ws);
 
@@ -221,6 +222,8 @@ cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_
 cudaError_t launch_materialize(const wmc_params& p, const View& v, const int32_t* hist, uint32_t t, int32_t* cell,
                                float* f, int16_t* M, int8_t* sign, long long capacity, cudaStream_t s);
 cudaError_t launch_density(const wmc_params& p, const int32_t* hist, int64_t* rho, cudaStream_t s);
+// Every cell's kernel row by the FP64 sliding window (CS: 2 Q doubles of scratch).
+cudaError_t launch_kernel_dft(const wmc_params& p, const float* V, double* CS, float* VWh, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, long long n, uint32_t* out,
                           cudaStream_t s);
 cudaError_t launch_philox_throughput(uint32_t k0, uint32_t k1, int pairs_per_thread, uint32_t* out, long long n_threads,

@@ -565,3 +565,82 @@ cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_
 }
 
 }  // namespace wmc
+
+namespace wmc {
+
+// ---------------------------------------------------------------- sliding-window evaluation (FP64)
+// Eq. (wigner-1d-discrete) on every cell by a sliding window: for the
+// half-period column r, E(l) = exp(i 2 pi l r / Q) and
+//   W(i) = sum_{l=i-h}^{i+h} V(l) E(l),   VWh[i][r] = c Im[E(-i) W(i)],
+// W(i + 1) = W(i) + V(i+h+1) E(i+h+1) - V(i-h) E(i-h).  One thread per
+// (column, run of kDftSeg cells): the window sum at the run's first cell
+// directly, then one slide per cell, all in FP64 with the exact integer
+// phases l r mod Q (cos and sin of the Q phases staged in shared memory).
+// Lanes take consecutive columns, so the potential loads are broadcasts and
+// the row stores coalesce.
+constexpr int kDftSeg = 256;
+
+__global__ __launch_bounds__(256) void k_kernel_dft(const float* __restrict__ V, int n_x, int bc, int Q,
+                                                    const double* __restrict__ CS, double c,
+                                                    float* __restrict__ VWh) {
+  extern __shared__ double s_cs[];  // [Q] cos, [Q] sin
+  const int h = Q / 2;
+  for (int q = threadIdx.x; q < 2 * Q; q += blockDim.x) s_cs[q] = CS[q];
+  __syncthreads();
+  const double* sC = s_cs;
+  const double* sS = s_cs + Q;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = (int)(idx % h);
+  const long long seg = idx / h;
+  const long long i0 = seg * kDftSeg;
+  if (i0 >= n_x) return;
+  const long long i1 = i0 + kDftSeg < n_x ? i0 + kDftSeg : n_x;
+  // W at i0
+  double wr = 0.0, wi = 0.0;
+  long long t = (((i0 - h) % Q) * r % Q + Q) % Q;
+  for (long long l = i0 - h; l <= i0 + h; ++l) {
+    const double v = (double)pot(V, n_x, bc, l);
+    wr = fma(v, sC[t], wr);
+    wi = fma(v, sS[t], wi);
+    t += r;
+    if (t >= Q) t -= Q;
+  }
+  long long ti = ((i0 % Q) * r) % Q;           // phase of E(i)
+  long long ta = (((i0 + h + 1) % Q) * r) % Q;  // of E(i + h + 1)
+  long long tb = ((((i0 - h) % Q + Q) % Q) * r) % Q;  // of E(i - h)
+  for (long long i = i0; i < i1; ++i) {
+    VWh[(size_t)i * h + r] = (float)(c * (sC[ti] * wi - sS[ti] * wr));
+    const double va = (double)pot(V, n_x, bc, i + h + 1), vb = (double)pot(V, n_x, bc, i - h);
+    wr += va * sC[ta] - vb * sC[tb];
+    wi += va * sS[ta] - vb * sS[tb];
+    ti += r;
+    if (ti >= Q) ti -= Q;
+    ta += r;
+    if (ta >= Q) ta -= Q;
+    tb += r;
+    if (tb >= Q) tb -= Q;
+  }
+}
+
+__global__ void k_dft_tables(int Q, double* __restrict__ CS) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Q; t += gridDim.x * blockDim.x) {
+    CS[t] = cospi(2.0 * (double)t / (double)Q);
+    CS[Q + t] = sinpi(2.0 * (double)t / (double)Q);
+  }
+}
+
+cudaError_t launch_kernel_dft(const wmc_params& p, const float* V, double* CS, float* VWh, cudaStream_t s) {
+  const int h = p.Q / 2;
+  k_dft_tables<<<(p.Q + 255) / 256, 256, 0, s>>>(p.Q, CS);
+  const long long threads = (long long)h * ((p.n_x + kDftSeg - 1) / kDftSeg);
+  const size_t sm = sizeof(double) * 2 * (size_t)p.Q;
+  if (sm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_kernel_dft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  const double c = -2.0 / (kHbarEVs * (double)p.Q);
+  k_kernel_dft<<<(unsigned)((threads + 255) / 256), 256, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, CS, c, VWh);
+  return cudaGetLastError();
+}
+
+}  // namespace wmc

@@ -33,6 +33,7 @@ EXPORTS = (
     "wmc_batch_autotune", "wmc_batch_get_counters", "wmc_potential_tanh", "wmc_potential_tanh_vjp",
     "wmc_kernel_eval_rows", "wmc_kernel_vjp", "wmc_check_wait", "wmc_step_timing", "wmc_step_timing_read",
     "wmc_get_error", "wmc_philox_throughput", "wmc_kernel_eval_n2", "wmc_set_id_base",
+    "wmc_kernel_eval_dft",
 )
 
 
@@ -140,6 +141,7 @@ def load(path: str | None = None):
             "wmc_kernel_vjp": ([pp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
             "wmc_kernel_eval_n2": ([pp, vp, vp, i32, i32, vp, vp, vp], i32),
             "wmc_set_id_base": ([pp, vp, ctypes.c_uint64, vp], i32),
+            "wmc_kernel_eval_dft": ([pp, vp, vp, vp, vp], i32),
             "wmc_get_error": ([pp, vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_char_p, ctypes.c_size_t], i32),
             "wmc_philox_throughput": ([u32, u32, i32, vp, i64, vp], i32),
         }
@@ -258,6 +260,15 @@ def kernel_eval_n2(p: Params, V: torch.Tensor, occ: torch.Tensor, ws: torch.Tens
         out = torch.empty((n, p.h), dtype=torch.float32, device=V.device)
     _check("wmc_kernel_eval_n2", load().wmc_kernel_eval_n2(ctypes.byref(p), _ptr(V), _ptr(occ), n, prec, _ptr(out),
                                                            _ptr(ws), _stream()))
+    return out
+
+
+def kernel_eval_dft(p: Params, V: torch.Tensor, ws: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """wmc_kernel_eval_dft: every cell's half-period row by the FP64 sliding window."""
+    if out is None:
+        out = torch.empty((p.n_x, p.h), dtype=torch.float32, device=V.device)
+    _check("wmc_kernel_eval_dft", load().wmc_kernel_eval_dft(ctypes.byref(p), _ptr(V), _ptr(out), _ptr(ws),
+                                                             _stream()))
     return out
 
 
