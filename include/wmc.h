@@ -82,13 +82,24 @@ typedef enum wmc_status {
   WMC_ERR_UNSUPPORTED = 6   /* precision or shape not supported by this build */
 } wmc_status;
 
-/* Input precision of the sine x dV contraction (accumulation is FP32). */
+/* Input precision of the sine x dV contraction (accumulation is FP32).
+ * WMC_FP32 asks for FP32 accuracy and lets the library choose the form: the
+ * 3xTF32 tensor-core form for windows Q > 256 (its split kernel keeps the
+ * TF32 hi x hi product of every K block in its own accumulator and sums the
+ * blocks in FP32 registers; measured normwise error 3.6e-7 at Q = 1024 and
+ * 4.9e-7 at Q = 2048 against 2.9e-7 for the CUDA-core form, at 3x its speed),
+ * the CUDA-core form for Q <= 256, for the N = 2 network and where the split
+ * kernel does not hold the window.  WMC_FP32_SIMT always takes the CUDA-core
+ * form.  The FP16 split is faster still but FP16's exponent range (|dV| below
+ * 65504 eV, full precision for |dV| above about 1e-4 eV) makes its accuracy
+ * depend on the potential's scale, so it stays an explicit choice. */
 typedef enum wmc_precision {
-  WMC_FP32 = 0,        /* FP32 inputs, compensated FP32 accumulation (SIMT) */
+  WMC_FP32 = 0,        /* FP32 accuracy, form chosen by the library (above) */
   WMC_BF16 = 1,        /* BF16 inputs on the tensor cores */
   WMC_FP16 = 2,        /* FP16 inputs on the tensor cores */
   WMC_FP16_SPLIT = 3,  /* FP16 hi/lo split, three tensor-core products */
-  WMC_TF32X3 = 4       /* TF32 hi/lo split, three tensor-core products */
+  WMC_TF32X3 = 4,      /* TF32 hi/lo split, three tensor-core products */
+  WMC_FP32_SIMT = 5    /* FP32 inputs, compensated FP32 accumulation on the CUDA cores */
 } wmc_precision;
 
 /* Device flags, readable with wmc_get_counters(). */
@@ -193,7 +204,8 @@ wmc_status wmc_get_error(const wmc_params* p, const void* ws, wmc_stream_t strea
  *   V    [dev] float[n_x], eV.
  *   occ  [dev] int32[n_occ], cells in [0, n_x) (any order, repeats allowed).
  *   n_occ 0 .. n_x (host value).
- *   prec WMC_FP32 or a tensor-core form (WMC_ERR_UNSUPPORTED if not built).
+ *   prec WMC_FP32 (FP32 accuracy, form chosen as described at wmc_precision),
+ *        WMC_FP32_SIMT or a tensor-core form (WMC_ERR_UNSUPPORTED if not built).
  *   VWh  [dev] float[n_occ][Q/2], half-period rows (layout above); written.
  * ------------------------------------------------------------------------- */
 wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
@@ -209,10 +221,12 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
  * library's device memory, which every GPU that loads the library holds until
  * the process exits; no call allocates.
  *   Limit: Q <= 1024, else WMC_ERR_CAPACITY (nothing is launched).
- *   V, occ, n_occ, VWh as for wmc_kernel_eval (FP32 form).
- *   The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any stream
- *   capture.  All calls share the array and each refills what it reads, so
+ *   V, occ, n_occ, VWh as for wmc_kernel_eval with WMC_FP32_SIMT (the same
+ *   tiled CUDA-core kernel and sine values: bit-identical for Q > 256).
+ *   Every call looks up the array's device address in the current context
+ *   (no address outlives a context, e.g. across cudaDeviceReset); make the
+ *   first call of a process before any stream capture, since it may load the
+ *   library's device code.  All calls share the array and each refills what it reads, so
  *   calls that overlap on the GPU (other streams, other threads) race on it:
  *   serialise them. */
 wmc_status wmc_kernel_eval_noalloc(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
@@ -278,7 +292,7 @@ wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows,
  * ------------------------------------------------------------------------- */
 
 /* Rule 2 rebuild: enumerates the survivors of the net histogram hist [dev]
- * int32[n_x][n_M] (row-major ids, work items of at most 7168 ids of one cell), marks the
+ * int32[n_x][n_M] (row-major ids, work items of at most 4096 ids of one cell), marks the
  * cells the next drift can reach (occupied cells and their neighbour in each
  * drift direction present) as the occupied list for the kernel, and, if
  * rho [dev] int64[n_x] is not NULL, writes the density (rule 1) of hist.

@@ -340,7 +340,8 @@ wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_p
                                 void* ws, wmc_stream_t stream) {
   NvtxRange nvtx("wmc_kernel_eval_rows");
   if (!params_ok(p) || !V || !VWh || !ws || n_pot < 0) return WMC_ERR_ARG;
-  if (prec != WMC_FP32 && prec != WMC_BF16 && prec != WMC_FP16 && prec != WMC_FP16_SPLIT && prec != WMC_TF32X3)
+  if (prec != WMC_FP32 && prec != WMC_BF16 && prec != WMC_FP16 && prec != WMC_FP16_SPLIT && prec != WMC_TF32X3 &&
+      prec != WMC_FP32_SIMT)
     return WMC_ERR_UNSUPPORTED;
   const long long rows = (long long)n_pot * p->n_x;
   if (rows == 0) return WMC_OK;
@@ -348,6 +349,7 @@ wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_p
   const View v = view(*p, ws);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
+  prec = (wmc_precision)resolve_precision(*p, (int)prec, 1);
   if (prec != WMC_FP32)
     e = launch_kernel_eval_tc(*p, (int)prec, V, nullptr, nullptr, (int)rows, (int)rows, v.tc, VWh, &v.hdr->flags, s);
   else if (small_window(*p))

@@ -145,7 +145,13 @@ __global__ void k_check_wait(const uint32_t* signal, long long max_cycles, DevHe
 static wmc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WMC_OK : WMC_ERR_CUDA; }
 
 static bool prec_supported(wmc_precision prec) {
-  return prec == WMC_FP32 || prec == WMC_BF16 || prec == WMC_FP16 || prec == WMC_FP16_SPLIT || prec == WMC_TF32X3;
+  return prec == WMC_FP32 || prec == WMC_BF16 || prec == WMC_FP16 || prec == WMC_FP16_SPLIT || prec == WMC_TF32X3 ||
+         prec == WMC_FP32_SIMT;
+}
+
+// the form that runs (internal code: WMC_FP32 = the CUDA cores)
+static wmc_precision form_of(const wmc_params& p, wmc_precision prec, int net = 1) {
+  return (wmc_precision)resolve_precision(p, (int)prec, net);
 }
 
 // Kernel rows, CDFs and thresholds of the occupied list in the workspace:
@@ -458,6 +464,7 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
   if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   if (n_occ == 0) return WMC_OK;
   const View v = view(*p, ws);
+  prec = form_of(*p, prec);
   if (prec != WMC_FP32)
     return cuda_status(launch_kernel_eval_tc(*p, (int)prec, V, occ, nullptr, n_occ, n_occ, v.tc, VWh, &v.hdr->flags,
                                              (cudaStream_t)stream));
@@ -474,6 +481,7 @@ wmc_status wmc_kernel_eval_n2(const wmc_params* p, const float* V, const int32_t
   if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   if (prec == WMC_TF32X3) return WMC_ERR_UNSUPPORTED;
   if (n_occ == 0) return WMC_OK;
+  prec = form_of(*p, prec, 2);
   const View v = view(*p, ws);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
@@ -515,7 +523,7 @@ wmc_status wmc_kernel_eval_occupied(const wmc_params* p, const float* V, wmc_pre
   if (!params_ok(p) || !V || !ws) return WMC_ERR_ARG;
   if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   const View v = view(*p, ws);
-  return cuda_status(kernel_and_cdf_occupied(*p, v, V, prec, (cudaStream_t)stream));
+  return cuda_status(kernel_and_cdf_occupied(*p, v, V, form_of(*p, prec), (cudaStream_t)stream));
 }
 
 wmc_status wmc_kernel_table_occupied(const wmc_params* p, const float* table, void* ws, wmc_stream_t stream) {
@@ -548,6 +556,7 @@ wmc_status wmc_run(const wmc_params* p, const float* V, int32_t* hist_a, int32_t
     return WMC_ERR_ARG;
   if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   if (n_steps == 0) return WMC_OK;
+  prec = form_of(*p, prec);
   const View v = view(*p, ws);
   cudaStream_t s = (cudaStream_t)stream;
   k_set_step<<<1, 1, 0, s>>>(v.hdr, t_first - 1u);

@@ -831,13 +831,18 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
 // block holds 128 rows x 64 FP16 or x 32 TF32 values.  One CTA per 128 rows
 // and one column tile.  K runs in passes of `bp` blocks (the A_hi / A_lo
 // blocks of a pass stay in shared memory while B_hi / B_lo stream through a
-// 2-stage ring); the first half of the passes accumulates A_hi B_hi into one
-// FP32 accumulator and the second half into another (the K halves of the
-// other forms), the cross terms go to a third.  Roles as in
-// k_kernel_eval_tc_ws; the builders start a pass once the MMAs of the previous
-// one have released A (a_free).
+// 2-stage ring).  The tensor core's FP32 accumulation does not round to
+// nearest: its error grows with the number of MMAs accumulated into one
+// TMEM accumulator.  So the A_hi B_hi product of every K block goes to its own
+// accumulator (three rotating 128-column TMEM buffers), which the epilogue
+// warps drain into FP32 registers (round to nearest) as each block completes;
+// the cross terms, 2^-11 smaller, share a fourth accumulator over all of K.
+// Roles as in k_kernel_eval_tc_ws; the builders build a pass, then drain its
+// blocks, and the drain of its last block (all MMAs before it complete) frees
+// A for the next pass.
 constexpr int kSpStages = 2;
 constexpr int kSpMaxHalf = 4;  // blocks resident per pass
+constexpr int kSpParts = 3;    // per-K-block accumulators (the cross-term accumulator is a fourth)
 
 // blocks per pass: half of K for FP16 (one or two passes), 4 for TF32
 __host__ __device__ constexpr int split_pass_blocks(int KB, bool tf32) {
@@ -872,7 +877,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
   float* sV = reinterpret_cast<float*>(sB + (size_t)kSpStages * 2 * kTileBytes);  // shared with the staging
   __shared__ __align__(8) uint64_t a_ready[kSpMaxHalf];
   __shared__ __align__(8) uint64_t b_full[kSpStages], b_empty[kSpStages];
-  __shared__ __align__(8) uint64_t a_free, acc_full, drain;
+  __shared__ __align__(8) uint64_t acc_full[kSpParts], acc_empty[kSpParts], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
 
@@ -883,7 +888,6 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nt = blockIdx.y;
   const int n_pass = (KB + bp - 1) / bp;
-  const int pass_m1 = (n_pass + 1) / 2;  // first pass accumulating into the second hi x hi accumulator
   const int n_tiles = KB;  // B tiles streamed: one per K block
 
   if (warp == 0) tmem_alloc(&tmem_slot, 512u);
@@ -893,8 +897,10 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
       mbar_init(&b_full[q], 1);
       mbar_init(&b_empty[q], 1);
     }
-    mbar_init(&a_free, 1);
-    mbar_init(&acc_full, 1);
+    for (int q = 0; q < kSpParts; ++q) {
+      mbar_init(&acc_full[q], 1);
+      mbar_init(&acc_empty[q], kWsBuilders / 32);  // one arrival per epilogue warp
+    }
     mbar_init(&drain, 1);
     fence_mbar_init();
     s_abort = 0;
@@ -903,7 +909,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t acc_m0 = tmem, acc_m1 = tmem + (uint32_t)TN, acc_x = tmem + 2u * TN;
+  const uint32_t acc_x = tmem + (uint32_t)(kSpParts * TN);  // cross terms; block buffers at tmem + TN b
 
   if (warp == kWsBuilders / 32 + 1) {
     // ---- B producer: tile kb of column tile nt, hi and lo, in K order
@@ -932,23 +938,24 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
     if (lane == 0) {
       for (int pass = 0; pass < n_pass && !s_abort; ++pass) {
         const int kb0 = pass * bp, kb1 = min(KB, kb0 + bp);
-        const uint32_t acc_m = pass >= pass_m1 ? acc_m1 : acc_m0;
         for (int kb = kb0; kb < kb1; ++kb) {
-          const int kbl = kb - kb0, st = kb % kSpStages;
+          const int kbl = kb - kb0, st = kb % kSpStages, buf = kb % kSpParts;
           if (!mbar_wait(&a_ready[kbl], (uint32_t)(pass & 1)) ||
-              !mbar_wait(&b_full[st], (uint32_t)((kb / kSpStages) & 1))) {
+              !mbar_wait(&b_full[st], (uint32_t)((kb / kSpStages) & 1)) ||
+              (kb >= kSpParts && !mbar_wait(&acc_empty[buf], (uint32_t)(((kb / kSpParts) - 1) & 1)))) {
             atomicOr(flags, WMC_FLAG_TIMEOUT);
             s_abort = 1;
             break;
           }
           tc_fence_after();
+          const uint32_t acc_m = tmem + (uint32_t)(buf * TN);
           const uint32_t ah = smem_u32(sAh + (size_t)kbl * kTileBytes), al = smem_u32(sAl + (size_t)kbl * kTileBytes);
           const uint32_t bh = smem_u32(sB + (size_t)st * 2 * kTileBytes), bl = bh + kTileBytes;
 #pragma unroll
           for (int s4 = 0; s4 < TK / 16; ++s4) {
             const uint32_t o = s4 * kKStepBytes;
             const uint64_t dah = smem_desc(ah + o), dbh = smem_desc(bh + o);
-            const bool first_m = kb == kb0 && s4 == 0 && (pass == 0 || pass == pass_m1);
+            const bool first_m = s4 == 0;
             if (TF32) {
               mma_tf32(acc_m, dah, dbh, idesc, first_m ? 0u : 1u);
               mma_tf32(acc_x, dah, smem_desc(bl + o), idesc, (kb == 0 && s4 == 0) ? 0u : 1u);
@@ -960,9 +967,8 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
             }
           }
           mma_commit(&b_empty[st]);
+          mma_commit(&acc_full[buf]);
         }
-        if (s_abort) break;
-        mma_commit(pass + 1 < n_pass ? &a_free : &acc_full);
       }
       if (s_abort) {
         mma_commit(&drain);
@@ -1007,17 +1013,15 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
       V_d[d] = V + (size_t)((occ || !valid_d[d]) ? 0 : row / n_x) * n_x;
     }
     const bool fast = contig && (h & 3) == 0;
+    // epilogue slice of warp w: TMEM lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31
+    const int quad = warp & 3, cq = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    float sacc[32];  // sum over the K blocks drained so far of A_hi B_hi
+#pragma unroll
+    for (int q = 0; q < 32; ++q) sacc[q] = 0.f;
+    bool drained_all = true;
     for (int pass = 0; pass < n_pass; ++pass) {
       const int kb0 = pass * bp, kb1 = min(KB, kb0 + bp), cnt = kb1 - kb0;
-      if (pass > 0) {
-        // the previous pass's MMAs must have read A before it is overwritten
-        const bool ok = __all_sync(0xffffffffu, !s_abort && mbar_wait(&a_free, (uint32_t)((pass - 1) & 1)));
-        if (!ok) {
-          if (lane == 0) atomicOr(flags, WMC_FLAG_TIMEOUT);
-          s_abort = 1;
-          break;
-        }
-      }
       for (int kbl = 1 - par; kbl < cnt; kbl += 2)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kbl])) : "memory");
 #pragma unroll 1
@@ -1089,32 +1093,49 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
         fence_proxy_async_smem();
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kbl])) : "memory");
       }
+      // drain the pass's K blocks in order; after the last one every MMA that
+      // reads this pass's A has completed, so the next pass may overwrite it
+      for (int kb = kb0; kb < kb1 && drained_all; ++kb) {
+        const int buf = kb % kSpParts;
+        int okw = 1;
+        if (lane == 0) okw = !s_abort && mbar_wait(&acc_full[buf], (uint32_t)((kb / kSpParts) & 1));
+        if (__shfl_sync(0xffffffffu, okw, 0) == 0) {  // warp-uniform: the TMEM loads are warp-collective
+          if (lane == 0) atomicOr(flags, WMC_FLAG_TIMEOUT);
+          s_abort = 1;
+          drained_all = false;
+          break;
+        }
+        tc_fence_after();
+        uint32_t r0[16], r1[16];
+        const uint32_t ta = tmem + (uint32_t)(buf * TN) + lane_base + (uint32_t)(cq * 32);
+        tmem_ld16_issue(ta, r0);
+        tmem_ld16_issue(ta + 16u, r1);
+        tmem_wait16(r0);
+        tmem_wait16(r1);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          sacc[q] = __fadd_rn(sacc[q], __uint_as_float(r0[q]));
+          sacc[16 + q] = __fadd_rn(sacc[16 + q], __uint_as_float(r1[q]));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
+      }
+      if (!drained_all) break;
     }
-    // epilogue: v = c ((hi-hi first half + hi-hi second half) + scale x cross)
-    const int quad = warp & 3, cq = warp >> 2;
+    // epilogue: v = c (sum of the block products + 2^-11 x cross)
     float* stg = sV + warp * kWsStageFloats;
-    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     const bool vec_ok = (h & 3) == 0 && (reinterpret_cast<uintptr_t>(VWh) & 15) == 0;
-    const bool ok = __all_sync(0xffffffffu, !s_abort && mbar_wait(&acc_full, 0u));
-    if (!ok) {
-      if (lane == 0) atomicOr(flags, WMC_FLAG_TIMEOUT);
-      s_abort = 1;
-    } else {
-      tc_fence_after();
-#pragma unroll 1
+    if (drained_all) {
+#pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         const int cc = cq * 32 + hf * 16;
         const int col0 = nt * TN + cc;
-        float a[16], b[16], x[16];
-        tmem_ld16(acc_m0 + lane_base + (uint32_t)cc, a);
-        if (n_pass > 1) tmem_ld16(acc_m1 + lane_base + (uint32_t)cc, b);
+        float a[16], x[16];
         tmem_ld16(acc_x + lane_base + (uint32_t)cc, x);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          float v = a[q];
-          if (n_pass > 1) v = __fadd_rn(v, b[q]);
-          a[q] = __fmul_rn(c, __fadd_rn(v, __fmul_rn(x[q], kLoScale)));
-        }
+        for (int q = 0; q < 16; ++q) a[q] = __fmul_rn(c, __fadd_rn(sacc[hf * 16 + q], __fmul_rn(x[q], kLoScale)));
 #pragma unroll
         for (int g = 0; g < 4; ++g)
           *reinterpret_cast<float4*>(stg + lane * 16 + 4 * (g ^ ((lane >> 1) & 3))) =
@@ -1191,6 +1212,17 @@ cudaError_t launch_init_tc_images(const wmc_params& p, void* images, cudaStream_
   const size_t n2 = g.bytes_per_image2 / 2;
   k_init_tc_images<<<256, 256, 0, s>>>(p.Q, g.KB2, g.NT, b2, b2 + n2, b2 + 2 * n2, 2);
   return cudaGetLastError();
+}
+
+// The form behind a requested precision: WMC_FP32 takes the 3xTF32 split
+// kernel for Q > 256 (N = 1 network) where its shared memory holds the
+// window, else the CUDA-core form; WMC_FP32_SIMT the CUDA-core form.  The
+// result is the internal code: WMC_FP32 then always means the CUDA cores.
+int resolve_precision(const wmc_params& p, int prec, int net) {
+  if (prec == WMC_FP32_SIMT) return WMC_FP32;
+  if (prec != WMC_FP32 || net != 1 || p.Q <= 256) return prec;
+  const TcImages g = tc_geometry(p);
+  return ws_split_smem_bytes(g.KB32, g_h(p), true) <= 226 * 1024 ? WMC_TF32X3 : WMC_FP32;
 }
 
 // The N = 2 network (net = 2) runs on the warp-specialised BF16 / FP16 and

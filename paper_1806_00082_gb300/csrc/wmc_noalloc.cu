@@ -19,8 +19,6 @@
 // earlier call left there, but calls that overlap on the GPU (on different
 // streams, or from several threads) race on it and must be serialised by the
 // caller.
-#include <mutex>
-
 #include "wmc_device.cuh"
 
 namespace wmc {
@@ -32,9 +30,6 @@ constexpr int kNoallocMaxNp = 512;  // Q/2 rounded up to 64
 
 static __device__ __align__(256) float g_sine_scratch[kNoallocMaxKp * kNoallocMaxNp];
 
-std::mutex g_scratch_mu;
-float* g_scratch_ptr[64] = {};
-
 // B[kk][r] = sin(2 pi ((kk+1) r mod Q) / Q) for kk < h-1, r < h, zero elsewhere.
 __global__ void k_fill_sine_scratch(float* __restrict__ B, int Q, int Kp, int Np) {
   const long long n = (long long)Kp * Np;
@@ -42,21 +37,16 @@ __global__ void k_fill_sine_scratch(float* __restrict__ B, int Q, int Kp, int Np
     B[q] = sine_entry_n1(Q, (int)(q / Np), (int)(q % Np));
 }
 
-// Device address of the scratch array on the current device.  In host code the
-// name g_sine_scratch is only a host-side stand-in for the symbol, so the
-// address is looked up once per device, with that device current, and cached.
+// Device address of the scratch array in the current context.  In host code
+// the name g_sine_scratch is only a host-side stand-in for the symbol, so the
+// address is looked up on every call: a cached address would outlive the
+// context it belongs to (after cudaDeviceReset the next context may place the
+// array elsewhere).
 wmc_status scratch_on_current_device(float** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return WMC_ERR_CUDA;
-  if (dev < 0 || dev >= 64) return WMC_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_sine_scratch);
-    if (e != cudaSuccess || ptr == nullptr) return WMC_ERR_CUDA;
-    g_scratch_ptr[dev] = static_cast<float*>(ptr);
-  }
-  *out = g_scratch_ptr[dev];
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_sine_scratch);
+  if (e != cudaSuccess || ptr == nullptr) return WMC_ERR_CUDA;
+  *out = static_cast<float*>(ptr);
   return WMC_OK;
 }
 

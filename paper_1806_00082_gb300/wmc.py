@@ -17,8 +17,9 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libwmc.so")
 
-FP32, BF16, FP16, FP16_SPLIT, TF32X3 = 0, 1, 2, 3, 4
-PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp16": FP16, "fp16_split": FP16_SPLIT, "tf32x3": TF32X3}
+FP32, BF16, FP16, FP16_SPLIT, TF32X3, FP32_SIMT = 0, 1, 2, 3, 4, 5
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp16": FP16, "fp16_split": FP16_SPLIT, "tf32x3": TF32X3,
+              "fp32_simt": FP32_SIMT}
 
 FLAG_RATE, FLAG_CAPACITY, FLAG_TIMEOUT = 1, 2, 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "capacity exceeded", 3: "gamma dt >= 1", 4: "CUDA error",

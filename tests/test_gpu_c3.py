@@ -6,7 +6,8 @@ with p' ~ V_W^+ / gamma, and the signed histogram (rule 2) all run at scale.
 
 Bars: with the oracle's FP64 kernel table fed to both sides (same Philox
 streams) histograms and counters are bit-exact over the first five steps; with
-the kernel evaluated in the loop by the GPU (FP32, FP16 hi/lo split, 3xTF32)
+the kernel evaluated in the loop by the GPU (FP32 accuracy: the 3xTF32
+tensor-core form at this Q; the CUDA-core FP32 form; the FP16 hi/lo split)
 the density stays within 1e-3 L1 of the oracle's FP64 run under common random
 numbers.
 """
@@ -69,7 +70,7 @@ def test_c3_full_size_bit_exact_with_oracle_table(wmc):
     assert int(ref.sum()) == int(h0.sum()) - st[oracle.ST_ABSORBED_SIGNED] - st[oracle.ST_DROPPED_SIGNED]
 
 
-@pytest.mark.parametrize("form", ["fp32", "fp16_split", "tf32x3"])
+@pytest.mark.parametrize("form", ["fp32", "fp32_simt", "fp16_split"])
 def test_c3_production_loop_density(wmc, form):
     """wmc_run with the kernel computed in the loop (CUDA graph) against the
     oracle's FP64 run over the first five steps."""

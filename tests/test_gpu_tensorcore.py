@@ -3,8 +3,11 @@
 error, reading 13), and the FP32 form.
 
 Expected input-rounding errors (numpy estimates at Q = 1024): BF16 about 3-6e-3,
-FP16 about 2e-4, FP16 hi/lo split at the FP32 level (the 1e-6 bar); 3xTF32
-measured 1.6e-6."""
+FP16 about 2e-4.  The split forms keep each K block's hi x hi product in its
+own tensor-memory accumulator and sum the blocks in FP32 registers: measured
+3.6e-7 at Q = 1024 and 4.9e-7 at Q = 2048 on every cell of the double barrier
+(the CUDA-core FP32 form: 2.9e-7), against 9.3e-7 and 2.1e-6 with the K halves
+in two accumulators.  WMC_FP32 runs the 3xTF32 form for Q > 256."""
 import numpy as np
 import pytest
 
@@ -15,9 +18,7 @@ from tests._util import normwise
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# 3xTF32 measures 1.6e-6 at Q = 1024, against 9.3e-7 for the FP16 split whose
-# hi/lo parts have the same width
-TOL = {"bf16": 1.5e-2, "fp16": 1e-3, "fp16_split": 1e-6, "tf32x3": 2.5e-6}
+TOL = {"bf16": 1.5e-2, "fp16": 1e-3, "fp16_split": 5e-7, "tf32x3": 5e-7, "fp32": 5e-7, "fp32_simt": 5e-7}
 
 
 @pytest.fixture(scope="module")
@@ -35,7 +36,7 @@ def _cells(wl, n, seed):
     return c.astype(np.int32)
 
 
-@pytest.mark.parametrize("form", ["bf16", "fp16", "fp16_split", "tf32x3"])
+@pytest.mark.parametrize("form", ["bf16", "fp16", "fp16_split", "tf32x3", "fp32", "fp32_simt"])
 @pytest.mark.parametrize("wl,n", [(wi.BARRIER_100, 100), (wi.BARRIER_2000, 333), (wi.DOUBLE_BARRIER_16384, 333)])
 def test_tensorcore_forms_vs_fp64(wmc, form, wl, n):
     p = wmc.Params.of(wl)
@@ -174,9 +175,24 @@ def test_tensorcore_wide_window(wmc, form):
         _REF["wide"] = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), V, cells)[:, wl.Q // 2:]
     ref = _REF["wide"]
     assert np.all(np.isfinite(got))
-    # the split forms accumulate the hi x hi products in FP32 over two halves of
-    # the 1023-term window (no compensation inside the tensor core): about
-    # twice their Q = 1024 error, measured 2.1e-6 (FP16 split) and 3.4e-6 (3xTF32)
-    tol = {"fp16_split": 3e-6, "tf32x3": 5e-6}.get(form, TOL[form])
+    # the split forms over the 1023-term window: 16 K blocks drained one by one
+    # (measured 4.9e-7 on every cell)
+    tol = {"fp16_split": 1e-6, "tf32x3": 1e-6}.get(form, TOL[form])
     assert normwise(got, ref) <= tol, (form, normwise(got, ref))
     assert wmc.get_counters(p, ws)["flags"] == 0
+
+
+@pytest.mark.parametrize("wl,form", [(wi.DOUBLE_BARRIER_16384, "tf32x3"), (wi.BARRIER_2000, "fp32_simt"),
+                                     (wi.BARRIER_100, "fp32_simt")])
+def test_fp32_request_runs_the_stated_form(wmc, wl, form):
+    """WMC_FP32 is the 3xTF32 tensor-core form for Q > 256 and the CUDA-core
+    form otherwise: bit-identical rows to the form asked for by name."""
+    p = wmc.Params.of(wl)
+    V = torch.from_numpy(wi.potential(wl)).cuda()
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    cells = np.concatenate([np.arange(wl.n_x // 2 - 70, wl.n_x // 2 + 70), [0, wl.n_x - 1]]).astype(np.int32)
+    occ = torch.from_numpy(cells % wl.n_x).cuda()
+    a = wmc.kernel_eval(p, V, occ, ws, prec=wmc.FP32).cpu().numpy()
+    b = wmc.kernel_eval(p, V, occ, ws, prec=wmc.PRECISIONS[form]).cpu().numpy()
+    assert np.array_equal(a, b)

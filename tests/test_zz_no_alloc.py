@@ -6,8 +6,10 @@ to a pool allocator, or one that forbids allocation after start-up.  Its
 scratch (the sine matrix) is a fixed array in the library's device memory.
 
 Checked through the C ABI against wmc_kernel_eval (the workspace entry point)
-within the kernel tolerance of the other tests, on consecutive calls that reuse
-the shared array with different window sizes.  Collected last on purpose; it
+on consecutive calls that reuse the shared array with different window sizes:
+bit-identical to its CUDA-core form where both run the tiled kernel (Q > 256),
+and within the kernel tolerance of the other tests otherwise and against the
+default FP32-accuracy form.  Collected last on purpose; it
 passes alone in a fresh process and after the rest of the suite.
 """
 import numpy as np
@@ -41,12 +43,16 @@ def test_noalloc_matches_workspace_entry_point_on_consecutive_calls():
         occ = torch.from_numpy(cells).cuda()
         ws = wmc.workspace(p)
         wmc.init(p, ws)
-        ref = wmc.kernel_eval(p, V, occ, ws)
+        ref = wmc.kernel_eval(p, V, occ, ws, prec=wmc.FP32_SIMT)
+        dflt = wmc.kernel_eval(p, V, occ, ws)
         out = torch.full_like(ref, float("nan"))
         wmc.kernel_eval_noalloc(p, V, occ, out)
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
+        if wl.Q > 256:
+            assert torch.equal(out, ref)
         assert _normwise(out, ref) <= KERNEL_TOL
+        assert _normwise(out, dflt) <= KERNEL_TOL
 
 
 def test_noalloc_rejects_window_beyond_limit():
