@@ -174,6 +174,49 @@ __device__ __forceinline__ void philox4x32_10_x2(uint4& a, uint4& b, uint32_t k0
   }
 }
 
+// The round keys of Philox4x32-10 under key (k0, k1): rk[2 r], rk[2 r + 1] =
+// k0 + r W0, k1 + r W1 (r = 0..9), the Weyl sequence of the key schedule.
+struct PhiloxKeys {
+  uint32_t rk[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys K;
+  for (int r = 0; r < 10; ++r) {
+    K.rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    K.rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  return K;
+}
+
+// The same two evaluations with the round keys read from K: inside a kernel
+// whose parameters hold K, the keys are constant operands of the XORs and the
+// key schedule costs no instructions.
+__device__ __forceinline__ void philox4x32_10_x2k(uint4& a, uint4& b, const PhiloxKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * a.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * a.z;
+    const unsigned long long q0 = (unsigned long long)0xD2511F53u * b.x;
+    const unsigned long long q1 = (unsigned long long)0xCD9E8D57u * b.z;
+    a = make_uint4((uint32_t)(p1 >> 32) ^ a.y ^ K.rk[2 * r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ a.w ^ K.rk[2 * r + 1],
+                   (uint32_t)p0);
+    b = make_uint4((uint32_t)(q1 >> 32) ^ b.y ^ K.rk[2 * r], (uint32_t)q1, (uint32_t)(q0 >> 32) ^ b.w ^ K.rk[2 * r + 1],
+                   (uint32_t)q0);
+  }
+}
+
+__device__ __forceinline__ uint4 philox4x32_10k(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.rk[2 * r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ K.rk[2 * r + 1],
+                   (uint32_t)p0);
+  }
+  return c;
+}
+
 // Work items of a cell holding t survivors (an upper bound when its first id
 // is not a multiple of 4; surplus items are empty).
 __host__ __device__ __forceinline__ int items_of_cell(unsigned long long t) {

@@ -45,6 +45,7 @@ struct StepArgs {
   int n_x, n_M, Q, r0, child_wrap;
   uint32_t sim, k0, k1, t;
   int t_from_device;
+  PhiloxKeys K;               // round keys of (k0, k1)
 };
 
 // p' of the pair created by particle id (column k, sign sgn) in cell c and the
@@ -56,7 +57,7 @@ __device__ __forceinline__ void pair_children(const StepArgs& a, int rows_by_cel
                                               long long& drop_signed) {
   const int n_M = a.n_M, h = a.Q / 2;
   const int orow = rows_by_cell ? c : __ldg(a.row_map + c);
-  const uint4 wp = philox4x32_10(make_uint4(id, t, kPurposePick, a.sim), a.k0, a.k1);
+  const uint4 wp = philox4x32_10k(make_uint4(id, t, kPurposePick, a.sim), a.K);
   const unsigned long long U2 = ((unsigned long long)(wp.x >> 5) << 26) | (unsigned long long)(wp.y >> 6);
   const float* vrow = a.VWh + (size_t)orow * h;
   const long long* crow = a.ccdf + (size_t)orow * kCdfBlocks;
@@ -180,6 +181,7 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
   uint32_t base = 0u;
   bool need_gen = false, any_full = false;
   uint32_t rej = 0u;
+  unsigned long long thr_st = 0ull;  // event threshold of a stayer: thr(i)
 
   int item = 0;
   if (lane == 0) item = (int)atomicAdd(&a.hdr->item_ticket, 1u);
@@ -245,6 +247,7 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
         s_thr[wid][2] = thr_p;
       }
       need_gen = (thr_m | thr_0 | thr_p) != 0ull;
+      thr_st = thr_0;
       // events: a stayer tests thr(i), a mover thr(i +- 1) (0 outside the
       // domain: absorbed particles create no pair); rej = the largest of them
       // as a quick rejection of a whole quad (exact unless a threshold is 2^32)
@@ -275,6 +278,7 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
     // bucket state
     int k = 0, sgn = 1, dir = 0;
     uint32_t end = 0u, flip = 0u, mthr = 0xffffffffu;
+    unsigned long long thr_mv = 0ull;  // event threshold of a mover: thr(i + dir)
     int n_st = 0, n_mv = 0;
     auto load_bucket = [&]() {
       end = base + (uint32_t)P(k + 1);
@@ -283,6 +287,7 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
       flip = xm.x;
       mthr = xm.y;
       dir = flip ? -1 : (mthr != 0xffffffffu ? 1 : 0);
+      thr_mv = s_thr[wid][dir + 1];
     };
     auto flush_bucket = [&]() {
       if (n_st) atomicAdd(out_i + k, sgn > 0 ? n_st : -n_st);
@@ -299,7 +304,7 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
     };
     // pair event of particle id (mover or not) of the current bucket
     auto test_event = [&](uint32_t id, uint32_t u, int mv) {
-      const unsigned long long thr = s_thr[wid][mv ? dir + 1 : 1];
+      const unsigned long long thr = mv ? thr_mv : thr_st;
       if ((unsigned long long)u < thr) {
         const int pos = atomicAdd(&s_qn[wid], 1);
         if (pos < kPairQ)  // always (the queue is drained whenever it could fill within one quad iteration)
@@ -348,31 +353,39 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
     for (int jq = 0; jq < nq; ++jq) {
       const uint32_t q = q_first + (uint32_t)jq;
       const uint32_t qa = q << 2;
-      if (has && qa < g1 && qa + 4u > g0) {
+      if (qa < g1 && qa + 4u > g0) {  // (g0 = g1 = 0 for a lane without ids)
         uint4 wr = make_uint4(q, t - 1u, kPurposeRepos, a.sim);
         uint4 wg = make_uint4(q, t, kPurposeGen, a.sim);
-        if (need_gen) philox4x32_10_x2(wr, wg, a.k0, a.k1);
-        else wr = philox4x32_10(wr, a.k0, a.k1);
+        if (need_gen) philox4x32_10_x2k(wr, wg, a.K);
+        else wr = philox4x32_10k(wr, a.K);
         const bool ev_possible = need_gen && (min(min(wg.x, wg.y), min(wg.z, wg.w)) < rej || any_full);
-        // the ids of the quad in [g0, g1), each in its bucket: a bucket ends
-        // exactly where the next non-empty one starts
-        const uint32_t vmask = first_mask((int)(g1 - qa)) & ~first_mask((int)(g0 - qa));
+        // the ids of the quad in [g0, g1), bucket by bucket: the ids below the
+        // current bucket's end are its members (a bucket ends exactly where the
+        // next non-empty one starts), counted together from their move bits;
+        // a lane whose quad crosses a bucket end takes a second pass
+        uint32_t rem = 0xfu;
+        if (qa < g0 || qa + 4u > g1) rem = first_mask((int)(g1 - qa)) & ~first_mask((int)(g0 - qa));
         const uint32_t w4[4] = {wr.x, wr.y, wr.z, wr.w};
         const uint32_t u4[4] = {wg.x, wg.y, wg.z, wg.w};
+        while (true) {
+          const uint32_t inb = rem & first_mask((int)(end - qa));
+          uint32_t mvb = 0u;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if ((vmask >> j) & 1u) {
-            const uint32_t id = qa + (uint32_t)j;
-            if (id >= end) {
-              flush_bucket();
-              k = s_nx[k];
-              load_bucket();
-            }
-            const int mv = (w4[j] ^ flip) > mthr;
-            n_mv += mv;
-            n_st += 1 - mv;
-            if (ev_possible) test_event(id, u4[j], mv);
+          for (int j = 0; j < 4; ++j) mvb |= (uint32_t)((w4[j] ^ flip) > mthr) << j;
+          mvb &= inb;
+          const int m = __popc(mvb);
+          n_mv += m;
+          n_st += __popc(inb) - m;
+          if (ev_possible) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if ((inb >> j) & 1u) test_event(qa + (uint32_t)j, u4[j], (int)((mvb >> j) & 1u));
           }
+          rem &= ~inb;
+          if (!rem) break;
+          flush_bucket();
+          k = s_nx[k];
+          load_bucket();
         }
       }
       __syncwarp();
@@ -458,6 +471,7 @@ cudaError_t launch_step(const wmc_params& p, const View& v, const int32_t* hist_
   a.sim = p.sim;
   a.k0 = (uint32_t)(p.seed & 0xffffffffu);
   a.k1 = (uint32_t)(p.seed >> 32);
+  a.K = philox_keys(a.k0, a.k1);
   a.t = t;
   a.t_from_device = t_from_device;
   const int grid = step_grid(p.n_M);
