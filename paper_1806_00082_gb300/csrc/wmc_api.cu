@@ -6,6 +6,8 @@
 #include <atomic>
 #include <mutex>
 
+#include <cuda.h>  // driver types only: the two driver calls below come through cudaGetDriverEntryPointByVersion
+
 #include "wmc_internal.cuh"
 
 namespace wmc {
@@ -175,11 +177,41 @@ static cudaError_t kernel_and_cdf_occupied(const wmc_params& p, const View& v, c
                     &v.hdr->flags, s, v.hdr, v.ccdf);
 }
 
+// Unique id of the calling thread's current CUDA context (0 if the driver
+// cannot say).  Streams, events and graphs cached per device are kept with the
+// id of the context that made them: after cudaDeviceReset the device has a
+// new context and those handles are dropped (not destroyed: they died with
+// their context) and made again.
+static unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    (void)cudaGetLastError();
+  });
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
+
 // A second stream per device and a fork/join event pair, for running the
 // single-block plan beside the kernel stage.
 struct AuxStream {
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  unsigned long long ctx = 0;
 };
 
 static bool aux_stream(AuxStream& out) {
@@ -187,9 +219,12 @@ static bool aux_stream(AuxStream& out) {
   static AuxStream per_dev[16];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return false;
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(mu);
   AuxStream& a = per_dev[dev];
+  if (a.s && a.ctx != ctx) a = AuxStream();  // made in an earlier context of this device
   if (!a.s) {
+    a.ctx = ctx;
     if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess) return false;
     if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess)
@@ -251,6 +286,7 @@ struct StepTiming {
   std::atomic<int> on{0};
   cudaEvent_t ev[8][2] = {};
   bool recorded[8] = {};
+  unsigned long long ctx[8] = {};
 };
 static StepTiming g_timing;
 
@@ -262,7 +298,13 @@ cudaError_t step_timing_record(cudaStream_t s, bool end) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 8) return cudaSuccess;  // devices beyond the table are not timed
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_timing.mu);
+  if (g_timing.ctx[dev] != ctx) {  // events of an earlier context of this device
+    g_timing.ev[dev][0] = g_timing.ev[dev][1] = nullptr;
+    g_timing.recorded[dev] = false;
+    g_timing.ctx[dev] = ctx;
+  }
   cudaEvent_t& ev = g_timing.ev[dev][end ? 1 : 0];
   if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return e;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -287,6 +329,7 @@ struct GraphSlot {
   int prec;
   cudaStream_t stream;
   int device;
+  unsigned long long ctx;
   int timing;
   cudaGraphExec_t exec = nullptr;
 };
@@ -307,10 +350,15 @@ static wmc_status launch_cached(GraphCache& gc, const wmc_params* p, const float
   std::lock_guard<std::mutex> lock(gc.mu);
   int dev = 0;
   cudaGetDevice(&dev);
+  const unsigned long long ctx = current_context_id();
   const int timing = step_timing_on();
   GraphSlot* hit = nullptr;
   GraphSlot* victim = &gc.slot[0];
   for (GraphSlot& g : gc.slot) {
+    if (g.valid && g.device == dev && g.ctx != ctx) {  // made in an earlier context of this device
+      g.valid = false;
+      g.exec = nullptr;
+    }
     if (g.valid && memcmp(&g.p, p, sizeof(wmc_params)) == 0 && g.V == V && g.a == a && g.b == b && g.ws == ws &&
         g.prec == (int)prec && g.stream == s && g.device == dev && g.timing == timing) {
       hit = &g;
@@ -345,6 +393,7 @@ static wmc_status launch_cached(GraphCache& gc, const wmc_params* p, const float
     gs.prec = (int)prec;
     gs.stream = s;
     gs.device = dev;
+    gs.ctx = ctx;
     gs.timing = timing;
     hit = &gs;
   }
@@ -427,7 +476,8 @@ wmc_status wmc_step_timing_read(float* ms) {
   cudaEvent_t b = nullptr, e = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_timing.mu);
-    if (dev < 0 || dev >= 8 || !g_timing.recorded[dev]) return WMC_ERR_UNSUPPORTED;
+    if (dev < 0 || dev >= 8 || !g_timing.recorded[dev] || g_timing.ctx[dev] != current_context_id())
+      return WMC_ERR_UNSUPPORTED;
     b = g_timing.ev[dev][0];
     e = g_timing.ev[dev][1];
   }
