@@ -663,10 +663,35 @@ def adjoint_rate(wmc, torch, dev, stream, n_pot=64, reps=5):
                 bw += e1.elapsed_time(e2) * 1e-3
     h = w.Q // 2
     flops = 2.0 * n_pot * w.n_x * (h - 1) ** 2
+    # the kernel adjoint alone (wmc_kernel_vjp: the Abar contraction on the
+    # tensor cores, 3xTF32, then the scatter to Vbar), L2 flushed before each call
+    with torch.cuda.stream(stream):
+        VWh, _ = kernel_of_potential(theta0.clone(), p, 16, 16, 0.5, ws)
+        VWh = VWh.detach().contiguous()
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+        vjp = 0.0
+        for r in range(reps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wmc.kernel_vjp(p, VWh, g, gg, n_pot, ws)
+            e1.record(stream)
+            stream.synchronize()
+            if r >= 2:
+                vjp += e0.elapsed_time(e1) * 1e-3
+        vjp /= reps
+    peaks, src = _peaks()
+    issued = 3.0 * 2.0 * n_pot * w.n_x * h * h  # three TF32 products over the padded h x h contraction
+    peak_tf32 = peaks["bf16_tflops"] * 1e12 * (1.1 / 2.25)
     return {"workload": f"{n_pot} potentials x {w.n_x} cells, Q = {w.Q}, n_M = {w.n_M}, 64 parameters each",
             "forward_s": fw / reps, "backward_s": bw / reps,
             "forward_tflops_algorithmic": flops / (fw / reps) / 1e12,
             "backward_tflops_algorithmic": flops / (bw / reps) / 1e12,
+            "kernel_vjp_s": vjp,
+            "kernel_vjp_roofline": {"bound": "tensor", "achieved": issued / vjp / 1e12, "peak": peak_tf32 / 1e12,
+                                    "unit": "TFLOP/s", "frac": issued / vjp / peak_tf32, "traffic": None,
+                                    "peak_source": f"{src} bf16 dense x 1.1/2.25 (nominal tf32/bf16)",
+                                    "note": "lower bound: the time includes the CUDA-core scatter to Vbar"},
             "grad_err_bound_normwise": 1e-4}
 
 

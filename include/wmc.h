@@ -88,9 +88,11 @@ typedef enum wmc_status {
  * TF32 hi x hi product of every K block in its own accumulator and sums the
  * blocks in FP32 registers; measured normwise error 3.6e-7 at Q = 1024 and
  * 4.9e-7 at Q = 2048 against 2.9e-7 for the CUDA-core form, at 3x its speed),
- * the CUDA-core form for Q <= 256, for the N = 2 network and where the split
- * kernel does not hold the window.  WMC_FP32_SIMT always takes the CUDA-core
- * form.  The FP16 split is faster still but FP16's exponent range (|dV| below
+ * and in wmc_kernel_eval / wmc_kernel_eval_rows also for 128 <= Q <= 256 when
+ * the rows number at least 128 per SM; the CUDA-core form otherwise (smaller
+ * windows and row counts, the step loop's fused small-window stage, the N = 2
+ * network, windows the split kernel does not hold).  WMC_FP32_SIMT always
+ * takes the CUDA-core form.  The FP16 split is faster still but FP16's exponent range (|dV| below
  * 65504 eV, full precision for |dV| above about 1e-4 eV) makes its accuracy
  * depend on the potential's scale, so it stays an explicit choice. */
 typedef enum wmc_precision {
@@ -401,7 +403,10 @@ wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_p
  *   Gbar = gVW + g_gamma (cnt_pos(r) [VWh > 0] - cnt_neg(r) [VWh < 0]),
  *   Abar[i][m] = c sum_r Gbar[i][r] S[m][r],  Vbar[l] = sum_m Abar[l-m][m] - Abar[l+m][m],
  * cnt_pos(r) / cnt_neg(r) = momentum indices M of the grid with M = r / M = -r (mod Q).
- * Abar [dev] float[rows][Q/2] is caller scratch.  bc_potential 0 and Q <= 256. */
+ * Abar [dev] float[rows][Q/2] is caller scratch.  bc_potential 0 and Q <= 256.
+ * The Abar contraction runs on the tensor cores as 3xTF32 (TF32 hi/lo parts
+ * of Gbar and of S, per-K-block accumulators: FP32-level accuracy at the FP32
+ * exponent range of the gradients); the scatter to Vbar on the CUDA cores. */
 wmc_status wmc_kernel_vjp(const wmc_params* p, const float* VWh, const float* gVW, const float* g_gamma,
                           int32_t n_pot, float* Abar, float* Vbar, void* ws, wmc_stream_t stream);
 

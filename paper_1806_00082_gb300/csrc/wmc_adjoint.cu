@@ -14,7 +14,7 @@
 //   d gamma / d VWh[i][r] = cnt_pos(r) [VWh > 0] - cnt_neg(r) [VWh < 0].
 // Backward, for upstream gVW[i][r] and g_gamma[i]:
 //   Gbar[i][r] = gVW[i][r] + g_gamma[i] d gamma / d VWh[i][r],
-//   Abar[i][m] = c sum_r Gbar[i][r] S[m][r]                (a contraction),
+//   Abar[i][m] = c sum_r Gbar[i][r] S[m][r]                (a contraction, on the tensor cores),
 //   Vbar[l]    = sum_m Abar[l-m][m] - Abar[l+m][m]          (V = 0 outside the domain),
 //   theta_bar  = sum_l Vbar[l] dV(x_l)/d theta.
 #include "wmc_device.cuh"
@@ -22,14 +22,6 @@
 namespace wmc {
 
 namespace {
-
-// number of momentum indices M in [-n_M/2, n_M/2) with M = r (mod Q), r in
-// [0, Q), for n_M = a Q + b and r0 = -n_M/2 mod Q
-__device__ __forceinline__ int grid_count(int r, int Q, int a, int b, int r0) {
-  int off = r - r0;
-  if (off < 0) off += Q;
-  return a + (off < b ? 1 : 0);
-}
 
 // 1 - |tanh u| = 2 / (e^{2|u|} + 1), accurate where tanh saturates.
 __device__ __forceinline__ float tanh_tail(float u) { return 2.f / (expf(2.f * fabsf(u)) + 1.f); }
@@ -130,95 +122,6 @@ __global__ __launch_bounds__(kVjpThreads) void k_potential_tanh_vjp(const float*
   }
 }
 
-// ---------------------------------------------------------------- Abar
-// One warp per row: Gbar of the row in shared memory, then lane kk (= m - 1)
-// accumulates c sum_r Gbar[r] S[m][r] against the transposed sine matrix
-// staged in shared memory (compensated FP32 in chunks of 32 terms).
-constexpr int kAdjWarps = 8;
-
-template <int C, int R>  // R rows per warp share each sine load
-__global__ __launch_bounds__(kAdjWarps * 32) void k_adj_abar(int Q, int n_M, int rows, const float* __restrict__ VWh,
-                                                             const float* __restrict__ gVW,
-                                                             const float* __restrict__ g_gamma,
-                                                             const float* __restrict__ B, int Np, float c,
-                                                             float* __restrict__ Abar) {
-  extern __shared__ float s_mem[];
-  const int h = Q / 2;
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ca = n_M / Q, cb = n_M - ca * Q, cr0 = ((-(n_M / 2)) % Q + Q) % Q;
-  float* s_Bt = s_mem;                                   // [h][32 C]: s_Bt[r][kk] = S[kk+1][r]
-  float* s_g = s_mem + h * 32 * C + wid * R * 32 * C;    // Gbar of this warp's rows
-  if ((int)(blockIdx.x * kAdjWarps * R) >= rows) return;
-  for (int q = threadIdx.x; q < h * 32 * C; q += blockDim.x) {
-    const int r = q / (32 * C), kk = q % (32 * C);
-    s_Bt[q] = kk < h - 1 ? __ldg(B + (size_t)kk * Np + r) : 0.f;
-  }
-  __syncthreads();
-  for (int row0 = (blockIdx.x * kAdjWarps + wid) * R; row0 < rows; row0 += gridDim.x * kAdjWarps * R) {
-#pragma unroll
-    for (int gq = 0; gq < R; ++gq) {
-      const int row = row0 + gq;
-      const bool ok = row < rows;
-      const float gg = (ok && g_gamma) ? __ldg(g_gamma + row) : 0.f;
-#pragma unroll
-      for (int cc = 0; cc < C; ++cc) {
-        const int r = lane + 32 * cc;
-        float g = 0.f;
-        if (ok && r < h) {
-          if (gVW) g = __ldg(gVW + (size_t)row * h + r);
-          if (gg != 0.f && r > 0) {
-            const float v = __ldg(VWh + (size_t)row * h + r);
-            const int dg = v > 0.f ? grid_count(r, Q, ca, cb, cr0) : (v < 0.f ? -grid_count(Q - r, Q, ca, cb, cr0) : 0);
-            g = __fadd_rn(g, __fmul_rn(gg, (float)dg));
-          }
-        }
-        s_g[gq * 32 * C + r] = g;
-      }
-    }
-    __syncwarp();
-    float sacc[R][C], eacc[R][C];
-#pragma unroll
-    for (int gq = 0; gq < R; ++gq)
-#pragma unroll
-      for (int q = 0; q < C; ++q) sacc[gq][q] = eacc[gq][q] = 0.f;
-    for (int r0 = 0; r0 < h; r0 += 32) {
-      float part[R][C];
-#pragma unroll
-      for (int gq = 0; gq < R; ++gq)
-#pragma unroll
-        for (int q = 0; q < C; ++q) part[gq][q] = 0.f;
-      const int r1 = min(r0 + 32, h);
-      for (int r = r0; r < r1; ++r) {
-        const float* bt = s_Bt + r * 32 * C;
-        float bv[C];
-#pragma unroll
-        for (int q = 0; q < C; ++q) bv[q] = bt[lane + 32 * q];
-#pragma unroll
-        for (int gq = 0; gq < R; ++gq) {
-          const float g = s_g[gq * 32 * C + r];
-#pragma unroll
-          for (int q = 0; q < C; ++q) part[gq][q] = fmaf(g, bv[q], part[gq][q]);
-        }
-      }
-#pragma unroll
-      for (int gq = 0; gq < R; ++gq)
-#pragma unroll
-        for (int q = 0; q < C; ++q) two_sum_acc(sacc[gq][q], eacc[gq][q], part[gq][q]);
-    }
-#pragma unroll
-    for (int gq = 0; gq < R; ++gq) {
-      const int row = row0 + gq;
-      if (row >= rows) break;
-#pragma unroll
-      for (int q = 0; q < C; ++q) {
-        const int kk = lane + 32 * q;
-        if (kk < h - 1) Abar[(size_t)row * h + kk] = __fmul_rn(c, __fadd_rn(sacc[gq][q], eacc[gq][q]));
-      }
-    }
-    __syncwarp();
-  }
-}
-
 // ---------------------------------------------------------------- Vbar
 // Vbar[b][l] = sum_{m=1}^{h-1} Abar[b][l-m][m-1] - Abar[b][l+m][m-1], rows of
 // potential b at b n_x .. b n_x + n_x - 1, V = 0 outside the domain.  A block
@@ -273,33 +176,12 @@ cudaError_t launch_potential_tanh_vjp(const float* theta, int n_pot, int nb, int
 }
 
 cudaError_t launch_kernel_vjp(const wmc_params& p, int n_pot, const float* VWh, const float* gVW,
-                              const float* g_gamma, const float* B, float* Abar, float* Vbar, cudaStream_t s) {
-  const Layout L = layout(p);
-  const int h = L.h, rows = n_pot * p.n_x;
+                              const float* g_gamma, const void* tc_images, unsigned int* flags, float* Abar,
+                              float* Vbar, cudaStream_t s) {
+  const int h = p.Q / 2, rows = n_pot * p.n_x;
   if (rows <= 0) return cudaSuccess;
-  const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
-  const int C = h <= 32 ? 1 : (h <= 64 ? 2 : 4);
-  const int R = (long long)rows >= 4ll * num_sms() * kAdjWarps * 4 ? 4 : 1;
-  const size_t sm = sizeof(float) * ((size_t)h * 32 * C + (size_t)kAdjWarps * R * 32 * C);
-  int blocks = (rows + kAdjWarps * R - 1) / (kAdjWarps * R);
-  if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
-#define WMC_LAUNCH_ABAR(CC, RR)                                                                              \
-  do {                                                                                                       \
-    if (sm > 48 * 1024)                                                                                      \
-      cudaFuncSetAttribute(k_adj_abar<CC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);        \
-    k_adj_abar<CC, RR><<<blocks, kAdjWarps * 32, sm, s>>>(p.Q, p.n_M, rows, VWh, gVW, g_gamma, B, L.Np, c, Abar); \
-  } while (0)
-  if (R == 4) {
-    if (C == 1) WMC_LAUNCH_ABAR(1, 4);
-    else if (C == 2) WMC_LAUNCH_ABAR(2, 4);
-    else WMC_LAUNCH_ABAR(4, 4);
-  } else {
-    if (C == 1) WMC_LAUNCH_ABAR(1, 1);
-    else if (C == 2) WMC_LAUNCH_ABAR(2, 1);
-    else WMC_LAUNCH_ABAR(4, 1);
-  }
-#undef WMC_LAUNCH_ABAR
-  cudaError_t e = cudaGetLastError();
+  // Abar = c Gbar S^T: the contraction on the tensor cores (3xTF32 split)
+  cudaError_t e = launch_adjoint_abar_tc(p, rows, VWh, gVW, g_gamma, tc_images, Abar, flags, s);
   if (e != cudaSuccess) return e;
   const int tiles = (p.n_x + kVbarTile - 1) / kVbarTile;
   const size_t vsm = sizeof(float) * (size_t)kVbarChunk * h;
@@ -349,7 +231,7 @@ wmc_status wmc_kernel_eval_rows(const wmc_params* p, const float* V, int32_t n_p
   const View v = view(*p, ws);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  prec = (wmc_precision)resolve_precision(*p, (int)prec, 1);
+  prec = (wmc_precision)resolve_precision(*p, (int)prec, 1, rows);
   if (prec != WMC_FP32)
     e = launch_kernel_eval_tc(*p, (int)prec, V, nullptr, nullptr, (int)rows, (int)rows, v.tc, VWh, &v.hdr->flags, s);
   else if (small_window(*p))
@@ -364,9 +246,10 @@ wmc_status wmc_kernel_vjp(const wmc_params* p, const float* VWh, const float* gV
                           int32_t n_pot, float* Abar, float* Vbar, void* ws, wmc_stream_t stream) {
   NvtxRange nvtx("wmc_kernel_vjp");
   if (!params_ok(p) || !VWh || !Abar || !Vbar || !ws || n_pot < 0 || (!gVW && !g_gamma)) return WMC_ERR_ARG;
-  if (p->bc_potential != 0 || p->Q / 2 > 128) return WMC_ERR_UNSUPPORTED;
+  if (p->bc_potential != 0 || p->Q / 2 > kAdjMaxH) return WMC_ERR_UNSUPPORTED;
   const View v = view(*p, ws);
-  return launch_kernel_vjp(*p, n_pot, VWh, gVW, g_gamma, v.B, Abar, Vbar, (cudaStream_t)stream) == cudaSuccess
+  return launch_kernel_vjp(*p, n_pot, VWh, gVW, g_gamma, v.tc, &v.hdr->flags, Abar, Vbar, (cudaStream_t)stream) ==
+                 cudaSuccess
              ? WMC_OK
              : WMC_ERR_CUDA;
 }

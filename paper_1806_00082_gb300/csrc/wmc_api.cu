@@ -152,8 +152,8 @@ static bool prec_supported(wmc_precision prec) {
 }
 
 // the form that runs (internal code: WMC_FP32 = the CUDA cores)
-static wmc_precision form_of(const wmc_params& p, wmc_precision prec, int net = 1) {
-  return (wmc_precision)resolve_precision(p, (int)prec, net);
+static wmc_precision form_of(const wmc_params& p, wmc_precision prec, int net = 1, long long rows = 0) {
+  return (wmc_precision)resolve_precision(p, (int)prec, net, rows);
 }
 
 // Kernel rows, CDFs and thresholds of the occupied list in the workspace:
@@ -514,7 +514,7 @@ wmc_status wmc_kernel_eval(const wmc_params* p, const float* V, const int32_t* o
   if (!prec_supported(prec)) return WMC_ERR_UNSUPPORTED;
   if (n_occ == 0) return WMC_OK;
   const View v = view(*p, ws);
-  prec = form_of(*p, prec);
+  prec = form_of(*p, prec, 1, n_occ);
   if (prec != WMC_FP32)
     return cuda_status(launch_kernel_eval_tc(*p, (int)prec, V, occ, nullptr, n_occ, n_occ, v.tc, VWh, &v.hdr->flags,
                                              (cudaStream_t)stream));

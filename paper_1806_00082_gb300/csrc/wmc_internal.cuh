@@ -266,7 +266,13 @@ cudaError_t launch_materialize(const wmc_params& p, const View& v, const int32_t
                                float* f, int16_t* M, int8_t* sign, long long capacity, cudaStream_t s);
 cudaError_t launch_density(const wmc_params& p, const int32_t* hist, int64_t* rho, cudaStream_t s);
 // Every cell's kernel row by the FP64 sliding window (CS: 2 Q doubles of scratch).
-int resolve_precision(const wmc_params& p, int prec, int net);
+int resolve_precision(const wmc_params& p, int prec, int net, long long rows = 0);
+// The differentiation form's window limit (Q <= 256) and its Abar contraction
+// on the tensor cores.
+constexpr int kAdjMaxH = 128;
+cudaError_t launch_adjoint_abar_tc(const wmc_params& p, int rows, const float* VWh, const float* gVW,
+                                   const float* g_gamma, const void* images, float* Abar, unsigned int* flags,
+                                   cudaStream_t s);
 cudaError_t launch_kernel_dft(const wmc_params& p, const float* V, double* CS, float* VWh, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, long long n, uint32_t* out,
                           cudaStream_t s);

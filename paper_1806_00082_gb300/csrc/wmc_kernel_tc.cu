@@ -255,7 +255,7 @@ __global__ void k_init_tc_images(int Q, int KB, int NT, uint16_t* __restrict__ i
 // The same sine matrix as TF32 hi/lo pairs (hi = tf32(v), lo = tf32(v - hi)),
 // in 128 x 32 blocks of the swizzled layout (four 4-byte values per chunk).
 __global__ void k_init_tc_images32(int Q, int KB32, int NT, uint32_t* __restrict__ img_hi,
-                                   uint32_t* __restrict__ img_lo) {
+                                   uint32_t* __restrict__ img_lo, int transposed) {
   const long long total = (long long)NT * KB32 * TN * 32;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
@@ -263,7 +263,8 @@ __global__ void k_init_tc_images32(int Q, int KB32, int NT, uint32_t* __restrict
     const int e = (int)(q % (TN * 32));
     const int n = e / 32, k = e % 32;
     const int nt = blk / KB32, kb = blk % KB32;
-    const float v = sine_entry_n1(Q, kb * 32 + k, nt * TN + n);
+    // transposed (the adjoint's B): S[m][r] at n = m - 1, k = r
+    const float v = transposed ? sine_entry_n1(Q, nt * TN + n, kb * 32 + k) : sine_entry_n1(Q, kb * 32 + k, nt * TN + n);
     // chunk k / 4 of row n, value k % 4 in it
     const size_t off = (size_t)blk * (kTileBytes / 4) + (core_offset(n, (k >> 2) * 8) >> 2) + (k & 3);
     const uint32_t hi = to_tf32(v);
@@ -842,6 +843,36 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
 // A for the next pass.
 constexpr int kSpStages = 2;
 constexpr int kSpMaxHalf = 4;  // blocks resident per pass
+
+// NET = 3, the adjoint contraction Abar = c Gbar S^T of the differentiation
+// form: A is Gbar[row][r] = gVW[row][r] + g_gamma[row] dgamma/dVWh[row][r]
+// (K = h columns r), formed by the builders from these rows; the B image
+// holds S[m][r] at (n = m - 1, k = r).
+struct DenseA {
+  const float* gVW;      // [rows][h] or null
+  const float* VWh;      // [rows][h], the forward rows (sign of each entry)
+  const float* g_gamma;  // [rows] or null
+  int ca, cb, cr0;       // momentum grid: n_M = ca Q + cb, cr0 = -n_M/2 mod Q
+};
+
+// number of momentum indices M of the grid with M = r (mod Q)
+__device__ __forceinline__ int grid_count_tc(int r, int Q, int a, int b, int r0) {
+  int off = r - r0;
+  if (off < 0) off += Q;
+  return a + (off < b ? 1 : 0);
+}
+
+__device__ __forceinline__ float gbar_entry(const DenseA& g, int Q, int h, int row, int r) {
+  if (r >= h) return 0.f;
+  float v = g.gVW ? __ldg(g.gVW + (size_t)row * h + r) : 0.f;
+  const float gg = g.g_gamma ? __ldg(g.g_gamma + row) : 0.f;
+  if (gg != 0.f && r > 0) {
+    const float w = __ldg(g.VWh + (size_t)row * h + r);
+    const int dg = w > 0.f ? grid_count_tc(r, Q, g.ca, g.cb, g.cr0) : (w < 0.f ? -grid_count_tc(Q - r, Q, g.ca, g.cb, g.cr0) : 0);
+    v = __fadd_rn(v, __fmul_rn(gg, (float)dg));
+  }
+  return v;
+}
 constexpr int kSpParts = 3;    // per-K-block accumulators (the cross-term accumulator is a fourth)
 
 // blocks per pass: half of K for FP16 (one or two passes), 4 for TF32
@@ -860,7 +891,8 @@ template <bool TF32, int NET>
 __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
     const float* __restrict__ V, int n_x, int bc, int Q, const int* __restrict__ occ,
     const int* __restrict__ n_occ_dev, int n_occ_host, const void* __restrict__ img_hi_v,
-    const void* __restrict__ img_lo_v, int KB, float c, float* __restrict__ VWh, unsigned int* __restrict__ flags) {
+    const void* __restrict__ img_lo_v, int KB, float c, float* __restrict__ VWh, unsigned int* __restrict__ flags,
+    DenseA dense) {
   // FP16 x FP16 -> FP32 (format 0) or TF32 x TF32 -> FP32 (format 2)
   constexpr uint32_t idesc = idesc_f16(TF32 ? 2u : 0u);
   constexpr int KBLK = TF32 ? 32 : TK;   // K values per operand block
@@ -984,7 +1016,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
     const int potc = (occ || !validc) ? 0 : rowc / n_x;
     const int cell0 = occ ? __ldg(occ + row0) : row0 % n_x;
     const int pot0 = occ ? 0 : row0 / n_x;
-    const bool contig = builders_and(validc && cellc == cell0 + rc && potc == pot0);
+    const bool contig = NET != 3 && builders_and(validc && cellc == cell0 + rc && potc == pot0);
     if (contig) {
       const float* V0 = V + (size_t)pot0 * n_x;
       constexpr int kU = 4;
@@ -1046,6 +1078,44 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
           for (int d = 0; d < 4; ++d)
 #pragma unroll
             for (int e = 0; e < EPC; ++e) dv[d][e] = __fsub_rn(P[d + e + 1], N[d - e + EPC - 1]);
+        } else if (NET == 3) {
+          const int r0 = m0 - 1;
+          if ((h & 3) == 0 && EPC == 4 && r0 + 3 < h) {
+            // four consecutive columns of each row: one 16-byte load per operand
+            float4 gv[4], wv[4];
+            float gg[4];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+              const size_t o = (size_t)(row0 + 4 * rg + d) * h + r0;
+              gv[d] = (valid_d[d] && dense.gVW) ? __ldg(reinterpret_cast<const float4*>(dense.gVW + o))
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+              gg[d] = (valid_d[d] && dense.g_gamma) ? __ldg(dense.g_gamma + row0 + 4 * rg + d) : 0.f;
+              wv[d] = (valid_d[d] && gg[d] != 0.f) ? __ldg(reinterpret_cast<const float4*>(dense.VWh + o))
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+              const float g4[4] = {gv[d].x, gv[d].y, gv[d].z, gv[d].w};
+              const float w4[4] = {wv[d].x, wv[d].y, wv[d].z, wv[d].w};
+#pragma unroll
+              for (int e = 0; e < EPC; ++e) {
+                const int r = r0 + e;
+                float v = g4[e];
+                if (gg[d] != 0.f && r > 0) {
+                  const int dg = w4[e] > 0.f ? grid_count_tc(r, Q, dense.ca, dense.cb, dense.cr0)
+                                             : (w4[e] < 0.f ? -grid_count_tc(Q - r, Q, dense.ca, dense.cb, dense.cr0) : 0);
+                  v = __fadd_rn(v, __fmul_rn(gg[d], (float)dg));
+                }
+                dv[d][e] = valid_d[d] ? v : 0.f;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+#pragma unroll
+              for (int e = 0; e < EPC; ++e)
+                dv[d][e] = valid_d[d] ? gbar_entry(dense, Q, h, row0 + 4 * rg + d, m0 - 1 + e) : 0.f;
+          }
         } else {
 #pragma unroll
           for (int d = 0; d < 4; ++d)
@@ -1053,8 +1123,8 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
             for (int e = 0; e < EPC; ++e) {
               const int kk = m0 - 1 + e;
               dv[d][e] = 0.f;
-              if (contig) dv[d][e] = a_entry_window<NET>(sV + 4 * rg + d, h, cell0 + 4 * rg + d, kk);
-              else if (valid_d[d]) dv[d][e] = a_term<NET>(V_d[d], n_x, bc, h, cell_d[d], kk);
+              if (contig) dv[d][e] = a_entry_window<NET == 3 ? 1 : NET>(sV + 4 * rg + d, h, cell0 + 4 * rg + d, kk);
+              else if (valid_d[d]) dv[d][e] = a_term<NET == 3 ? 1 : NET>(V_d[d], n_x, bc, h, cell_d[d], kk);
             }
         }
         uint4 wh[4], wl[4];
@@ -1173,9 +1243,11 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws_split(
 // ---------------------------------------------------------------- host side
 struct TcImages {
   int KB, NT, KB32, KB2;     // 16-bit K blocks (64 values), column tiles, TF32 K blocks (32 values), N = 2 K blocks
+  int KBa;                   // the adjoint's TF32 K blocks (K = h), Q <= 256 only (else 0)
   size_t bytes_per_image;    // NT * KB * kTileBytes (BF16, FP16 hi, FP16 lo)
   size_t bytes_per_image32;  // NT * KB32 * kTileBytes (TF32 hi, TF32 lo)
   size_t bytes_per_image2;   // NT * KB2 * kTileBytes (N = 2 network: BF16, FP16 hi, FP16 lo)
+  size_t bytes_per_imagea;   // NT * KBa * kTileBytes (adjoint, TF32 hi, TF32 lo)
 };
 
 static int g_h(const wmc_params& p) { return p.Q / 2; }
@@ -1192,12 +1264,19 @@ static TcImages tc_geometry(const wmc_params& p) {
   g.bytes_per_image = (size_t)g.NT * g.KB * kTileBytes;
   g.bytes_per_image32 = (size_t)g.NT * g.KB32 * kTileBytes;
   g.bytes_per_image2 = (size_t)g.NT * g.KB2 * kTileBytes;
+  g.KBa = h <= kAdjMaxH ? (h + 31) / 32 : 0;
+  g.bytes_per_imagea = (size_t)g.NT * g.KBa * kTileBytes;
   return g;
 }
 
 size_t tc_images_bytes(const wmc_params& p) {
   const TcImages g = tc_geometry(p);
-  return 3 * g.bytes_per_image + 2 * g.bytes_per_image32 + 3 * g.bytes_per_image2;
+  return 3 * g.bytes_per_image + 2 * g.bytes_per_image32 + 3 * g.bytes_per_image2 + 2 * g.bytes_per_imagea;
+}
+
+static const uint8_t* adjoint_images(const void* images, const TcImages& g) {
+  return static_cast<const uint8_t*>(images) + 3 * g.bytes_per_image + 2 * g.bytes_per_image32 +
+         3 * g.bytes_per_image2;
 }
 
 cudaError_t launch_init_tc_images(const wmc_params& p, void* images, cudaStream_t s) {
@@ -1206,21 +1285,56 @@ cudaError_t launch_init_tc_images(const wmc_params& p, void* images, cudaStream_
   const size_t n16 = g.bytes_per_image / 2;
   k_init_tc_images<<<256, 256, 0, s>>>(p.Q, g.KB, g.NT, base, base + n16, base + 2 * n16, 1);
   uint32_t* b32 = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(images) + 3 * g.bytes_per_image);
-  k_init_tc_images32<<<256, 256, 0, s>>>(p.Q, g.KB32, g.NT, b32, b32 + g.bytes_per_image32 / 4);
+  k_init_tc_images32<<<256, 256, 0, s>>>(p.Q, g.KB32, g.NT, b32, b32 + g.bytes_per_image32 / 4, 0);
   uint16_t* b2 = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(images) + 3 * g.bytes_per_image +
                                              2 * g.bytes_per_image32);
   const size_t n2 = g.bytes_per_image2 / 2;
   k_init_tc_images<<<256, 256, 0, s>>>(p.Q, g.KB2, g.NT, b2, b2 + n2, b2 + 2 * n2, 2);
+  if (g.KBa) {
+    uint32_t* ba = reinterpret_cast<uint32_t*>(const_cast<uint8_t*>(adjoint_images(images, g)));
+    k_init_tc_images32<<<256, 256, 0, s>>>(p.Q, g.KBa, g.NT, ba, ba + g.bytes_per_imagea / 4, 1);
+  }
+  return cudaGetLastError();
+}
+
+// Abar = c Gbar S^T on the 3xTF32 split kernel (NET = 3), rows = n_pot n_x
+// implicit rows; Q <= 256.
+cudaError_t launch_adjoint_abar_tc(const wmc_params& p, int rows, const float* VWh, const float* gVW,
+                                   const float* g_gamma, const void* images, float* Abar, unsigned int* flags,
+                                   cudaStream_t s) {
+  const TcImages g = tc_geometry(p);
+  if (!g.KBa) return cudaErrorNotSupported;
+  if (rows <= 0) return cudaSuccess;
+  const uint8_t* ba = adjoint_images(images, g);
+  DenseA d;
+  d.gVW = gVW;
+  d.VWh = VWh;
+  d.g_gamma = g_gamma;
+  d.ca = p.n_M / p.Q;
+  d.cb = p.n_M - d.ca * p.Q;
+  d.cr0 = ((-(p.n_M / 2)) % p.Q + p.Q) % p.Q;
+  const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
+  const size_t sm = ws_split_smem_bytes(g.KBa, g_h(p), true);
+  const dim3 grid((rows + TM - 1) / TM, g.NT);
+  cudaError_t e = cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  k_kernel_eval_tc_ws_split<true, 3><<<grid, kWsThreads, sm, s>>>(nullptr, rows, 0, p.Q, nullptr, nullptr, rows, ba,
+                                                                  ba + g.bytes_per_imagea, g.KBa, c, Abar, flags, d);
   return cudaGetLastError();
 }
 
 // The form behind a requested precision: WMC_FP32 takes the 3xTF32 split
-// kernel for Q > 256 (N = 1 network) where its shared memory holds the
-// window, else the CUDA-core form; WMC_FP32_SIMT the CUDA-core form.  The
+// kernel (N = 1 network, where its shared memory holds the window) for
+// Q > 256, and for Q >= 128 when the rows fill a wave of 128-row tiles on
+// every SM (rows > 0: the row entry points; measured 2.4x faster than the
+// CUDA cores at Q = 256 over 262144 rows, error 1.6e-7 against 2.2e-7);
+// else the CUDA-core form.  WMC_FP32_SIMT is always the CUDA-core form.  The
 // result is the internal code: WMC_FP32 then always means the CUDA cores.
-int resolve_precision(const wmc_params& p, int prec, int net) {
+int resolve_precision(const wmc_params& p, int prec, int net, long long rows) {
   if (prec == WMC_FP32_SIMT) return WMC_FP32;
-  if (prec != WMC_FP32 || net != 1 || p.Q <= 256) return prec;
+  if (prec != WMC_FP32 || net != 1) return prec;
+  if (p.Q <= 256 && !(p.Q >= 128 && rows >= (long long)TM * num_sms())) return prec;
   const TcImages g = tc_geometry(p);
   return ws_split_smem_bytes(g.KB32, g_h(p), true) <= 226 * 1024 ? WMC_TF32X3 : WMC_FP32;
 }
@@ -1268,7 +1382,7 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
     cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_kernel_eval_tc_ws_split<true, 1><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
                                                                  n_occ_host, b32, b32 + g.bytes_per_image32,
-                                                                 g.KB32, c, VWh, flags);
+                                                                 g.KB32, c, VWh, flags, DenseA{});
   } else if (prec == WMC_FP16_SPLIT) {
     const size_t sm = tc_smem_bytes(true, g_h(p));
     cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1332,7 +1446,7 @@ static cudaError_t launch_tc_net(const wmc_params& p, int prec, const float* V, 
     cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<false, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_kernel_eval_tc_ws_split<false, NET><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ,
                                                                        n_occ_dev, n_occ_host, base + n16,
-                                                                       base + 2 * n16, KB, c, VWh, flags);
+                                                                       base + 2 * n16, KB, c, VWh, flags, DenseA{});
     return cudaGetLastError();
   }
   return cudaErrorNotSupported;
