@@ -135,11 +135,10 @@ __host__ __device__ __forceinline__ int step_lg_block(int n_M) {
 // Shared memory of a step block: the per-column move test (flip, threshold)
 // of the block, then per warp the row prefix in a padded layout (column k at
 // k + (k >> lg), so that lane l's block of E2 = 2^lg columns is contiguous and
-// bank-conflict free), the sign bits, the non-empty bits, the next non-empty
-// column after each column (16 bits) and the event queue.
+// bank-conflict free), the sign bits, the non-empty bits and the event queue.
 __host__ __device__ __forceinline__ int step_warp_words(int n_M) {
   const int E2 = 1 << step_lg_block(n_M);
-  return 32 * (E2 + 1) + 1 + 2 * ((n_M + 31) / 32) + (n_M + 1) / 2 + kPairQ;
+  return 32 * (E2 + 1) + 1 + 2 * ((n_M + 31) / 32) + kPairQ;
 }
 
 static size_t step_smem(int n_M) {
@@ -149,7 +148,7 @@ static size_t step_smem(int n_M) {
 // 4-bit mask of the elements j of a quad with j < d (d may be <= 0 or >= 4).
 __device__ __forceinline__ uint32_t first_mask(int d) { return d >= 4 ? 0xfu : (d <= 0 ? 0u : (1u << d) - 1u); }
 
-__global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
+__global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
   extern __shared__ __align__(16) uint32_t smem_step[];
   __shared__ int s_qn[kStepWarps];
   __shared__ unsigned long long s_thr[kStepWarps][3];  // event thresholds of cells i - 1, i, i + 1
@@ -162,8 +161,7 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
   const int NW = (n_M + 31) / 32;
   uint32_t* s_sg = wsm + 32 * (E2 + 1) + 1;             // sign bits (1: negative)
   uint32_t* s_nz = s_sg + NW;                            // non-empty bits
-  uint16_t* s_nx = reinterpret_cast<uint16_t*>(s_nz + NW);  // next non-empty column
-  uint32_t* s_q = s_nz + NW + (n_M + 1) / 2;              // event queue
+  uint32_t* s_q = s_nz + NW;                              // event queue
   const int rows_by_cell = (int)a.hdr->rows_by_cell;
   const uint32_t t = a.t_from_device ? a.hdr->step : a.t;
   const int n_items = a.hdr->n_items;
@@ -176,6 +174,13 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
   if (lane == 0) s_qn[wid] = 0;
   __syncthreads();
   auto P = [&](int k) { return s_pp[k + (k >> lg)]; };
+  // the first non-empty column after kk (n_M if none), from the non-empty bits
+  auto next_nonempty = [&](int kk) -> int {
+    int c = (kk + 1) >> 5;
+    uint32_t w = c < NW ? s_nz[c] & (0xffffffffu << ((kk + 1) & 31)) : 0u;
+    while (!w && ++c < NW) w = s_nz[c];
+    return w ? (c << 5) + __ffs(w) - 1 : n_M;
+  };
 
   int cur_i = -1;
   uint32_t base = 0u;
@@ -207,18 +212,6 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
         }
       }
       __syncwarp();
-      // next non-empty column after each column (n_M if none), word by word
-      // from the last, carrying the first non-empty column of later words
-      {
-        int carry = n_M;
-        for (int c = NW - 1; c >= 0; --c) {
-          const uint32_t z = s_nz[c];
-          const uint32_t above = z & ~((2u << lane) - 1u);  // (2 << 31 wraps to 0: no bits above lane 31)
-          const int kk = (c << 5) + lane;
-          if (kk < n_M) s_nx[kk] = (uint16_t)(above ? (c << 5) + __ffs(above) - 1 : carry);
-          if (z) carry = (c << 5) + __ffs(z) - 1;
-        }
-      }
       const int kb0 = min(lane << lg, n_M), kb1 = min(kb0 + E2, n_M);
       int* blk = s_pp + lane * (E2 + 1);
       int local = 0;
@@ -384,7 +377,7 @@ __global__ __launch_bounds__(kStepThreads, 3) void k_step(StepArgs a) {
           rem &= ~inb;
           if (!rem) break;
           flush_bucket();
-          k = s_nx[k];
+          k = next_nonempty(k);
           load_bucket();
         }
       }
