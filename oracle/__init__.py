@@ -23,6 +23,10 @@ Functions and the passages they follow:
   :func:`simulate_subdomain` one step of a range of cells whose particles are
   numbered after those of the cells before it.
 - :func:`density` -- rule 1: signed counts summed over M.
+
+``oracle/adjoint.py`` holds the differentiation form's FP64 adjoint and
+``oracle/n2train.py`` the trained N = 2 network of Sec. 2.3 (model, MSE loss,
+gradients and SGD), both in numpy.
 """
 from __future__ import annotations
 

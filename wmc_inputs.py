@@ -206,3 +206,31 @@ def tanh_parameters(n_pot: int, n_x: int = 4096, dx_nm: float = 0.25, n_barriers
             -slot / 4, slot / 4, n_barriers)
         th[b, 3 * n_barriers:] = rng.uniform(-0.02, 0.02, n_segments)
     return th.astype(np.float32)
+
+
+# The trained N = 2 network's data set (Sec. 2.3): Gaussian-bump potentials on
+# 256 cells of 0.5 nm, window L_C = 32 nm (Q = 64 = n_M), kernels of one period.
+N2_TRAIN = Workload(
+    name="n2-train-256", n_x=256, dx_m=0.5 * NM, Q=64, n_M=64, dt_s=0.05 * FS, steps=1, seed=4)
+
+
+def gaussian_bumps(n_examples: int, n_x: int = 256, dx_nm: float = 0.5, seed: int = 4) -> np.ndarray:
+    """Potentials [n_examples, n_x] (FP32, eV) of single Gaussian bumps
+    V0 exp(-(x - c)^2 / s^2) at the cell centres: height V0 U[0.05, 0.3] eV,
+    centre c U[0.25 L, 0.75 L], dispersion s U[1, 5] nm (PCG64 seed `seed`)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = n_x * dx_nm
+    x = (np.arange(n_x) + 0.5) * dx_nm
+    out = np.empty((n_examples, n_x), np.float32)
+    for e in range(n_examples):
+        V0 = rng.uniform(0.05, 0.3)
+        c = rng.uniform(0.25 * L, 0.75 * L)
+        s = rng.uniform(1.0, 5.0)
+        out[e] = (V0 * np.exp(-((x - c) / s) ** 2)).astype(np.float32)
+    return out
+
+
+def sgd_order(epochs: int, n_examples: int, seed: int = 5) -> np.ndarray:
+    """The examples of each epoch in a fresh random order: int32 [epochs, n_examples]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.stack([rng.permutation(n_examples) for _ in range(epochs)]).astype(np.int32)
