@@ -237,6 +237,7 @@ def native_arm(args, w):
     drift = drift_only_rate(wmc, torch, dev, stream, flush) if rank == 0 and not args.no_batched else None
     bat = batched_rate(wmc, torch, dev, stream) if rank == 0 and not args.no_batched else None
     adjo = adjoint_rate(wmc, torch, dev, stream) if rank == 0 and not args.no_batched else None
+    n2t = n2_train_rate(wmc, torch, dev, stream) if rank == 0 and not args.no_batched else None
 
     if rank != 0:
         if world > 1:
@@ -268,6 +269,7 @@ def native_arm(args, w):
         "drift_only": drift,
         "batched": bat,
         "adjoint": adjo,
+        "n2_train": n2t,
         "counters": {k: c[k] for k in ("pairs", "absorbed", "dropped", "n_occ", "population", "flags")},
         "device_status": {"code": err[0], "message": err[1]},
     }
@@ -574,6 +576,61 @@ def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
                            "forms": n2}}
 
 
+def n2_train_rate(wmc, torch, dev, stream, n_examples=100, epochs=200, n_runs=152):
+    """The trained N = 2 network (Sec. 2.3): 100 Gaussian-bump potentials on
+    256 cells (Q = n_M = 64), 200 epochs of SGD (one example per step), a sweep
+    of n_runs learning rates log-spaced over [1e-5, 1e-2] (the paper's 1e-5,
+    1e-4, 1e-3 among them), one thread block per run, all in one launch; the
+    exact kernels from wmc_kernel_eval_rows.  The FP64 oracle's SGD step is
+    timed on a bounded sample of steps."""
+    from paper_1806_00082_gb300 import n2train
+    w = wi.N2_TRAIN
+    p = wmc.Params.of(w)
+    ws = wmc.workspace(p, dev)
+    Vs = torch.from_numpy(wi.gaussian_bumps(n_examples, n_x=w.n_x)).to(dev)
+    order = torch.from_numpy(wi.sgd_order(epochs, n_examples)).to(dev)
+    lrs = torch.logspace(-5, -2, n_runs, device=dev)
+    for k, v in enumerate((1e-5, 1e-4, 1e-3)):  # the paper's three rates as exact values
+        lrs[int(round((math.log10(v) + 5) / 3 * (n_runs - 1)))] = v
+    with torch.cuda.stream(stream):
+        wmc.init(p, ws)
+        n2train.train(p, Vs, order[:2], lrs, ws)  # warm-up
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        params, loss = n2train.train(p, Vs, order, lrs, ws)
+        e1.record(stream)
+        stream.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    h = w.Q // 2
+    steps = n_runs * epochs * n_examples
+    terms = steps * w.n_x * h * h * 3.0  # model terms per step: forward + the two gradient sums
+    by_lr = {}
+    for v in (1e-5, 1e-4, 1e-3):
+        r = int(round((math.log10(v) + 5) / 3 * (n_runs - 1)))
+        by_lr[f"{v:g}"] = {"loss_first_epoch": float(loss[r, 0]), "loss_last_epoch": float(loss[r, -1])}
+    orc = {}
+    try:
+        import oracle
+        from oracle import n2train as nt
+        po = oracle.params(w)
+        Vh = Vs.cpu().numpy()
+        T = np.stack([oracle.kernel_rows(po, Vh[e], np.arange(w.n_x))[:, w.Q // 2:] for e in range(4)]) * nt.target_scale(w.Q)
+        prm = nt.initial_params(w.Q)
+        t0 = time.perf_counter()
+        n_s = 0
+        while time.perf_counter() - t0 < 5.0:
+            _, g = nt.loss_and_grad(prm, Vh[n_s % 4], T[n_s % 4], w.Q)
+            prm = prm - 1e-4 * g
+            n_s += 1
+        orc = {"sgd_steps_per_s": n_s / (time.perf_counter() - t0), "cores": 1, "sample": f"{n_s} SGD steps, FP64 numpy"}
+    except Exception as e:  # the timing is context; the GPU numbers stand without it
+        orc = {"unavailable": str(e)[:200]}
+    return {"workload": f"{w.name}: {n_examples} Gaussian bumps, {epochs} epochs, {n_runs} learning rates",
+            "seconds": sec, "sgd_steps_per_s": steps / sec, "model_terms_per_s": terms / sec,
+            "paper_learning_rates": by_lr, "oracle_fp64": orc}
+
+
 def drift_only_rate(wmc, torch, dev, stream, flush, steps=20, warmup=4):
     """Secondary leg, labelled drift-only: the 2000-cell barrier with 1e7
     particles, whose packet starts farther than L_C / 2 from the barrier, so
@@ -708,6 +765,8 @@ def single_leg(args):
         out = kernel_eval_rate(wmc, torch, dev, stream, flush, reps=max(1, args.steps))
     elif args.leg == "drift":
         out = drift_only_rate(wmc, torch, dev, stream, flush)
+    elif args.leg == "n2train":
+        out = n2_train_rate(wmc, torch, dev, stream)
     elif args.leg == "batched":
         out = batched_rate(wmc, torch, dev, stream, steps=max(2, args.steps), warmup=1)
     else:
@@ -726,7 +785,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the secondary legs (kernel, drift-only, "
                     "batched, adjoint)")
-    ap.add_argument("--leg", default="all", choices=["all", "kernel", "drift", "batched", "adjoint"],
+    ap.add_argument("--leg", default="all", choices=["all", "kernel", "drift", "batched", "adjoint", "n2train"],
                     help="run one secondary leg alone (for profiling); 'all' is the benchmark")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

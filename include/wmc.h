@@ -267,6 +267,39 @@ wmc_status wmc_kernel_eval_dft(const wmc_params* p, const float* V, float* VWh, 
 wmc_status wmc_kernel_eval_n2(const wmc_params* p, const float* V, const int32_t* occ, int32_t n_occ,
                               wmc_precision prec, float* VWh, void* ws, wmc_stream_t stream);
 
+/* The trained N = 2 network of Sec. 2.3: Eq. (kernel_ML) with N = 2 whose
+ * weights are learnt by stochastic gradient descent on a mean-squared-error
+ * loss against exact kernels.  Reduced units (kernels times hbar Q / 2, V in eV):
+ *   y(i, j) = cos(pi j / Q) sum_{d in D(i)} W[d] (wv1 V(i + d) + wv2 V(i + d + 1))
+ *                                           sin(2 pi j / Q (wt1 d + wt2 (d + 1))),
+ * D(i) = {d in [-h, h - 1] : i + d even} (the absolute pairs (2q, 2q + 1)
+ * inside the window), W indexed by d + h.  A parameter vector is
+ * float[Q + 4] = [W[0 .. Q-1], wv1, wv2, wt1, wt2]; W = -1, wv = (1, 1),
+ * wt = (1/2, 1/2) is the analytic N = 2 network (wmc_kernel_eval_n2).
+ * Loss of an example: mean over cells i and columns j = 1 .. h - 1 of
+ * (y - t)^2; one SGD step per example, p <- p - lr dL/dp.
+ *   V      [dev] float[n_examples][n_x] potentials (eV).
+ *   VW     [dev] float[n_examples][n_x][Q/2] their exact kernels in 1/s, half
+ *          period (columns j = 0 .. h - 1, e.g. from wmc_kernel_eval_rows).
+ *   order  [dev] int32[epochs][n_examples]: the examples of each epoch in turn.
+ *   lr     [dev] float[n_runs]: runs train the same examples in the same order,
+ *          one learning rate each (one thread block per run).
+ *   params [dev] float[n_runs][Q + 4]: initial weights in, trained weights out.
+ *   loss   [dev] float[n_runs][epochs] or NULL: mean loss of each epoch (each
+ *          step's loss taken before its update).
+ * n_x even; WMC_ERR_UNSUPPORTED if n_x (Q/2 + 1) + Q^2 floats exceed the shared
+ * memory of one block (about 200 KB).  Deterministic for given inputs. */
+wmc_status wmc_n2_train(const wmc_params* p, int32_t n_examples, const float* V, const float* VW, int32_t epochs,
+                        const int32_t* order, int32_t n_runs, const float* lr, float* params, float* loss,
+                        wmc_stream_t stream);
+
+/* Rows of the trained N = 2 network in 1/s for parameters params [dev]
+ * float[Q + 4] (layout as wmc_n2_train): V [dev] float[n_pot][n_x];
+ * VWh [dev] float[n_pot n_x][Q/2], row b n_x + i = cell i of potential b, half
+ * period.  The rows can drive the simulation through wmc_kernel_table_occupied. */
+wmc_status wmc_n2_eval(const wmc_params* p, const float* params, const float* V, int32_t n_pot, float* VWh,
+                       wmc_stream_t stream);
+
 /* gamma and the momentum CDF of kernel rows -- Eq. (momentum_integral) and the
  * postulate's draw of p' with probability V_W^+ / gamma.  The positive parts
  * x_k = max(V_W(k), 0) of a row are quantised relative to the row maximum:

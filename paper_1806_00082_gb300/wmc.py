@@ -35,6 +35,8 @@ EXPORTS = (
     "wmc_kernel_eval_rows", "wmc_kernel_vjp", "wmc_check_wait", "wmc_step_timing", "wmc_step_timing_read",
     "wmc_get_error", "wmc_philox_throughput", "wmc_kernel_eval_n2", "wmc_set_id_base",
     "wmc_kernel_eval_dft",
+    "wmc_n2_train",
+    "wmc_n2_eval",
 )
 
 
@@ -143,6 +145,8 @@ def load(path: str | None = None):
             "wmc_kernel_eval_n2": ([pp, vp, vp, i32, i32, vp, vp, vp], i32),
             "wmc_set_id_base": ([pp, vp, ctypes.c_uint64, vp], i32),
             "wmc_kernel_eval_dft": ([pp, vp, vp, vp, vp], i32),
+            "wmc_n2_train": ([pp, i32, vp, vp, i32, vp, i32, vp, vp, vp, vp], i32),
+            "wmc_n2_eval": ([pp, vp, vp, i32, vp, vp], i32),
             "wmc_get_error": ([pp, vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_char_p, ctypes.c_size_t], i32),
             "wmc_philox_throughput": ([u32, u32, i32, vp, i64, vp], i32),
         }
@@ -270,6 +274,25 @@ def kernel_eval_dft(p: Params, V: torch.Tensor, ws: torch.Tensor, out: torch.Ten
         out = torch.empty((p.n_x, p.h), dtype=torch.float32, device=V.device)
     _check("wmc_kernel_eval_dft", load().wmc_kernel_eval_dft(ctypes.byref(p), _ptr(V), _ptr(out), _ptr(ws),
                                                              _stream()))
+    return out
+
+
+def n2_train(p: Params, V: torch.Tensor, VW: torch.Tensor, order: torch.Tensor, lr: torch.Tensor,
+             params: torch.Tensor, loss: torch.Tensor | None = None) -> None:
+    """wmc_n2_train: SGD of the trained N = 2 network; params [n_runs, Q + 4] updated in place."""
+    n_ex, epochs, n_runs = V.shape[0], order.shape[0], lr.numel()
+    _check("wmc_n2_train", load().wmc_n2_train(ctypes.byref(p), n_ex, _ptr(V), _ptr(VW), epochs, _ptr(order),
+                                               n_runs, _ptr(lr), _ptr(params),
+                                               _ptr(loss) if loss is not None else None, _stream()))
+
+
+def n2_eval(p: Params, params: torch.Tensor, V: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """wmc_n2_eval: rows [n_pot * n_x, Q/2] of the trained N = 2 network in 1/s."""
+    V2 = V.reshape(-1, p.n_x)
+    if out is None:
+        out = torch.empty((V2.shape[0] * p.n_x, p.h), dtype=torch.float32, device=V.device)
+    _check("wmc_n2_eval", load().wmc_n2_eval(ctypes.byref(p), _ptr(params), _ptr(V2), V2.shape[0], _ptr(out),
+                                             _stream()))
     return out
 
 
