@@ -74,8 +74,10 @@ struct DevHeader {
   unsigned int pairs_done;   // pair-kernel blocks finished (the last one resets the queue and the ticket)
   unsigned int plan_epoch;   // launches of the plan so far (tags its blocks' published prefixes)
   unsigned int plan_ticket;  // logical block index of the running plan launch (reset by its last block)
-  unsigned int pad0;
+  unsigned int chunk;        // ids per work item of the current plan (0: kChunk)
   unsigned long long id_base;  // number of the first survivor (a sub-domain numbers after the cells before it)
+  unsigned int chunk_next;   // the plan's choice for the next step (the pair kernel makes it current)
+  unsigned int pad1;
 };
 
 // Totals of a run of cells in the plan's scan: survivors (64 bits), work
@@ -219,8 +221,16 @@ __device__ __forceinline__ uint4 philox4x32_10k(uint4 c, const PhiloxKeys& K) {
 
 // Work items of a cell holding t survivors (an upper bound when its first id
 // is not a multiple of 4; surplus items are empty).
-__host__ __device__ __forceinline__ int items_of_cell(unsigned long long t) {
-  return t ? (int)((t + 3 + kChunk - 1) / kChunk) : 0;
+__host__ __device__ __forceinline__ int items_of_cell(unsigned long long t, unsigned int chunk = kChunk) {
+  return t ? (int)((t + 3 + chunk - 1) / chunk) : 0;
+}
+
+// Ids per work item: the header's current choice (kChunk until a step has
+// chosen); a power of two in [kMinChunk, kChunk].
+constexpr unsigned int kMinChunk = 512;
+__device__ __forceinline__ unsigned int work_chunk(const DevHeader* hdr) {
+  const unsigned int c = *(const volatile unsigned int*)&hdr->chunk;
+  return c ? c : (unsigned int)kChunk;
 }
 
 // ---------------------------------------------------------------- launchers

@@ -96,7 +96,7 @@ __global__ __launch_bounds__(kPlanCells) void k_plan(int n_x, const unsigned lon
                                                      int* __restrict__ occ, int* __restrict__ row_map,
                                                      int2* __restrict__ items, long long max_items,
                                                      unsigned long long* __restrict__ thr_cell, DevHeader* hdr,
-                                                     PlanStatus* st, int advance_step, int clear_thr) {
+                                                     PlanStatus* st, int advance_step, int clear_thr, int step_warps) {
   __shared__ PlanSums w_s[kPlanCells / 32];
   __shared__ PlanSums s_ex;
   __shared__ int s_blk;
@@ -111,9 +111,10 @@ __global__ __launch_bounds__(kPlanCells) void k_plan(int n_x, const unsigned lon
   const unsigned int epoch = s_epoch;
   const int i = blk * kPlanCells + tid;
   const unsigned long long t = i < n_x ? __ldg(T + i) : 0ull;
+  const unsigned int chunk = work_chunk(hdr);  // (changed only after the step, by the pair kernel)
   PlanSums mine;
   mine.T = t;
-  mine.I = items_of_cell(t);
+  mine.I = items_of_cell(t, chunk);
   mine.N = i < n_x ? cell_needs_kernel(reach, i, n_x) : 0;
   mine.big = t > 0x7fffffffull;
   mine.pad = 0;
@@ -232,6 +233,15 @@ __global__ __launch_bounds__(kPlanCells) void k_plan(int n_x, const unsigned lon
     hdr->n_occ = tot.N;
     if (!ok) atomicOr(&hdr->flags, WMC_FLAG_CAPACITY);
     if (advance_step) hdr->step += 1u;
+    // items for the next step: about four per step warp at this population,
+    // at least kMinChunk ids, at most kChunk (work distribution only: results
+    // do not depend on it)
+    {
+      const unsigned long long per = tot.T / (4ull * (unsigned long long)(step_warps > 0 ? step_warps : 1));
+      unsigned int c = kMinChunk;
+      while (c < per && c < (unsigned int)kChunk) c <<= 1;
+      hdr->chunk_next = c;
+    }
     hdr->plan_ticket = 0u;
     hdr->plan_epoch = (epoch + 1u) & 0x3fffffffu;
     __threadfence();
@@ -311,7 +321,8 @@ cudaError_t launch_rows(const wmc_params& p, const View& v, const int32_t* hist,
 cudaError_t launch_plan_scan(const wmc_params& p, const View& v, int advance_step, int clear_thr, cudaStream_t s) {
   const int blocks = (p.n_x + kPlanCells - 1) / kPlanCells;
   k_plan<<<blocks, kPlanCells, 0, s>>>(p.n_x, v.T, v.reach, v.R, v.IP, v.occ, v.row_map, v.items,
-                                       layout(p).max_items, v.thr_cell, v.hdr, v.plan, advance_step, clear_thr);
+                                       layout(p).max_items, v.thr_cell, v.hdr, v.plan, advance_step, clear_thr,
+                                       step_grid(p.n_M) * kStepWarps);
   return cudaGetLastError();
 }
 

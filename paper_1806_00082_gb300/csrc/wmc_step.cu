@@ -165,6 +165,7 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
   const int rows_by_cell = (int)a.hdr->rows_by_cell;
   const uint32_t t = a.t_from_device ? a.hdr->step : a.t;
   const int n_items = a.hdr->n_items;
+  const unsigned int chunk = work_chunk(a.hdr);
   // move test of column k: moves iff (w ^ flip) > thr, i.e. w > xhi (rightward
   // drift), w < xlo (leftward, by complementing), never (thr = 2^32 - 1)
   for (int k = tid; k < n_M; k += kStepThreads) {
@@ -256,8 +257,8 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
     // lane takes a quad-aligned span of it
     const unsigned long long A = base & ~3u;
     const unsigned long long row_end = (unsigned long long)base + Ti;
-    const unsigned long long item0 = A + (unsigned long long)ch * kChunk;
-    const unsigned long long item1 = item0 + kChunk < row_end ? item0 + kChunk : row_end;
+    const unsigned long long item0 = A + (unsigned long long)ch * chunk;
+    const unsigned long long item1 = item0 + chunk < row_end ? item0 + chunk : row_end;
     const uint32_t len = item1 > item0 ? (uint32_t)(item1 - item0) : 0u;
     const uint32_t span = ((len + 127u) >> 7) << 2;
     const unsigned long long lo64 = item0 + (unsigned long long)lane * span;
@@ -411,6 +412,7 @@ __global__ __launch_bounds__(kStepThreads) void k_pairs(StepArgs a) {
     if (atomicAdd(&a.hdr->pairs_done, 1u) == gridDim.x - 1u) {
       a.hdr->pair_count = 0u;
       a.hdr->item_ticket = 0u;
+      a.hdr->chunk = a.hdr->chunk_next ? a.hdr->chunk_next : (unsigned int)kChunk;
       a.hdr->pairs_done = 0u;
       __threadfence();
     }
@@ -558,8 +560,8 @@ __global__ __launch_bounds__(kStepThreads) void k_materialize(const int32_t* __r
     __syncthreads();
     const int Ti = s_pre[n_M];
     const uint32_t base = (uint32_t)__ldg(R + i);
-    constexpr int kPer = kChunk / kStepThreads;
-    const int lo = chunk * kChunk + tid * kPer;  // ids [chunk kChunk, (chunk + 1) kChunk) of the row
+    const int per_item = (int)work_chunk(hdr), kPer = per_item / kStepThreads;
+    const int lo = chunk * per_item + tid * kPer;  // ids [chunk c, (chunk + 1) c) of the row, c ids per item
     const int hi = min(lo + kPer, Ti);
     if (lo < hi) {
       int k = bucket_of(s_pre, n_M, lo);
