@@ -26,6 +26,9 @@
 namespace wmc {
 
 constexpr int kPairQ = 256;  // per-warp event queue (one quad iteration adds at most 128)
+// a queue entry packs the id's offset in its item (13 bits), the column (12),
+// the event cell relative to i - 1 (2) and the sign (1)
+static_assert(kChunk <= 8192, "item offsets take 13 bits of a queue entry");
 
 struct StepArgs {
   const int32_t* hist_in;
@@ -187,7 +190,9 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
   uint32_t base = 0u;
   bool need_gen = false, any_full = false;
   uint32_t rej = 0u;
-  unsigned long long thr_st = 0ull;  // event threshold of a stayer: thr(i)
+  // event threshold of a stayer, thr(i), as u < thr <=> u < min(thr, 2^32 - 1) or thr >= 2^32
+  uint32_t thr_st32 = 0u;
+  bool all_st = false;
 
   int item = 0;
   if (lane == 0) item = (int)atomicAdd(&a.hdr->item_ticket, 1u);
@@ -241,7 +246,8 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
         s_thr[wid][2] = thr_p;
       }
       need_gen = (thr_m | thr_0 | thr_p) != 0ull;
-      thr_st = thr_0;
+      all_st = (thr_0 >> 32) != 0ull;
+      thr_st32 = all_st ? 0xffffffffu : (uint32_t)thr_0;
       // events: a stayer tests thr(i), a mover thr(i +- 1) (0 outside the
       // domain: absorbed particles create no pair); rej = the largest of them
       // as a quick rejection of a whole quad (exact unless a threshold is 2^32)
@@ -272,7 +278,8 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
     // bucket state
     int k = 0, sgn = 1, dir = 0;
     uint32_t end = 0u, flip = 0u, mthr = 0xffffffffu;
-    unsigned long long thr_mv = 0ull;  // event threshold of a mover: thr(i + dir)
+    uint32_t thr_mv32 = 0u;  // event threshold of a mover, thr(i + dir), in the same form
+    bool all_mv = false;
     int n_st = 0, n_mv = 0;
     auto load_bucket = [&]() {
       end = base + (uint32_t)P(k + 1);
@@ -281,7 +288,9 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
       flip = xm.x;
       mthr = xm.y;
       dir = flip ? -1 : (mthr != 0xffffffffu ? 1 : 0);
-      thr_mv = s_thr[wid][dir + 1];
+      const unsigned long long thr_mv = s_thr[wid][dir + 1];
+      all_mv = (thr_mv >> 32) != 0ull;
+      thr_mv32 = all_mv ? 0xffffffffu : (uint32_t)thr_mv;
     };
     auto flush_bucket = [&]() {
       if (n_st) atomicAdd(out_i + k, sgn > 0 ? n_st : -n_st);
@@ -298,11 +307,10 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
     };
     // pair event of particle id (mover or not) of the current bucket
     auto test_event = [&](uint32_t id, uint32_t u, int mv) {
-      const unsigned long long thr = mv ? thr_mv : thr_st;
-      if ((unsigned long long)u < thr) {
+      if (u < (mv ? thr_mv32 : thr_st32) || (mv ? all_mv : all_st)) {
         const int pos = atomicAdd(&s_qn[wid], 1);
         if (pos < kPairQ)  // always (the queue is drained whenever it could fill within one quad iteration)
-          s_q[pos] = (id - i0) | ((uint32_t)k << 12) | ((uint32_t)(mv ? dir + 1 : 1) << 24) | (sgn < 0 ? 1u << 26 : 0u);
+          s_q[pos] = (id - i0) | ((uint32_t)k << 13) | ((uint32_t)(mv ? dir + 1 : 1) << 25) | (sgn < 0 ? 1u << 27 : 0u);
       }
     };
     // queued events of this item to the global queue (warp-collective)
@@ -315,9 +323,9 @@ __global__ __launch_bounds__(kStepThreads, 4) void k_step(StepArgs a) {
         qb = __shfl_sync(0xffffffffu, qb, 0);
         for (int e = lane; e < n; e += 32) {
           const uint32_t q = s_q[e];
-          const uint32_t id = i0 + (q & 4095u);
-          const int kk = (int)((q >> 12) & 4095u), c = i - 1 + (int)((q >> 24) & 3u);
-          const int sg = (q >> 26) & 1u ? -1 : 1;
+          const uint32_t id = i0 + (q & 8191u);
+          const int kk = (int)((q >> 13) & 4095u), c = i - 1 + (int)((q >> 25) & 3u);
+          const int sg = (q >> 27) & 1u ? -1 : 1;
           const unsigned slot = qb + (unsigned)e;
           if (slot >= qb && slot < a.pair_cap)
             a.pairs[slot] = make_uint4(id, (uint32_t)c, (uint32_t)kk, sg < 0 ? 1u : 0u);
