@@ -531,7 +531,7 @@ struct BatchStepArgs {
 // so a sparse item touches only the buckets it holds.
 constexpr int kBStepWarps = 8;
 
-__global__ __launch_bounds__(kBStepWarps * 32, 3) void k_b_step(BatchStepArgs a) {
+__global__ __launch_bounds__(kBStepWarps * 32, 4) void k_b_step(BatchStepArgs a) {
   extern __shared__ int smem[];
   const int NM = a.NM;
   const int tid = threadIdx.x, lane = tid & 31;
