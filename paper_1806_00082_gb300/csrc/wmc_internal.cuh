@@ -42,7 +42,7 @@ constexpr uint32_t kPurposePick = 3u;
 // of at most kChunk / 32 consecutive ids.
 constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
-constexpr int kChunk = 4096;
+constexpr int kChunk = 2048;
 constexpr int kMaxStepBlocks = 8192;
 constexpr long long kMaxItemsBase = 1ll << 20;   // item descriptors: 2^32 / kChunk + n_x
 // Lane blocks of the coarse momentum CDF: a row's n_M columns are cut into 32
