@@ -327,7 +327,7 @@ wmc_status wmc_kernel_cdf(const wmc_params* p, const float* VWh, int32_t n_rows,
  * ------------------------------------------------------------------------- */
 
 /* Rule 2 rebuild: enumerates the survivors of the net histogram hist [dev]
- * int32[n_x][n_M] (row-major ids, work items of at most 4096 ids of one cell), marks the
+ * int32[n_x][n_M] (row-major ids, work items of 512 to 2048 ids of one cell, sized from the previous population), marks the
  * cells the next drift can reach (occupied cells and their neighbour in each
  * drift direction present) as the occupied list for the kernel, and, if
  * rho [dev] int64[n_x] is not NULL, writes the density (rule 1) of hist.
