@@ -67,6 +67,10 @@ class Clocks:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # live before the work starts: wait (at most 3 s) for the first sample
+            t_end = time.time() + 3.0
+            while not self.lines and time.time() < t_end:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
         return self
@@ -203,16 +207,19 @@ def native_arm(args, w):
     with torch.cuda.stream(stream):
         wmc.init(p, ws)
         t = 1
-        for _ in range(max(1, (args.warmup + 1) // 2)):
-            wmc.run(p, V, a, b, t, 2, ws)
-            t += 2
-        wmc.reset_counters(p, ws)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_iter)]
-        stream.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        with Clocks(local) as clk:
+        # clocks sampled from the warm-up steps through the timed region (at 20
+        # steps the timed region alone is shorter than one sampling interval)
+        clk = Clocks(local).__enter__()
+        try:
+            for _ in range(max(1, (args.warmup + 1) // 2)):
+                wmc.run(p, V, a, b, t, 2, ws)
+                t += 2
+            wmc.reset_counters(p, ws)
+            stream.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
             for q in range(n_iter):
                 flush.zero_()                    # L2 flushed between timed iterations
                 ev[q][0].record(stream)
@@ -220,6 +227,8 @@ def native_arm(args, w):
                 ev[q][1].record(stream)
                 t += 2
             stream.synchronize()
+        finally:
+            clk.__exit__(None, None, None)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
