@@ -183,32 +183,30 @@ __device__ __forceinline__ unsigned long long event_threshold(double g, double d
 }
 
 // Loads the signed counts of cell i into s_n and the exclusive prefix of |n|
-// into s_pre[0..n_M] (s_pre[n_M] = survivors of the cell), by one warp (lane l
-// takes the contiguous columns [l E, (l+1) E)).
+// into s_pre[0..n_M] (s_pre[n_M] = survivors of the cell), by one warp: 32
+// columns at a time (lane l takes column k0 + l, so the loads coalesce and the
+// shared-memory stores hit distinct banks), a warp scan per chunk and a carry.
 __device__ __forceinline__ void warp_row_prefix(const int32_t* __restrict__ hist, int i, int n_M, int* s_n,
                                                 int* s_pre, int lane) {
-  const int E = (n_M + 31) >> 5;
-  const int k0 = min(lane * E, n_M), k1 = min(k0 + E, n_M);
   const int32_t* row = hist + (size_t)i * n_M;
-  int local = 0;
-  for (int k = k0; k < k1; ++k) {
-    const int n = __ldg(row + k);
-    s_n[k] = n;
-    local += n < 0 ? -n : n;
-  }
-  int incl = local;
+  int carry = 0;
+  for (int k0 = 0; k0 < n_M; k0 += 32) {
+    const int k = k0 + lane;
+    const int n = k < n_M ? __ldg(row + k) : 0;
+    const int v = n < 0 ? -n : n;
+    int incl = v;
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += u;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += u;
+    }
+    if (k < n_M) {
+      s_n[k] = n;
+      s_pre[k] = carry + incl - v;
+    }
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
-  int excl = incl - local;
-  for (int k = k0; k < k1; ++k) {
-    s_pre[k] = excl;
-    const int n = s_n[k];
-    excl += n < 0 ? -n : n;
-  }
-  if (lane == 31) s_pre[n_M] = incl;
+  if (lane == 0) s_pre[n_M] = carry;
 }
 
 // Cell i needs its kernel row this step: occupied, or a neighbour drifts into
