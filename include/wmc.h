@@ -8,8 +8,9 @@
  * caller allocates every buffer and keeps ownership; the library allocates no
  * device memory on any call below.  Every call is asynchronous on the given
  * stream unless it says it synchronises.  Argument errors are returned at once;
- * conditions found on the device (population too large, gamma dt >= 1) set
- * flags in the workspace that wmc_get_counters() reads.
+ * conditions found on the device (population too large, gamma dt >= 1, a
+ * bounded wait that gave up) set flags in the workspace that wmc_get_error()
+ * turns into a status and wmc_get_counters() reports.
  *
  * Notation (Sec. 2 of the paper):
  *   cells i = 0 .. n_x-1 of width dx, centre (i + 1/2) dx;
@@ -40,6 +41,13 @@
  * grid are dropped (or wrapped).  Counts of parents and children in each
  * (cell, M) are summed with their signs: that sum is the annihilated state of
  * step t.
+ * Calls and the method's objects: the particles of the postulate are the
+ * histogram's survivors (wmc_materialize lists them: cell, offset, momentum,
+ * sign); the kernel of the occupied cells is wmc_kernel_eval (rows) with
+ * wmc_kernel_cdf (their CDF and gamma), or both at once into the workspace
+ * with wmc_kernel_eval_occupied; wmc_annihilate enumerates the survivors and
+ * the occupied cells, wmc_step advances them one step, wmc_density sums them
+ * per cell, wmc_run chains the whole step.
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key (seed_lo, seed_hi).
  * Particle id takes word id % 4 of counter (id / 4, step, purpose, sim): the
  * offset with purpose REPOS = 2, u24(w) = (w >> 8) 2^-24, at the step that
