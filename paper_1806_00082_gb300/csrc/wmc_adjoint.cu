@@ -185,7 +185,7 @@ cudaError_t launch_kernel_vjp(const wmc_params& p, int n_pot, const float* VWh, 
   if (e != cudaSuccess) return e;
   const int tiles = (p.n_x + kVbarTile - 1) / kVbarTile;
   const size_t vsm = sizeof(float) * (size_t)kVbarChunk * h;
-  if (vsm > 48 * 1024) cudaFuncSetAttribute(k_adj_vbar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+  if (vsm > 48 * 1024) raise_smem_limit(reinterpret_cast<const void*>(k_adj_vbar), vsm);
   k_adj_vbar<<<(unsigned)((long long)tiles * n_pot), kVbarTile, vsm, s>>>(p.Q, p.n_x, n_pot, Abar, Vbar);
   return cudaGetLastError();
 }

@@ -206,6 +206,40 @@ static unsigned long long current_context_id() {
   return 0;
 }
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`, calling
+// the runtime only when the limit set before in this context is lower: the
+// attribute persists, and a runtime call in front of every launch would sit
+// between a caller's start event and the kernel.
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long ctx = current_context_id();
+  struct Entry {
+    const void* f;
+    int dev;
+    unsigned long long ctx;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static Entry table[256];
+  static int n = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  int slot = -1;
+  for (int q = 0; q < n; ++q)
+    if (table[q].f == func && table[q].dev == dev) {
+      if (table[q].ctx == ctx && table[q].bytes >= bytes) return cudaSuccess;
+      slot = q;
+      break;
+    }
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  if (slot < 0 && n < 256) slot = n++;
+  if (slot >= 0) table[slot] = Entry{func, dev, ctx, bytes};
+  return cudaSuccess;
+}
+
 // A second stream per device and a fork/join event pair, for running the
 // single-block plan beside the kernel stage.
 struct AuxStream {

@@ -714,7 +714,7 @@ size_t b_step_smem(int NM) { return sizeof(int) * (size_t)kBStepWarps * (2 * NM 
 int b_step_grid(int NM) {
   int per_sm = 0;
   const size_t sm = b_step_smem(NM);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_b_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (sm > 48 * 1024) raise_smem_limit(reinterpret_cast<const void*>(k_b_step), sm);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_step, kBStepWarps * 32, sm);
   if (per_sm < 1) per_sm = 1;
   return per_sm * num_sms();

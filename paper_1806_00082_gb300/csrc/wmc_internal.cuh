@@ -290,6 +290,9 @@ cudaError_t launch_philox_throughput(uint32_t k0, uint32_t k1, int pairs_per_thr
                                      cudaStream_t s);
 
 int num_sms();
+// Raises a kernel's dynamic shared-memory limit (kept per kernel, device and
+// context; the runtime is called only when the limit has to grow).
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
 // Optional CUDA events around the particle-step kernel (wmc_step_timing): records
 // the begin (end = false) or end event of the current device on s, as an
 // event-record node when s is being captured.  No-op while timing is off.

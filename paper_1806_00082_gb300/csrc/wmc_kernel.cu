@@ -508,7 +508,7 @@ cudaError_t launch_kernel_rows_small(const wmc_params& p, const float* V, const 
 #define WMC_LAUNCH_ROWS_NET(CC, RR, NN)                                                                           \
   do {                                                                                                            \
     if (sm > 48 * 1024)                                                                                           \
-      cudaFuncSetAttribute(k_kernel_rows_small<CC, RR, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);\
+      raise_smem_limit(reinterpret_cast<const void*>(k_kernel_rows_small<CC, RR, NN>), sm);                   \
     k_kernel_rows_small<CC, RR, NN><<<blocks, kRowWarps * 32, sm, s>>>(                                           \
         V, p.n_x, p.bc_potential, p.Q, p.n_M, lg, occ, n_occ_dev, n_occ_host, B, L.Np, c, VWh, ccdf, scale,       \
         gamma, gthr, thr_cell, flags, p.dt_s, reach, hdr);                                                        \
@@ -555,7 +555,7 @@ cudaError_t launch_cdf(const wmc_params& p, const float* VWh, const int* n_rows_
   }
   const size_t sm = sizeof(float) * (size_t)kCdfWarps * (size_t)(p.Q / 2 + p.Q / 64 + 1);
   if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_cdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(k_cdf), sm);
     if (e != cudaSuccess) return e;
   }
   k_cdf<<<(max_rows + kCdfWarps - 1) / kCdfWarps, kCdfWarps * 32, sm, s>>>(
@@ -635,7 +635,7 @@ cudaError_t launch_kernel_dft(const wmc_params& p, const float* V, double* CS, f
   const long long threads = (long long)h * ((p.n_x + kDftSeg - 1) / kDftSeg);
   const size_t sm = sizeof(double) * 2 * (size_t)p.Q;
   if (sm > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(k_kernel_dft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(k_kernel_dft), sm);
     if (e != cudaSuccess) return e;
   }
   const double c = -2.0 / (kHbarEVs * (double)p.Q);

@@ -1316,8 +1316,7 @@ cudaError_t launch_adjoint_abar_tc(const wmc_params& p, int rows, const float* V
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   const size_t sm = ws_split_smem_bytes(g.KBa, g_h(p), true);
   const dim3 grid((rows + TM - 1) / TM, g.NT);
-  cudaError_t e = cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(k_kernel_eval_tc_ws_split<true, 3>), sm);
   if (e != cudaSuccess) return e;
   k_kernel_eval_tc_ws_split<true, 3><<<grid, kWsThreads, sm, s>>>(nullptr, rows, 0, p.Q, nullptr, nullptr, rows, ba,
                                                                   ba + g.bytes_per_imagea, g.KBa, c, Abar, flags, d);
@@ -1368,24 +1367,24 @@ cudaError_t launch_kernel_eval_tc(const wmc_params& p, int prec, const float* V,
   dim3 grid((max_rows + TM - 1) / TM, g.NT);
   if (prec == WMC_BF16) {
     const size_t sm = tc_smem_bytes(false, g_h(p));
-    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit(reinterpret_cast<const void*>(k_kernel_eval_tc<WMC_BF16>), sm);
     k_kernel_eval_tc<WMC_BF16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
                                                      base, nullptr, g.KB, c, VWh, flags);
   } else if (prec == WMC_FP16) {
     const size_t sm = tc_smem_bytes(false, g_h(p));
-    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit(reinterpret_cast<const void*>(k_kernel_eval_tc<WMC_FP16>), sm);
     k_kernel_eval_tc<WMC_FP16><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev, n_occ_host,
                                                      base + n16, nullptr, g.KB, c, VWh, flags);
   } else if (prec == WMC_TF32X3 && ws_split_smem_bytes(g.KB32, g_h(p), true) <= 226 * 1024) {
     const size_t sm = ws_split_smem_bytes(g.KB32, g_h(p), true);
     const uint8_t* b32 = reinterpret_cast<const uint8_t*>(images) + 3 * g.bytes_per_image;
-    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit(reinterpret_cast<const void*>(k_kernel_eval_tc_ws_split<true, 1>), sm);
     k_kernel_eval_tc_ws_split<true, 1><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
                                                                  n_occ_host, b32, b32 + g.bytes_per_image32,
                                                                  g.KB32, c, VWh, flags, DenseA{});
   } else if (prec == WMC_FP16_SPLIT) {
     const size_t sm = tc_smem_bytes(true, g_h(p));
-    cudaFuncSetAttribute(k_kernel_eval_tc<WMC_FP16_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit(reinterpret_cast<const void*>(k_kernel_eval_tc<WMC_FP16_SPLIT>), sm);
     k_kernel_eval_tc<WMC_FP16_SPLIT><<<grid, 128, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
                                                            n_occ_host, base + n16, base + 2 * n16, g.KB, c, VWh,
                                                            flags);
@@ -1424,8 +1423,7 @@ static cudaError_t launch_tc_net(const wmc_params& p, int prec, const float* V, 
     const dim3 ws_grid(row_tiles, n_split);
 #define WMC_LAUNCH_WS(PR, TW)                                                                                    \
   do {                                                                                                           \
-    cudaFuncSetAttribute(k_kernel_eval_tc_ws<PR, TW, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                         (int)ws_sm);                                                                            \
+    raise_smem_limit(reinterpret_cast<const void*>(k_kernel_eval_tc_ws<PR, TW, NET>), ws_sm);                   \
     k_kernel_eval_tc_ws<PR, TW, NET><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ,      \
                                                                         n_occ_dev, n_occ_host, img, KB, g.NT,    \
                                                                         n_split, c, VWh, flags);                 \
@@ -1443,7 +1441,7 @@ static cudaError_t launch_tc_net(const wmc_params& p, int prec, const float* V, 
   if (prec == WMC_FP16_SPLIT && ws_split_smem_bytes(KB, g_h(p)) <= 226 * 1024) {
     const size_t sm = ws_split_smem_bytes(KB, g_h(p));
     const dim3 grid(row_tiles, g.NT);
-    cudaFuncSetAttribute(k_kernel_eval_tc_ws_split<false, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit(reinterpret_cast<const void*>(k_kernel_eval_tc_ws_split<false, NET>), sm);
     k_kernel_eval_tc_ws_split<false, NET><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ,
                                                                        n_occ_dev, n_occ_host, base + n16,
                                                                        base + 2 * n16, KB, c, VWh, flags, DenseA{});

@@ -222,7 +222,7 @@ wmc_status wmc_n2_train(const wmc_params* p, int32_t n_examples, const float* V,
   if (sm > 200 * 1024) return WMC_ERR_UNSUPPORTED;
   if (n_runs == 0 || epochs == 0) return WMC_OK;
   if (sm > 48 * 1024 &&
-      cudaFuncSetAttribute(k_n2_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      raise_smem_limit(reinterpret_cast<const void*>(k_n2_train), sm) != cudaSuccess)
     return WMC_ERR_CUDA;
   const float scale = (float)(kHbarEVs * (double)p->Q / 2.0);
   k_n2_train<<<n_runs, kN2Threads, sm, (cudaStream_t)stream>>>(p->n_x, p->Q, p->bc_potential, n_examples, V, VW,
@@ -239,7 +239,7 @@ wmc_status wmc_n2_eval(const wmc_params* p, const float* params, const float* V,
   const size_t sm = sizeof(float) * ((size_t)p->Q * h + (size_t)(p->Q + 4));
   if (sm > 200 * 1024) return WMC_ERR_UNSUPPORTED;
   if (sm > 48 * 1024 &&
-      cudaFuncSetAttribute(k_n2_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      raise_smem_limit(reinterpret_cast<const void*>(k_n2_eval), sm) != cudaSuccess)
     return WMC_ERR_CUDA;
   long long blocks = (rows * h + 255) / 256;
   if (blocks > 8LL * num_sms()) blocks = 8LL * num_sms();

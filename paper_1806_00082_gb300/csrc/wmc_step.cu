@@ -436,7 +436,7 @@ int step_grid(int n_M) {
   if (cached_nM[slot] == n_M && cached_grid[slot] > 0) return cached_grid[slot];
   int per_sm = 0;
   const size_t sm = step_smem(n_M);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (sm > 48 * 1024) raise_smem_limit(reinterpret_cast<const void*>(k_step), sm);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, kStepThreads, sm);
   if (per_sm < 1) per_sm = 1;
   int g = per_sm * num_sms();
