@@ -55,21 +55,44 @@ def test_tensorcore_forms_vs_fp64(wmc, form, wl, n):
     assert wmc.get_counters(p, ws)["flags"] == 0
 
 
-def test_tensorcore_ragged_rows_and_tiles(wmc):
-    """Row counts around the 128-row tile and an empty list."""
+@pytest.mark.parametrize("form", ["fp16_split", "bf16", "fp16"])
+def test_tensorcore_ragged_rows_and_tiles(wmc, form):
+    """Row counts below, at and around the 128-row tile (1, 15, 17, 127-129,
+    300) and an empty list, for scattered and for consecutive cells (the
+    potential-window path of the builders, with a ragged last tile)."""
     wl = wi.DOUBLE_BARRIER_16384
     p = wmc.Params.of(wl)
     V = torch.from_numpy(wi.potential(wl)).cuda()
     ws = wmc.workspace(p)
     wmc.init(p, ws)
-    for n in (0, 1, 127, 128, 129, 300):
-        cells = (np.arange(n) * 37 + 8000) % wl.n_x
-        occ = torch.from_numpy(cells.astype(np.int32)).cuda()
-        out = torch.full((n, wl.Q // 2), 3.0, device="cuda")
-        wmc.kernel_eval(p, V, occ, ws, prec=wmc.FP16_SPLIT, out=out)
-        if n:
-            ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), wi.potential(wl), cells)[:, wl.Q // 2:]
-            assert normwise(out.cpu().numpy(), ref) <= TOL["fp16_split"]
+    for n in (0, 1, 15, 17, 127, 128, 129, 300):
+        for stride in (37, 1):
+            cells = (np.arange(n) * stride + 8000) % wl.n_x
+            occ = torch.from_numpy(cells.astype(np.int32)).cuda()
+            out = torch.full((n, wl.Q // 2), 3.0, device="cuda")
+            wmc.kernel_eval(p, V, occ, ws, prec=wmc.PRECISIONS[form], out=out)
+            if n:
+                ref = oracle.kernel_rows(oracle.params(wl.replace(n_M=wl.Q)), wi.potential(wl), cells)[:, wl.Q // 2:]
+                assert normwise(out.cpu().numpy(), ref) <= TOL[form], (form, n, stride)
+    assert wmc.get_counters(p, ws)["flags"] == 0
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16"])
+def test_tensorcore_consecutive_rows_window_not_multiple_of_4(wmc, form):
+    """Consecutive cells with h = Q/2 not a multiple of 4 (Q = n_M = 1020):
+    the potential window is staged but read element by element; the whole
+    domain (sampled) and a ragged run of 300 cells."""
+    wl = wi.DOUBLE_BARRIER_16384.replace(Q=1020, n_M=1020)
+    p = wmc.Params.of(wl)
+    V = wi.potential(wl)
+    ws = wmc.workspace(p)
+    wmc.init(p, ws)
+    for cells in (np.arange(wl.n_x, dtype=np.int32), np.arange(8000, 8300, dtype=np.int32)):
+        got = wmc.kernel_eval(p, torch.from_numpy(V).cuda(), torch.from_numpy(cells).cuda(), ws,
+                              prec=wmc.PRECISIONS[form]).cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert _sampled_err(got, wl, V, cells, 120, 3) <= TOL[form], (form, cells.size)
+    assert wmc.get_counters(p, ws)["flags"] == 0
 
 
 def test_tensorcore_in_production_loop(wmc):
