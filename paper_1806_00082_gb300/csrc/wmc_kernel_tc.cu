@@ -5,25 +5,24 @@
 //
 // The sine matrix S is precomputed once per workspace as operand images in
 // global memory (BF16, FP16 hi, FP16 lo, TF32 hi, TF32 lo) in 16 KB blocks of
-// 128 rows in the layout below; A is generated in shared memory from
-// the potential and never written to global memory.  Three kernels:
-//   - k_kernel_eval_tc_ws<BF16 | FP16, N>: warp-specialised (16 builder /
+// 128 rows in the layout below; A is generated on chip from the potential
+// and never written to global memory.  Three kernels:
+//   - k_kernel_eval_tc_ta<BF16 | FP16, N>: warp-specialised (16 builder /
 //     epilogue warps, one MMA-issuing thread, one bulk-copy thread), the whole
-//     A operand of a 128-row tile resident in shared memory, B streamed
-//     through a ring of stages, M = 128, N = 256 (128 for narrow windows),
-//     two TMEM accumulator buffers so that the epilogue of one column tile
-//     overlaps the MMAs of the next;
+//     A operand of a 128-row tile in tensor memory, B streamed through a deep
+//     ring of shared-memory stages, M = N = 128, two TMEM accumulator buffers
+//     so that the epilogue of one column tile overlaps the MMAs of the next
+//     (K <= 512);
 //   - k_kernel_eval_tc_ws_split<FP16 | TF32>: the hi/lo split forms, three MMAs
-//     per K step (hi x hi, hi x lo, lo x hi), A resident per K pass;
+//     per K step (hi x hi, hi x lo, lo x hi), A resident in shared memory per
+//     K pass, each K block's main product in its own accumulator;
 //   - k_kernel_eval_tc: a per-tile kernel with both operands streamed, for
-//     BF16 / FP16 windows whose A operand does not fit in shared memory.
-// Operands use the K-major 128-byte swizzled layout: rows of 128 bytes
-// (64 16-bit or 32 TF32 values), 8-row atoms 1024 bytes apart, the 16-byte
-// chunks of row r XOR-swizzled by r % 8; shared-memory blocks are aligned to
-// 1024 bytes.  Accumulation is FP32 in TMEM; the main product is split over
-// two K halves held in separate accumulators and the split forms' cross terms
-// go to a third; the epilogue reads them with tcgen05.ld and combines them in
-// FP32.
+//     BF16 / FP16 windows wider than the tensor-memory form holds.
+// Shared-memory operands use the K-major 128-byte swizzled layout: rows of
+// 128 bytes (64 16-bit or 32 TF32 values), 8-row atoms 1024 bytes apart, the
+// 16-byte chunks of row r XOR-swizzled by r % 8; shared-memory blocks are
+// aligned to 1024 bytes.  Accumulation is FP32 in TMEM; the epilogue reads
+// the accumulators with tcgen05.ld and combines and scales them in FP32.
 //
 // Every wait is bounded (about one second of SM clock); on a timeout the CTA
 // sets WMC_FLAG_TIMEOUT, stops issuing work, lets its copies and MMAs in
@@ -190,6 +189,32 @@ __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
                  "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
                :
                : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane from registers;
+// tmem_wait_st waits until this thread's stores are complete.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// kind::f16 MMA with the A operand in tensor memory: M = 128 rows in the 128
+// lanes, each 32-bit column holding two consecutive K values (the lower K in
+// the low half), K = 16 over 8 columns starting at a_tmem.
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
 
 __device__ __forceinline__ float potential_at(const float* __restrict__ V, int n_x, int bc, long long l) {
@@ -473,45 +498,16 @@ __global__ __launch_bounds__(128, 1) void k_kernel_eval_tc(const float* __restri
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
-// ---------------------------------------------------------------- warp-specialised form
-// BF16 / FP16: one CTA per 128 rows and a run of column tiles of TNW = 128 or
-// 256 columns (the MMA's N; 256 halves the A operand reads per flop and is
-// used for windows wider than 128).  The whole A operand (128 x Kp, 16-bit)
-// stays in shared memory, so it is built once and reused by every column tile
-// of the CTA.  A B stage holds TNW / 128 consecutive 128 x 64 operand images,
-// which in the core-matrix layout are one TNW x 64 operand.  Roles (576 threads):
-//   warps 0-15 build A (four rows and one core-matrix column of every other
-//              block each), signalling a_ready[kb]; then run the epilogue
-//              of each column tile from TMEM (warp w reads lane quadrant w % 4,
-//              32 columns at 32 (w / 4)), transposing each 32 x 16 piece
-//              through shared memory so that global stores are whole 64-byte
-//              row segments;
-//   warp 16    one thread issues the MMAs: tile j into the FP32 accumulator
-//              buffer j % 2, waiting for A blocks, B stages and a drained
-//              buffer, committing each B stage and each tile;
-//   warp 17    one thread streams the B operand images through a ring of 4
-//              (TNW 128) or 2 (TNW 256) stages,
-//              starting as soon as the barriers exist.
-// Synchronisation is by mbarriers and one named barrier among the builders;
-// every wait is bounded and an abort flag makes all roles drain to the final
-// barrier, after which TMEM is freed.
-constexpr int kWsStages = 4;
-constexpr int kWsMaxKB = 32;  // Q <= 4096
+// ---------------------------------------------------------------- warp-specialised forms
+// Roles of the warp-specialised kernels below (576 threads): warps 0-15 build
+// the A operand and then run the epilogue, warp 16 has one thread issue the
+// MMAs, warp 17 one thread stream the B operand images.  The epilogue warp w
+// reads TMEM lane quadrant w % 4 and transposes each 32 x 16 piece through
+// shared memory, so that global stores are whole 64-byte row segments.
 constexpr int kWsBuilders = 512;
 constexpr int kWsThreads = kWsBuilders + 64;
 
 constexpr int kWsStageFloats = 32 * 16;  // epilogue staging per warp: 32 rows x 16 columns
-
-// A blocks, B ring, then one region used first for the potential window
-// (TM + 2h floats, building A) and then for the epilogue staging.
-__host__ __device__ constexpr int ws_stages(int tnw) { return tnw == 256 ? 2 : kWsStages; }
-
-__host__ __device__ constexpr size_t ws_smem_bytes(int KB, int h, int tnw) {
-  return kSmemAlignPad + (size_t)KB * kTileBytes + (size_t)ws_stages(tnw) * (tnw / TN) * kTileBytes +
-         sizeof(float) * (size_t)((TM + 2 * h) > (kWsBuilders / 32) * kWsStageFloats
-                                      ? (TM + 2 * h)
-                                      : (kWsBuilders / 32) * kWsStageFloats);
-}
 
 // AND of pred over the kWsBuilders builder threads (named barrier 1).
 __device__ __forceinline__ bool builders_and(bool pred) {
@@ -540,27 +536,49 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
-template <int PREC, int TNW, int NET>
-__global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float* __restrict__ V, int n_x, int bc,
+// ---------------------------------------------------------------- A in tensor memory
+// BF16 / FP16, K <= 512: one CTA per 128 rows and a run of 128-column tiles.
+// The whole A operand of the row tile lives in tensor memory (up to 8 blocks
+// of 64 K values, 32 columns each, at columns 0 .. 255), built once and used
+// by every column tile; two 128-column FP32 accumulator buffers at columns
+// 256 and 384 let the epilogue of tile j overlap the MMAs of tile j + 1; the
+// shared memory holds a ring of 11 B stages (one 128-column x 64-K image
+// each), so the tensor core reads only B from shared memory and the ring
+// covers a copy round trip.  Builder warp w writes TMEM lanes 32 (w % 4) ..
+// + 31 (one row of the tile per thread) for the K blocks kb = w / 4 (mod 4):
+// its row's entries, packed in pairs, by tcgen05.st, then arrives on
+// a_ready[kb].  The MMA thread waits for a_ready (first tile), each B stage
+// and a drained accumulator buffer, commits each stage and each tile.  Every
+// wait is bounded; on a timeout an abort flag makes all roles drain to the
+// final barrier, after which TMEM is freed.
+constexpr int kTaStages = 11;
+constexpr int kTaMaxKB = 8;
+constexpr uint32_t kTaAccCol = 256;
+
+__host__ __device__ constexpr size_t ta_smem_bytes(int h) {
+  return kSmemAlignPad + (size_t)kTaStages * kTileBytes +
+         sizeof(float) * (size_t)((TM + 2 * h) > (kWsBuilders / 32) * kWsStageFloats
+                                      ? (TM + 2 * h)
+                                      : (kWsBuilders / 32) * kWsStageFloats);
+}
+
+template <int PREC, int NET>
+__global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ta(const float* __restrict__ V, int n_x, int bc,
                                                                      int Q, const int* __restrict__ occ,
                                                                      const int* __restrict__ n_occ_dev, int n_occ_host,
                                                                      const uint16_t* __restrict__ img_b, int KB,
                                                                      int NT, int n_split, float c,
                                                                      float* __restrict__ VWh,
                                                                      unsigned int* __restrict__ flags) {
-  constexpr uint32_t kind_fmt = PREC == WMC_BF16 ? 1u : 0u;
-  constexpr uint32_t idesc =
-      (1u << 4) | (kind_fmt << 7) | (kind_fmt << 10) | ((uint32_t)(TNW >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-  constexpr int STG = ws_stages(TNW);          // B stages
-  constexpr int IMG = TNW / TN;                // 128-column images per stage
-  constexpr uint32_t kStageBytes = IMG * kTileBytes;
+  constexpr uint32_t idesc = idesc_f16(PREC == WMC_BF16 ? 1u : 0u);  // M = N = 128
+  constexpr int STG = kTaStages;
+  constexpr uint32_t n_cols = 512;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = align_smem(smem_raw);
-  uint8_t* sA = smem;                                         // KB blocks of 128 x 64
-  uint8_t* sB = smem + (size_t)KB * kTileBytes;              // STG stages of TNW x 64
-  float* sV = reinterpret_cast<float*>(sB + (size_t)STG * kStageBytes);  // shared with the staging
-  __shared__ __align__(8) uint64_t a_ready[kWsMaxKB];
-  __shared__ __align__(8) uint64_t b_full[kWsStages], b_empty[kWsStages];
+  uint8_t* sB = smem;                                                     // STG stages of 128 x 64
+  float* sV = reinterpret_cast<float*>(sB + (size_t)STG * kTileBytes);  // window, then epilogue staging
+  __shared__ __align__(8) uint64_t a_ready[kTaMaxKB];
+  __shared__ __align__(8) uint64_t b_full[kTaStages], b_empty[kTaStages];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ __align__(8) uint64_t drain;
   __shared__ uint32_t tmem_slot;
@@ -571,17 +589,14 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
   const int h = Q / 2;
   if (row0 >= n_rows) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t n_cols = 2u * TNW;  // two accumulator buffers of TNW columns
-  // NT counts 128-column images; this CTA's TNW-column tiles are
-  // [nt_begin, nt_begin + n_my); local tile j = nt - nt_begin
-  const int NTW = (NT + IMG - 1) / IMG;
-  const int nt_begin = (int)(((long long)blockIdx.y * NTW) / n_split);
-  const int n_my = (int)(((long long)(blockIdx.y + 1) * NTW) / n_split) - nt_begin;
+  // this CTA's 128-column tiles: [nt_begin, nt_begin + n_my)
+  const int nt_begin = (int)(((long long)blockIdx.y * NT) / n_split);
+  const int n_my = (int)(((long long)(blockIdx.y + 1) * NT) / n_split) - nt_begin;
   const int n_tiles = n_my * KB;
 
   if (warp == 0) tmem_alloc(&tmem_slot, n_cols);
   if (tid == 0) {
-    for (int q = 0; q < KB; ++q) mbar_init(&a_ready[q], kWsBuilders);
+    for (int q = 0; q < KB; ++q) mbar_init(&a_ready[q], 4);  // one arrival per lane-quarter warp
     for (int q = 0; q < STG; ++q) {
       mbar_init(&b_full[q], 1);
       mbar_init(&b_empty[q], 1);
@@ -610,12 +625,10 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
           s_abort = 1;
           break;
         }
-        const int n0 = (nt_begin + t / KB) * IMG, kb = t % KB;
-        const int n_img = min(IMG, NT - n0);  // images past the window stay stale (columns >= h)
-        mbar_expect_tx(&b_full[st], (uint32_t)n_img * kTileBytes);
-        for (int u = 0; u < n_img; ++u)
-          bulk_g2s(sB + (size_t)st * kStageBytes + (size_t)u * kTileBytes,
-                   img_b + ((size_t)(n0 + u) * KB + kb) * (kTileBytes / 2), kTileBytes, &b_full[st]);
+        const int nt = nt_begin + t / KB, kb = t % KB;
+        mbar_expect_tx(&b_full[st], kTileBytes);
+        bulk_g2s(sB + (size_t)st * kTileBytes, img_b + ((size_t)nt * KB + kb) * (kTileBytes / 2), kTileBytes,
+                 &b_full[st]);
         issued = t + 1;
       }
       if (s_abort)  // let the copies still in flight land before the CTA exits (bounded)
@@ -633,7 +646,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
           break;
         }
         tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)(buf * TNW);
+        const uint32_t acc = tmem + kTaAccCol + (uint32_t)(buf * TN);
         for (int kb = 0; kb < KB; ++kb) {
           const int t = j * KB + kb, st = t % STG;
           if ((j == 0 && !mbar_wait(&a_ready[kb], 0u)) ||
@@ -643,13 +656,11 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
             break;
           }
           tc_fence_after();
-          const int first = kb == 0;
-          const uint32_t a_base = smem_u32(sA + (size_t)kb * kTileBytes);
-          const uint32_t b_base = smem_u32(sB + (size_t)st * kStageBytes);
+          const uint32_t b_base = smem_u32(sB + (size_t)st * kTileBytes);
 #pragma unroll
           for (int s4 = 0; s4 < TK / 16; ++s4)
-            mma_f16(acc, smem_desc(a_base + s4 * kKStepBytes), smem_desc(b_base + s4 * kKStepBytes), idesc,
-                    (first && s4 == 0) ? 0u : 1u);
+            mma_f16_ta(acc, tmem + (uint32_t)(kb * (TK / 2) + s4 * 8), smem_desc(b_base + s4 * kKStepBytes), idesc,
+                       (kb == 0 && s4 == 0) ? 0u : 1u);
           mma_commit(&b_empty[st]);
         }
         if (s_abort) break;
@@ -687,76 +698,52 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
       }
       builders_sync();
     }
-    // Build mapping: thread (rg, k8, par) fills rows 4 rg .. 4 rg + 3 of core-matrix
-    // column k8 in every block of parity par.  With contiguous rows the four rows
-    // share their potential windows: 12 + 12 values (three 16-byte loads each)
-    // serve 32 differences.  It arrives at once on the blocks of the other parity.
-    const int rg = tid & 31, k8 = (tid >> 5) & 7, par = tid >> 8;
-    for (int kb = 1 - par; kb < KB; kb += 2)
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kb])) : "memory");
-    int cell_d[4];
-    bool valid_d[4];
-    const float* V_d[4];
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const int row = row0 + 4 * rg + d;
-      valid_d[d] = row < n_rows;
-      cell_d[d] = (contig || !valid_d[d]) ? 0 : (occ ? __ldg(occ + row) : row % n_x);
-      V_d[d] = V + (size_t)((occ || !valid_d[d]) ? 0 : row / n_x) * n_x;
-    }
-    const bool fast = contig && (h & 3) == 0;
+    // this thread's row of the tile = its TMEM lane
+    const int quad = warp & 3, kp = warp >> 2;
+    const int rr = 32 * quad + lane;
+    const int row = row0 + rr;
+    const bool valid = row < n_rows;
+    const int cell = (contig || !valid) ? 0 : (occ ? __ldg(occ + row) : row % n_x);
+    const float* Vr = V + (size_t)((occ || !valid) ? 0 : row / n_x) * n_x;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
 #pragma unroll 1
-    for (int kb = par; kb < KB; kb += 2) {
-      uint8_t* blk = sA + (size_t)kb * kTileBytes;
-      const int m0 = kb * TK + k8 * 8 + 1;
-      float dv[4][8];
-      if (NET == 1 && fast && m0 + 7 <= h - 1) {
-        // P[j] = V at offset m0 - 1 + j right of row 4 rg, N[j] = V at offset m0 + 7 - j left of it
-        float P[12], N[12];
-        const float* pp = sV + 4 * rg + h + m0 - 1;
-        const float* pn = sV + 4 * rg + h - m0 - 7;
+    for (int kb = kp; kb < KB; kb += 4) {
+      uint32_t wv[32];
+      const int k0 = kb * TK;  // K index of the block's first value
+      if (NET == 1 && contig && k0 + TK <= h - 1) {
+        // m = k0 + 1 .. k0 + 64, all inside the sum: wp[m] = V(i + m), wp[-m] = V(i - m)
+        const float* wp = sV + rr + h;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const float4 a = *reinterpret_cast<const float4*>(pp + 4 * q);
-          const float4 b = *reinterpret_cast<const float4*>(pn + 4 * q);
-          P[4 * q] = a.x, P[4 * q + 1] = a.y, P[4 * q + 2] = a.z, P[4 * q + 3] = a.w;
-          N[4 * q] = b.x, N[4 * q + 1] = b.y, N[4 * q + 2] = b.z, N[4 * q + 3] = b.w;
+        for (int e = 0; e < 32; ++e) {
+          const int m = k0 + 2 * e + 1;
+          wv[e] = pack2<PREC>(__fsub_rn(wp[m], wp[-m]), __fsub_rn(wp[m + 1], wp[-m - 1]));
         }
-#pragma unroll
-        for (int d = 0; d < 4; ++d)
-#pragma unroll
-          for (int e = 0; e < 8; ++e) dv[d][e] = __fsub_rn(P[d + e + 1], N[d - e + 7]);
       } else {
 #pragma unroll
-        for (int d = 0; d < 4; ++d)
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int kk = m0 - 1 + e;
-            dv[d][e] = 0.f;
-            if (contig) dv[d][e] = a_entry_window<NET>(sV + 4 * rg + d, h, cell0 + 4 * rg + d, kk);
-            else if (valid_d[d]) dv[d][e] = a_term<NET>(V_d[d], n_x, bc, h, cell_d[d], kk);
+        for (int e = 0; e < 32; ++e) {
+          const int kk = k0 + 2 * e;
+          float a = 0.f, b = 0.f;
+          if (contig) {
+            a = a_entry_window<NET>(sV + rr, h, cell0 + rr, kk);
+            b = a_entry_window<NET>(sV + rr, h, cell0 + rr, kk + 1);
+          } else if (valid) {
+            a = a_term<NET>(Vr, n_x, bc, h, cell, kk);
+            b = a_term<NET>(Vr, n_x, bc, h, cell, kk + 1);
           }
+          wv[e] = pack2<PREC>(a, b);
+        }
       }
-      uint4 w[4];
-#pragma unroll
-      for (int d = 0; d < 4; ++d)
-        w[d] = make_uint4(pack2<PREC>(dv[d][0], dv[d][1]), pack2<PREC>(dv[d][2], dv[d][3]),
-                          pack2<PREC>(dv[d][4], dv[d][5]), pack2<PREC>(dv[d][6], dv[d][7]));
-      // store i writes row 4 rg + x, x = (i + rg / 2) % 4: eight consecutive
-      // lanes then cover the eight 16-byte bank groups
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int x = (i + (rg >> 1)) & 3;
-        const uint4 v = x == 0 ? w[0] : x == 1 ? w[1] : x == 2 ? w[2] : w[3];
-        *reinterpret_cast<uint4*>(blk + core_offset(4 * rg + x, k8 * 8)) = v;
-      }
-      fence_proxy_async_smem();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kb])) : "memory");
+      tmem_st16(tmem + lane_base + (uint32_t)(kb * (TK / 2)), wv);
+      tmem_st16(tmem + lane_base + (uint32_t)(kb * (TK / 2) + 16), wv + 16);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[kb])) : "memory");
     }
-    // epilogue of each column tile: warp w reads lanes 32 (w % 4) .. + 31, columns TNW/4 (w / 4) .. + TNW/4 - 1
-    const int quad = warp & 3, cq = warp >> 2;
+    // epilogue of each column tile: warp w reads lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31
+    const int cq = warp >> 2;
     float* stg = sV + warp * kWsStageFloats;
-    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     const bool vec_ok = (h & 3) == 0 && (reinterpret_cast<uintptr_t>(VWh) & 15) == 0;
     for (int j = 0; j < n_my; ++j) {
       const int buf = j & 1;
@@ -771,22 +758,19 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
         break;
       }
       tc_fence_after();
-      // pieces of 16 columns; the load of piece hf + 1 is in flight while
-      // piece hf is scaled, transposed and stored
-      constexpr int NP = TNW / 64;
+      constexpr int NP = TN / 64;  // pieces of 16 columns per warp
       uint32_t rg2[2][16];
-      const uint32_t tbase = tmem + (uint32_t)(buf * TNW) + lane_base + (uint32_t)(cq * (TNW / 4));
+      const uint32_t tbase = tmem + kTaAccCol + (uint32_t)(buf * TN) + lane_base + (uint32_t)(cq * (TN / 4));
       tmem_ld16_issue(tbase, rg2[0]);
       tmem_wait16(rg2[0]);
 #pragma unroll
       for (int hf = 0; hf < NP; ++hf) {
         if (hf + 1 < NP) tmem_ld16_issue(tbase + (uint32_t)((hf + 1) * 16), rg2[(hf + 1) & 1]);
         const uint32_t* a = rg2[hf & 1];
-        const int cc = cq * (TNW / 4) + hf * 16;
-        const int col0 = (nt_begin + j) * TNW + cc;
+        const int col0 = (nt_begin + j) * TN + cq * (TN / 4) + hf * 16;
         // row `lane` of the piece; its four 16-byte groups are XOR-swizzled by
-        // (row / 2) % 4, which keeps both the row-wise writes and the
-        // group-wise reads below free of bank conflicts
+        // (row / 2) % 4, so that the row-wise writes and the group-wise reads
+        // below are free of bank conflicts
 #pragma unroll
         for (int g = 0; g < 4; ++g)
           *reinterpret_cast<float4*>(stg + lane * 16 + 4 * (g ^ ((lane >> 1) & 3))) =
@@ -795,9 +779,9 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int rr = 8 * i + (lane >> 2), g = lane & 3;
-          const float4 v = *reinterpret_cast<const float4*>(stg + rr * 16 + 4 * (g ^ ((rr >> 1) & 3)));
-          const int grow = row0 + quad * 32 + rr, gcol = col0 + 4 * g;
+          const int r2 = 8 * i + (lane >> 2), g = lane & 3;
+          const float4 v = *reinterpret_cast<const float4*>(stg + r2 * 16 + 4 * (g ^ ((r2 >> 1) & 3)));
+          const int grow = row0 + quad * 32 + r2, gcol = col0 + 4 * g;
           if (grow < n_rows && gcol < h) {
             float* out = VWh + (size_t)grow * h + gcol;
             if (vec_ok) {
@@ -842,7 +826,7 @@ __global__ __launch_bounds__(kWsThreads, 1) void k_kernel_eval_tc_ws(const float
 // accumulator (three rotating 128-column TMEM buffers), which the epilogue
 // warps drain into FP32 registers (round to nearest) as each block completes;
 // the cross terms, 2^-11 smaller, share a fourth accumulator over all of K.
-// Roles as in k_kernel_eval_tc_ws; the builders build a pass, then drain its
+// Roles as in k_kernel_eval_tc_ta; the builders build a pass, then drain its
 // blocks, and the drain of its last block (all MMAs before it complete) frees
 // A for the next pass.
 constexpr int kSpStages = 2;
@@ -1405,41 +1389,34 @@ static cudaError_t launch_tc_net(const wmc_params& p, int prec, const float* V, 
   const size_t n16 = (size_t)g.NT * KB * kTileBytes / 2;
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   const int row_tiles = (max_rows + TM - 1) / TM;
-  const int tnw = g_h(p) > TN ? 256 : 128;
-  const size_t ws_sm = ws_smem_bytes(KB, g_h(p), tnw);
-  if ((prec == WMC_BF16 || prec == WMC_FP16) && KB <= kWsMaxKB && ws_sm <= 226 * 1024) {
-    // warp-specialised form.  The column tiles are split over grid.y by the
-    // factor that minimises waves x per-CTA work, with the fixed part of a CTA
-    // (set-up and building A) counted as three 128-column tiles.
+  if ((prec == WMC_BF16 || prec == WMC_FP16) && KB <= kTaMaxKB && ta_smem_bytes(g_h(p)) <= 226 * 1024) {
+    // A in tensor memory; 128-column tiles split over grid.y as below
     const uint16_t* img = prec == WMC_BF16 ? base : base + n16;
     const long long sms = num_sms();
-    const int ntw = (g.NT * TN + tnw - 1) / tnw;
     int n_split = 1;
     long long best = -1;
-    for (int ns = 1; ns <= ntw; ns *= 2) {
+    for (int ns = 1; ns <= g.NT; ns *= 2) {
       const long long waves = ((long long)row_tiles * ns + sms - 1) / sms;
-      const long long cost = waves * (3 + (long long)((ntw + ns - 1) / ns) * (tnw / TN));
+      const long long cost = waves * (3 + (long long)((g.NT + ns - 1) / ns));
       if (best < 0 || cost < best) {
         best = cost;
         n_split = ns;
       }
     }
-    const dim3 ws_grid(row_tiles, n_split);
-#define WMC_LAUNCH_WS(PR, TW)                                                                                    \
-  do {                                                                                                           \
-    raise_smem_limit(reinterpret_cast<const void*>(k_kernel_eval_tc_ws<PR, TW, NET>), ws_sm);                   \
-    k_kernel_eval_tc_ws<PR, TW, NET><<<ws_grid, kWsThreads, ws_sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ,      \
-                                                                        n_occ_dev, n_occ_host, img, KB, g.NT,    \
-                                                                        n_split, c, VWh, flags);                 \
-  } while (0)
-    if (prec == WMC_BF16) {
-      if (tnw == 256) WMC_LAUNCH_WS(WMC_BF16, 256);
-      else WMC_LAUNCH_WS(WMC_BF16, 128);
-    } else {
-      if (tnw == 256) WMC_LAUNCH_WS(WMC_FP16, 256);
-      else WMC_LAUNCH_WS(WMC_FP16, 128);
-    }
-#undef WMC_LAUNCH_WS
+    const size_t sm = ta_smem_bytes(g_h(p));
+    const void* fn = prec == WMC_BF16 ? reinterpret_cast<const void*>(k_kernel_eval_tc_ta<WMC_BF16, NET>)
+                                      : reinterpret_cast<const void*>(k_kernel_eval_tc_ta<WMC_FP16, NET>);
+    const cudaError_t e = raise_smem_limit(fn, sm);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(row_tiles, n_split);
+    if (prec == WMC_BF16)
+      k_kernel_eval_tc_ta<WMC_BF16, NET><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                                      n_occ_host, img, KB, g.NT, n_split, c, VWh,
+                                                                      flags);
+    else
+      k_kernel_eval_tc_ta<WMC_FP16, NET><<<grid, kWsThreads, sm, s>>>(V, p.n_x, p.bc_potential, p.Q, occ, n_occ_dev,
+                                                                      n_occ_host, img, KB, g.NT, n_split, c, VWh,
+                                                                      flags);
     return cudaGetLastError();
   }
   if (prec == WMC_FP16_SPLIT && ws_split_smem_bytes(KB, g_h(p)) <= 226 * 1024) {
