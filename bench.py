@@ -40,6 +40,11 @@ L2_BYTES = 129 * 2 ** 20
 K_STEP_DRAM_BYTES = 23258368
 K_STEP_TRAFFIC_SOURCE = ("ncu --set full capture of k_step on double-barrier-16384 (5th launch): dram read "
                          "23.26 MB + write 0 per launch (profiles/k_step_double-barrier-16384.md)")
+# DRAM bytes of one BF16 launch of k_kernel_eval_tc_ta on all 16384 cells (the sine image and the potential
+# come from L2 after the first touch; the 32 MB of output rows stay in L2)
+TC_TA_DRAM_BYTES = 743424 + 1280
+TC_TA_DRAM_SOURCE = ("ncu --set full capture of k_kernel_eval_tc_ta<BF16> on double-barrier-16384 (4th launch): "
+                     "dram read 743.4 KB + write 1.3 KB (profiles/k_kernel_eval_tc_ta_double-barrier-16384.md)")
 
 
 def _env_int(k, d):
@@ -561,6 +566,9 @@ def kernel_eval_rate(wmc, torch, dev, stream, flush, reps=10):
                 r["roofline"] = {"bound": "tensor", "achieved": issued / sec / 1e12, "peak": peak / 1e12,
                                  "unit": "TFLOP/s", "frac": issued / sec / peak, "traffic": None,
                                  "peak_source": psrc}
+                if form == "bf16":
+                    r["roofline"]["traffic"] = TC_TA_DRAM_BYTES
+                    r["roofline"]["traffic_source"] = TC_TA_DRAM_SOURCE
             res[form] = r
     # the N = 2 barycentric network (Sec. 2.3) on the same cells
     n2 = {}
