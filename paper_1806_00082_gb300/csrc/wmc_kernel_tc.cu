@@ -1390,7 +1390,9 @@ static cudaError_t launch_tc_net(const wmc_params& p, int prec, const float* V, 
   const float c = (float)(-2.0 / (kHbarEVs * (double)p.Q));
   const int row_tiles = (max_rows + TM - 1) / TM;
   if ((prec == WMC_BF16 || prec == WMC_FP16) && KB <= kTaMaxKB && ta_smem_bytes(g_h(p)) <= 226 * 1024) {
-    // A in tensor memory; 128-column tiles split over grid.y as below
+    // A in tensor memory.  The 128-column tiles are split over grid.y by the
+    // factor that minimises waves x per-CTA work, with the fixed part of a CTA
+    // (set-up and building A) counted as three column tiles.
     const uint16_t* img = prec == WMC_BF16 ? base : base + n16;
     const long long sms = num_sms();
     int n_split = 1;
